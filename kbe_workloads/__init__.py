@@ -1,0 +1,211 @@
+"""Seeded, synthetic inputs for the Kadanoff-Baym time stepper.
+
+This module is shared by the FP64 CPU oracle, the tests and ``bench.py``.  It
+holds only *inputs*: the imaginary-time grid (DLR nodes), the model
+parameters drawn from seeds, the equilibrium Matsubara Green's function of the
+models whose thermal state has a closed form, and the drive protocols.  It
+contains none of the time-stepping arithmetic (weights, history integrals,
+Volterra solves, self-energies); those live separately in ``oracle/`` and in
+the CUDA library.
+
+Conventions (Sec. 2 of the paper, Table 1): fermions (xi = -1), matrices are
+N_o x N_o complex, G^M(tau) = -<T d(tau) d^dagger> on (0, beta).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+XI_FERMION = -1
+
+
+# ---------------------------------------------------------------------------
+# DLR imaginary-time grid (Sec. 2.5; the construction of Kaye et al., the
+# paper's reference kaye22: interpolative decomposition of the Lehmann kernel).
+# ---------------------------------------------------------------------------
+
+def _cheb_panel(a: float, b: float, p: int) -> np.ndarray:
+    """p Chebyshev points of the first kind mapped to (a, b)."""
+    j = np.arange(p)
+    x = np.cos((2 * j + 1) * np.pi / (2 * p))[::-1]
+    return 0.5 * (a + b) + 0.5 * (b - a) * x
+
+
+def _lehmann_kernel_unit(tau: np.ndarray, om: np.ndarray) -> np.ndarray:
+    """Fermionic kernel K(tau, w) = exp(-tau w) / (1 + exp(-w)) at beta = 1."""
+    t = tau[:, None]
+    w = om[None, :]
+    pos = w >= 0
+    out = np.empty(np.broadcast_shapes(t.shape, w.shape))
+    wp = np.where(pos, w, 0.0)
+    wn = np.where(pos, 0.0, w)
+    kp = np.exp(-t * wp) / (1.0 + np.exp(-wp))
+    kn = np.exp((1.0 - t) * wn) / (1.0 + np.exp(wn))
+    out[...] = np.where(pos, kp, kn)
+    return out
+
+
+def dlr_grid(lam: float, eps: float, beta: float, p: int = 24):
+    """DLR real frequencies and imaginary-time nodes for cutoff ``lam`` and
+    accuracy ``eps`` (Sec. 2.5).  Returns ``(tau_nodes, omega_nodes)``, both
+    sorted, of equal length r = O(log(lam) log(1/eps)).
+
+    Frequencies are chosen by column-pivoted QR of the kernel sampled on a
+    fine composite Chebyshev grid, dyadically refined toward w = 0; the tau
+    nodes by pivoted QR of the selected columns' rows (fine tau grid refined
+    toward both ends of (0, beta)).  The result is a grid (input data): the
+    oracle and the CUDA library each build their own interpolation and
+    quadrature matrices from it.
+    """
+    from scipy.linalg import qr
+
+    nlev = max(1, int(math.ceil(math.log2(max(lam, 2.0)))))
+    # frequency panels: [0,1],[1,2],[2,4],...,[lam/2,lam] and mirror
+    edges = [0.0, 1.0] + [2.0 ** j for j in range(1, nlev)] + [lam]
+    edges = sorted(set(e for e in edges if e <= lam))
+    wpos = np.concatenate([_cheb_panel(edges[i], edges[i + 1], p)
+                           for i in range(len(edges) - 1)])
+    wfine = np.concatenate([-wpos[::-1], wpos])
+    # tau panels on (0, 1/2] refined toward 0, mirrored onto [1/2, 1)
+    tedges = [0.0] + [2.0 ** (-j) for j in range(nlev + 1, 0, -1)]
+    tl = np.concatenate([_cheb_panel(tedges[i], tedges[i + 1], p)
+                         for i in range(len(tedges) - 1)])
+    tfine = np.concatenate([tl, 1.0 - tl[::-1]])
+    A = _lehmann_kernel_unit(tfine, wfine)
+    _, R, piv = qr(A, mode="economic", pivoting=True)
+    d = np.abs(np.diag(R))
+    r = int(np.sum(d > eps * d[0]))
+    om = wfine[piv[:r]]
+    _, _, piv2 = qr(A[:, piv[:r]].T, mode="economic", pivoting=True)
+    tau = tfine[piv2[:r]]
+    return np.sort(tau) * beta, np.sort(om) / beta
+
+
+# ---------------------------------------------------------------------------
+# Equilibrium initial states that have closed forms (inputs, not solved here)
+# ---------------------------------------------------------------------------
+
+def fermi(e, beta):
+    e = np.asarray(e, dtype=float)
+    return 0.5 * (1.0 - np.tanh(0.5 * beta * e))
+
+
+def semicircle_gm(tau: np.ndarray, beta: float, eps0: float, v: float = 1.0,
+                  nquad: int = 4000) -> np.ndarray:
+    """G^M(tau) of the Bethe lattice (semicircular DOS of half-bandwidth 2v
+    centred on eps0): -int A(w) exp(-tau w) / (1 + exp(-beta w)) dw, by
+    Gauss-Chebyshev quadrature of the second kind (exact weight sqrt(1-x^2))."""
+    j = np.arange(1, nquad + 1)
+    th = j * np.pi / (nquad + 1)
+    x = np.cos(th)
+    wq = np.pi / (nquad + 1) * np.sin(th) ** 2  # int_{-1}^{1} f sqrt(1-x^2)
+    w = eps0 + 2.0 * v * x
+    # A(w) dw = sqrt(4v^2-(w-eps0)^2)/(2 pi v^2) dw = (2/pi) sqrt(1-x^2) dx
+    t = np.asarray(tau, dtype=float)[:, None]
+    ker = _lehmann_kernel_unit(t[:, 0] / beta, w * beta)
+    return -(2.0 / np.pi) * (ker * wq[None, :]).sum(axis=1)
+
+
+def two_level_gm(tau, beta, ed, eb, V):
+    """Impurity block G_dd^M(tau) of the two-site model H = [[ed, V], [V, eb]]
+    (exact diagonalisation of the 2x2 single-particle Hamiltonian)."""
+    H = np.array([[ed, V], [V, eb]], dtype=float)
+    E, U = np.linalg.eigh(H)
+    wgt = np.abs(U[0, :]) ** 2
+    t = np.asarray(tau, dtype=float)
+    ker = _lehmann_kernel_unit(t / beta, E * beta)
+    return -(ker * wgt[None, :]).sum(axis=1)
+
+
+def free_level_gm(tau, beta, eps_mat):
+    """G^M(tau) of a non-interacting N_o-level system with Hermitian level
+    matrix eps_mat: -U diag(K(tau, E)) U^dagger."""
+    E, U = np.linalg.eigh(np.asarray(eps_mat, dtype=complex))
+    t = np.asarray(tau, dtype=float)
+    ker = _lehmann_kernel_unit(t / beta, E * beta)  # (ntau, No)
+    return -np.einsum("ia,ta,ja->tij", U, ker, U.conj())
+
+
+# ---------------------------------------------------------------------------
+# Workload descriptions (the five configurations this project is measured on)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    model: str                 # "none" | "bethe" | "bath"
+    nt: int
+    h: float
+    k: int
+    beta: float
+    nao: int = 1
+    n_inst: int = 1
+    dlr_lambda: float = 100.0
+    dlr_eps: float = 1e-10
+    svd_tol: float = 0.0       # 0 -> dense (uncompressed) storage
+    leaf: int = 64
+    rho_mode: int = 0          # 0 horizontal, 1 diagonal
+    max_iter: int = 50
+    tol: float = 1e-12
+    seed: int = 0
+    params: dict = field(default_factory=dict)
+
+
+def bethe_eps0(seed: int, n: int = 1) -> np.ndarray:
+    """On-site levels eps0 ~ U[-0.5, 0.5] drawn from numpy's default_rng(seed)."""
+    return np.random.default_rng(seed).uniform(-0.5, 0.5, size=n)
+
+
+def quench_eps(nt: int, h: float, eps_before: float, eps_after: float,
+               t_quench: float) -> np.ndarray:
+    """Level eps(t) on the grid t = n h (n = -1 is the equilibrium branch),
+    switched from eps_before to eps_after for t >= t_quench."""
+    n = np.arange(-1, nt)
+    t = np.maximum(n, 0) * h
+    e = np.where((n >= 0) & (t >= t_quench - 1e-12), eps_after, eps_before)
+    return e.astype(float)
+
+
+def bethe_workload(name="C1", nt=256, h=0.025, k=5, beta=5.0, seed=0,
+                   n_inst=1, svd_tol=0.0, leaf=64, quench=None,
+                   dlr_lambda=100.0, dlr_eps=1e-10, tol=1e-12, max_iter=50,
+                   rho_mode=0):
+    """Bethe-lattice workload (Sigma = v^2 G, v = 1).  Returns a dict of
+    arrays with everything both implementations need: DLR grid, eps(t) per
+    instance (index 0 is the equilibrium branch), G^M on the DLR nodes."""
+    tau, om = dlr_grid(dlr_lambda, dlr_eps, beta)
+    eps0 = bethe_eps0(seed, n_inst)
+    eps = np.zeros((n_inst, nt + 1, 1, 1), dtype=complex)
+    gm = np.zeros((n_inst, len(tau), 1, 1), dtype=complex)
+    for i in range(n_inst):
+        if quench is None:
+            eps[i, :, 0, 0] = eps0[i]
+            gm[i, :, 0, 0] = semicircle_gm(tau, beta, eps0[i])
+        else:
+            e_before, e_after, tq = quench
+            eps[i, :, 0, 0] = quench_eps(nt, h, e_before, e_after, tq)
+            gm[i, :, 0, 0] = semicircle_gm(tau, beta, e_before)
+    wl = Workload(name=name, model="bethe", nt=nt, h=h, k=k, beta=beta,
+                  nao=1, n_inst=n_inst, dlr_lambda=dlr_lambda, dlr_eps=dlr_eps,
+                  svd_tol=svd_tol, leaf=leaf, tol=tol, max_iter=max_iter,
+                  seed=seed, rho_mode=rho_mode, params={"v": 1.0})
+    return {"wl": wl, "tau": tau, "omega": om, "eps": eps, "gm": gm,
+            "model_params": np.array([[1.0]] * n_inst)}
+
+
+def c1_workload(seed=0, **kw):
+    """Plain FP64 Bethe lattice, beta=5, N_t=256, h=0.025, order 5, DLR
+    (Lambda=100, eps=1e-10), undriven, eps0 ~ U[-0.5,0.5] from ``seed``."""
+    return bethe_workload(name="C1", nt=kw.pop("nt", 256), h=kw.pop("h", 0.025),
+                          k=kw.pop("k", 5), beta=5.0, seed=seed, **kw)
+
+
+def c2_workload(seed=0, **kw):
+    """Bethe lattice with HODLR (leaf 64, SVD tol 1e-8), N_t=4096, h=0.02,
+    beta=5, level quench eps0: 0 -> 1 at t = 5."""
+    return bethe_workload(name="C2", nt=kw.pop("nt", 4096), h=kw.pop("h", 0.02),
+                          k=kw.pop("k", 5), beta=5.0, seed=seed,
+                          svd_tol=kw.pop("svd_tol", 1e-8), leaf=kw.pop("leaf", 64),
+                          quench=(0.0, 1.0, 5.0), **kw)
