@@ -1,0 +1,175 @@
+/*
+ * hkbe.h -- C ABI of the GB300 Kadanoff-Baym time stepper (HODLR history
+ * integrals, high-order Gregory/BDF weights, DLR thermal leg).
+ *
+ * The calls follow the user workflow of the paper: construct the objects
+ * (Sec. 3.1), set the initial thermal state on the DLR grid (Sec. 2.5, 3.2),
+ * bootstrap the first k steps (Sec. 2.6 / 3.3), time-step with a
+ * self-consistency loop per step (Sec. 3.4), and read G^R, G^<, G^tv and
+ * observables (Tables 2-5, Sec. 4.2 observables).
+ *
+ * Conventions for every call
+ *   - Return value: HKBE_OK (0) or a negative HKBE_ERR_* code; the message of
+ *     the last failure is returned by hkbe_last_error().
+ *   - Complex numbers are interleaved (re, im) pairs of double.  An N_o x N_o
+ *     matrix is stored row-major, so one matrix is 2*N_o*N_o doubles.
+ *   - Every pointer argument is a HOST pointer owned by the caller; the
+ *     library copies in or out before returning (inputs) or after the device
+ *     work of the call completed (outputs).  The library owns all device
+ *     memory it allocates and frees it in hkbe_destroy().
+ *   - Device work is issued on the CUDA stream given to hkbe_create() (NULL
+ *     means the legacy default stream).
+ *   - A handle is not thread-safe (the paper's dyson/dlr_info objects are not
+ *     either, Sec. 4.3); use one handle per host thread.
+ *   - Time arguments are step indices t = 0..nt-1; the equilibrium branch
+ *     value of one-time functions (eps, drive) is index -1 (Sec. 3.2).
+ *   - Fermions only (xi = -1) in this version; HKBE_ERR_ARG otherwise.
+ */
+#ifndef HKBE_H
+#define HKBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HKBE_OK = 0,
+  HKBE_ERR_ARG = -1,      /* invalid argument, size or call order          */
+  HKBE_ERR_CUDA = -2,     /* CUDA runtime failure (message has the detail) */
+  HKBE_ERR_NOCONV = -3,   /* self-consistency did not reach tol in max_iter */
+  HKBE_ERR_RANGE = -4,    /* time index outside the stored/allowed region   */
+  HKBE_ERR_RANK = -5,     /* HODLR block rank exceeded its capacity r_max   */
+  HKBE_ERR_NAN = -6,      /* non-finite value met during a step             */
+  HKBE_ERR_NOMEM = -7     /* device or host allocation failed               */
+};
+
+/* Self-energy functionals (evaluated on the device at every step). */
+enum {
+  HKBE_MODEL_NONE = 0,   /* Sigma = 0                                              */
+  HKBE_MODEL_BETHE = 1,  /* Bethe-lattice DMFT: Sigma = v^2 G (Eq. Hybrid, N_o=1)  */
+  HKBE_MODEL_BATH = 2    /* fixed bath: Sigma = V g_b V^dagger, bath levels eps_b   */
+};
+
+/* Storage / arithmetic of the history integrals. */
+enum {
+  HKBE_PREC_FP64 = 0      /* dense lower-triangular complex128 storage, FP64 */
+};
+
+typedef struct {
+  int32_t nt;         /* number of time steps N_t (>= k + 2)                    */
+  int32_t k;          /* integration order, 1..5 (Appendix A)                   */
+  int32_t nao;        /* orbitals N_o, 1..4                                     */
+  int32_t xi;         /* statistics: -1 fermions                                */
+  int32_t n_inst;     /* independent instances stepped together (>= 1)          */
+  int32_t rho_mode;   /* 0 horizontal, 1 diagonal density-matrix scheme (Sec. 3.3) */
+  int32_t precision;  /* HKBE_PREC_*                                             */
+  int32_t max_iter;   /* self-consistency iterations per step (Sec. 3.4)        */
+  double h;           /* time step                                              */
+  double beta;        /* inverse temperature of the thermal initial state       */
+  double tol;         /* self-consistency tolerance on max |G^(i) - G^(i-1)|     */
+} hkbe_params;
+
+typedef struct hkbe_s hkbe_t;
+
+/* Create a stepper for p->n_inst instances sharing nt, k, nao, h, beta.
+ * `stream` is a cudaStream_t (or NULL).  On success *out receives the handle.
+ * Errors: HKBE_ERR_ARG (bad sizes), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
+int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out);
+
+/* Release every device and host resource of h (NULL is accepted). */
+int hkbe_destroy(hkbe_t* h);
+
+/* Message of the last failure on h (or of the last failed hkbe_create when h
+ * is NULL).  The pointer stays valid until the next call on h. */
+const char* hkbe_last_error(const hkbe_t* h);
+
+/* DLR imaginary-time grid (Sec. 2.5): r nodes tau[r] in (0, beta) and the r
+ * DLR real frequencies omega[r] (both produced by the caller's DLR
+ * construction for cutoff Lambda and accuracy eps).  The library builds its
+ * own evaluation, reversal, product and convolution matrices from them.
+ * Must precede hkbe_set_matsubara.  Errors: HKBE_ERR_ARG (r < 1, r > 128,
+ * nodes outside (0, beta)). */
+int hkbe_set_dlr(hkbe_t* h, int r, const double* tau, const double* omega);
+
+/* Equilibrium Matsubara Green's function on the DLR nodes, G^M(tau_i), for
+ * every instance: gm[n_inst][r][N_o][N_o] complex (Table 4, get_mat/set_mat).
+ * Also precomputes the convolution tensor of Eq. KBET (initGMConvTensor). */
+int hkbe_set_matsubara(hkbe_t* h, const double* gm);
+
+/* Mean-field Hamiltonian eps(t) = h0(t) + Sigma^MF(t) - mu (Eq. KBEM-KBEL) for
+ * t = -1..nt-1 and every instance: eps[n_inst][nt+1][N_o][N_o] complex, index
+ * 0 holding the equilibrium branch eps(0_|). */
+int hkbe_set_hamiltonian(hkbe_t* h, const double* eps);
+
+/* Self-energy functional and its parameters, params[n_inst][nparams]:
+ *   HKBE_MODEL_NONE : nparams 0.
+ *   HKBE_MODEL_BETHE: nparams >= 1, params[0] = v (Sigma = v^2 G).
+ *   HKBE_MODEL_BATH : nparams = 1 + nb + 2*N_o*nb with
+ *       params[0] = nb (1..4 bath levels), params[1..nb] = eps_b,
+ *       then V[N_o][nb] complex interleaved (Sigma = V g_b V^dagger). */
+int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams);
+
+/* Bootstrap the first k+1 time steps (Sec. 3.3, dyson_start_ntti): mean-field
+ * guess (green_from_H) followed by global iterations of Sigma and the start
+ * square with the polynomial weights of Appendix A.  Outputs (may be NULL):
+ * iters[n_inst], err[n_inst].  Errors: HKBE_ERR_NOCONV if max_iter is
+ * reached without err < tol (state is kept), HKBE_ERR_ARG (call order). */
+int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* err);
+
+/* Advance every instance by n_steps time steps (Sec. 3.4: extrapolate, then
+ * per iteration Sigma, retarded row, mixed, lesser column, density matrix,
+ * until max |G^(i) - G^(i-1)| < tol or max_iter).  Outputs (may be NULL):
+ * iters[n_inst*n_steps], err[n_inst*n_steps].  Errors: HKBE_ERR_RANGE (past
+ * nt-1), HKBE_ERR_NOCONV (state kept; the step counter still advances). */
+int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err);
+
+/* Current time step T (the last completed step), -1 before the bootstrap. */
+int hkbe_current_step(const hkbe_t* h, int32_t* T);
+
+/* G^R(t, t') for 0 <= t' <= t <= T into out[N_o][N_o] (Table 3 get_ret).
+ * Errors: HKBE_ERR_RANGE outside the computed triangle. */
+int hkbe_get_ret(hkbe_t* h, int inst, int t, int tp, double* out);
+
+/* G^<(t, t') for any 0 <= t, t' <= T (Table 3 get_les; the upper triangle
+ * uses G^<(t,t') = -[G^<(t',t)]^dagger, Eq. GLantiHerm). */
+int hkbe_get_les(hkbe_t* h, int inst, int t, int tp, double* out);
+
+/* Mixed row G^tv(t, tau_i), i = 0..r-1, into out[r][N_o][N_o] (Table 4 get_tv). */
+int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out);
+
+/* Whole retarded row G^R(T, 0..T) and lesser column G^<(0..T, T) of step T:
+ * gr[T+1][N_o][N_o], gl[T+1][N_o][N_o] (either may be NULL). */
+int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl);
+
+/* Density matrix rho(t) = xi i G^<(t,t) (Sec. 3.3) for t = 0..T of every
+ * instance: rho[n_inst][T+1][N_o][N_o] complex. */
+int hkbe_get_density(hkbe_t* h, double* rho);
+
+/* Device bytes held by the handle. */
+int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);
+
+/* ---- host-only numerics, exported for inspection (no device work) ---- */
+
+/* Appendix A weights for order k (1..5): a[k+1] (BDF), omega[k+1] (Gregory),
+ * D[(k+1)*(k+1)] (D_ml), I0[(k+1)*(k+1)] (I_{0,n,l}, row n).  Any output may
+ * be NULL. */
+int hkbe_weights(int k, double* a, double* omega, double* D, double* I0);
+
+/* Integration rule w^(n)_l of int_0^{n h} (unit spacing) into w[max(n,k)+1]. */
+int hkbe_rule(int k, int n, double* w);
+
+/* DLR matrices the library builds from the grid (cardinal functions by LU
+ * solves, integrals by tanh-sinh quadrature): e0[r] (evaluation at tau=0), ebeta[r] (at beta), rev[r*r]
+ * (values at beta - tau_i), q[r*r] (int l_a l_b), phi[r*r*r] (phi[a][c][i] =
+ * int l_a(t) l_c^ext(t - tau_i) dt).  Outputs may be NULL. */
+int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta,
+                      int xi, double* e0, double* ebeta, double* rev, double* q,
+                      double* phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HKBE_H */

@@ -1,0 +1,306 @@
+"""Python binding of libhkbe, the GB300 Kadanoff-Baym time stepper.
+
+The functions mirror the C ABI of ``include/hkbe.h`` one to one (same names,
+same argument order); they only marshal numpy arrays to host pointers and turn
+negative status codes into ``HKBEError``.  All computation happens in the CUDA
+library; there is no Python fallback: importing works without a GPU (for the
+host-only utilities), but any stepping call needs the CUDA library and a GPU
+and raises otherwise.
+
+``Stepper`` is a thin convenience wrapper owning a handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+HKBE_OK = 0
+ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "HKBE_ERR_RANGE",
+          -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM"}
+MODEL_NONE, MODEL_BETHE, MODEL_BATH = 0, 1, 2
+PREC_FP64 = 0
+
+
+class HKBEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hkbe_params(C.Structure):
+    _fields_ = [("nt", C.c_int32), ("k", C.c_int32), ("nao", C.c_int32), ("xi", C.c_int32),
+                ("n_inst", C.c_int32), ("rho_mode", C.c_int32), ("precision", C.c_int32),
+                ("max_iter", C.c_int32), ("h", C.c_double), ("beta", C.c_double), ("tol", C.c_double)]
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int32)
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libhkbe.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libhkbe.so is not built; run __graft_entry__.build()")
+    L = C.CDLL(_build.LIB)
+    H = C.c_void_p
+    sig = {
+        "hkbe_create": ([C.POINTER(hkbe_params), C.c_void_p, C.POINTER(H)], C.c_int),
+        "hkbe_destroy": ([H], C.c_int),
+        "hkbe_last_error": ([H], C.c_char_p),
+        "hkbe_set_dlr": ([H, C.c_int, _D, _D], C.c_int),
+        "hkbe_set_matsubara": ([H, _D], C.c_int),
+        "hkbe_set_hamiltonian": ([H, _D], C.c_int),
+        "hkbe_set_model": ([H, C.c_int, _D, C.c_int], C.c_int),
+        "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
+        "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
+        "hkbe_current_step": ([H, _I], C.c_int),
+        "hkbe_get_ret": ([H, C.c_int, C.c_int, C.c_int, _D], C.c_int),
+        "hkbe_get_les": ([H, C.c_int, C.c_int, C.c_int, _D], C.c_int),
+        "hkbe_get_tv": ([H, C.c_int, C.c_int, _D], C.c_int),
+        "hkbe_get_row": ([H, C.c_int, C.c_int, _D, _D], C.c_int),
+        "hkbe_get_density": ([H, _D], C.c_int),
+        "hkbe_get_stats": ([H, C.POINTER(C.c_size_t)], C.c_int),
+        "hkbe_weights": ([C.c_int, _D, _D, _D, _D], C.c_int),
+        "hkbe_rule": ([C.c_int, C.c_int, _D], C.c_int),
+        "hkbe_dlr_matrices": ([C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, _D, _D, _D], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_I)
+
+
+def _cplx(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128).reshape(shape))
+    return a.view(np.float64)
+
+
+def _check(rc, h=None):
+    if rc != HKBE_OK:
+        msg = load().hkbe_last_error(h).decode()
+        raise HKBEError(rc, msg)
+
+
+# ---- one-to-one wrappers of the C ABI -------------------------------------
+
+def hkbe_create(params: hkbe_params, stream=None):
+    h = C.c_void_p()
+    _check(load().hkbe_create(C.byref(params), stream, C.byref(h)), None)
+    return h
+
+
+def hkbe_destroy(h):
+    load().hkbe_destroy(h)
+
+
+def hkbe_set_dlr(h, tau, omega):
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    _check(load().hkbe_set_dlr(h, len(tau), _dp(tau), _dp(om)), h)
+
+
+def hkbe_set_matsubara(h, gm):
+    g = _cplx(gm, np.shape(gm))
+    _check(load().hkbe_set_matsubara(h, _dp(g)), h)
+
+
+def hkbe_set_hamiltonian(h, eps):
+    e = _cplx(eps, np.shape(eps))
+    _check(load().hkbe_set_hamiltonian(h, _dp(e)), h)
+
+
+def hkbe_set_model(h, model, params):
+    p = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64))) if params is not None else None
+    npar = 0 if p is None else p.shape[1]
+    _check(load().hkbe_set_model(h, int(model), _dp(p), int(npar)), h)
+
+
+def hkbe_bootstrap(h, n_inst, max_iter, tol):
+    it = np.zeros(n_inst, np.int32)
+    er = np.zeros(n_inst)
+    rc = load().hkbe_bootstrap(h, int(max_iter), float(tol), _ip(it), _dp(er))
+    _check(rc, h)
+    return it, er
+
+
+def hkbe_step(h, n_inst, n_steps, check=True):
+    it = np.zeros(max(1, n_inst * n_steps), np.int32)
+    er = np.zeros(max(1, n_inst * n_steps))
+    rc = load().hkbe_step(h, int(n_steps), _ip(it), _dp(er))
+    if check:
+        _check(rc, h)
+    return it[:n_inst * n_steps].reshape(n_steps, n_inst), er[:n_inst * n_steps].reshape(n_steps, n_inst), rc
+
+
+def hkbe_current_step(h):
+    t = np.zeros(1, np.int32)
+    _check(load().hkbe_current_step(h, _ip(t)), h)
+    return int(t[0])
+
+
+def hkbe_get_ret(h, nao, inst, t, tp):
+    out = np.zeros((nao, nao), np.complex128)
+    _check(load().hkbe_get_ret(h, inst, t, tp, _dp(out.view(np.float64))), h)
+    return out
+
+
+def hkbe_get_les(h, nao, inst, t, tp):
+    out = np.zeros((nao, nao), np.complex128)
+    _check(load().hkbe_get_les(h, inst, t, tp, _dp(out.view(np.float64))), h)
+    return out
+
+
+def hkbe_get_tv(h, nao, r, inst, t):
+    out = np.zeros((r, nao, nao), np.complex128)
+    _check(load().hkbe_get_tv(h, inst, t, _dp(out.view(np.float64))), h)
+    return out
+
+
+def hkbe_get_row(h, nao, inst, T):
+    gr = np.zeros((T + 1, nao, nao), np.complex128)
+    gl = np.zeros((T + 1, nao, nao), np.complex128)
+    _check(load().hkbe_get_row(h, inst, T, _dp(gr.view(np.float64)), _dp(gl.view(np.float64))), h)
+    return gr, gl
+
+
+def hkbe_get_density(h, n_inst, nao, T):
+    out = np.zeros((n_inst, T + 1, nao, nao), np.complex128)
+    _check(load().hkbe_get_density(h, _dp(out.view(np.float64))), h)
+    return out
+
+
+def hkbe_get_stats(h):
+    b = C.c_size_t()
+    _check(load().hkbe_get_stats(h, C.byref(b)), h)
+    return int(b.value)
+
+
+def hkbe_weights(k):
+    a = np.zeros(k + 1)
+    om = np.zeros(k + 1)
+    D = np.zeros((k + 1) * (k + 1))
+    I0 = np.zeros((k + 1) * (k + 1))
+    _check(load().hkbe_weights(k, _dp(a), _dp(om), _dp(D), _dp(I0)))
+    return a, om, D.reshape(k + 1, k + 1), I0.reshape(k + 1, k + 1)
+
+
+def hkbe_rule(k, n):
+    w = np.zeros(max(n, k) + 1)
+    _check(load().hkbe_rule(k, n, _dp(w)))
+    return w
+
+
+def hkbe_dlr_matrices(tau, omega, beta, xi=-1):
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    r = len(tau)
+    e0, eb = np.zeros(r), np.zeros(r)
+    rev, q, phi = np.zeros(r * r), np.zeros(r * r), np.zeros(r * r * r)
+    _check(load().hkbe_dlr_matrices(r, _dp(tau), _dp(om), float(beta), int(xi), _dp(e0), _dp(eb),
+                                    _dp(rev), _dp(q), _dp(phi)))
+    return e0, eb, rev.reshape(r, r), q.reshape(r, r), phi.reshape(r, r, r)
+
+
+# ---- convenience wrapper -----------------------------------------------------
+
+class Stepper:
+    """Owns one handle; inputs are numpy arrays shaped as in include/hkbe.h."""
+
+    def __init__(self, nt, h, k, beta, nao=1, n_inst=1, rho_mode=0, max_iter=50, tol=1e-12,
+                 precision=PREC_FP64, stream=None):
+        self.p = hkbe_params(nt=nt, k=k, nao=nao, xi=-1, n_inst=n_inst, rho_mode=rho_mode,
+                             precision=precision, max_iter=max_iter, h=h, beta=beta, tol=tol)
+        self.nao, self.n_inst, self.nt = nao, n_inst, nt
+        self.h = hkbe_create(self.p, stream)
+        self.r = 0
+
+    def close(self):
+        if self.h:
+            hkbe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_inputs(self, tau, omega, gm, eps, model, model_params):
+        self.r = len(tau)
+        hkbe_set_dlr(self.h, tau, omega)
+        hkbe_set_matsubara(self.h, gm)
+        hkbe_set_hamiltonian(self.h, eps)
+        hkbe_set_model(self.h, model, model_params)
+
+    def bootstrap(self, max_iter=200, tol=None):
+        return hkbe_bootstrap(self.h, self.n_inst, max_iter, self.p.tol if tol is None else tol)
+
+    def step(self, n_steps=1):
+        it, er, _ = hkbe_step(self.h, self.n_inst, n_steps)
+        return it, er
+
+    def run(self):
+        self.bootstrap()
+        T = hkbe_current_step(self.h)
+        return self.step(self.nt - 1 - T)
+
+    def row(self, inst, T):
+        return hkbe_get_row(self.h, self.nao, inst, T)
+
+    def tv(self, inst, t):
+        return hkbe_get_tv(self.h, self.nao, self.r, inst, t)
+
+    def density(self):
+        return hkbe_get_density(self.h, self.n_inst, self.nao, hkbe_current_step(self.h))
+
+    def dense(self, inst=0):
+        """All rows up to the current step as lower-triangular arrays
+        GR[T, t] = G^R(T, t), GLs[T, t] = G^<(t, T) and GTV[T, i]."""
+        T = hkbe_current_step(self.h)
+        GR = np.zeros((T + 1, T + 1, self.nao, self.nao), np.complex128)
+        GL = np.zeros_like(GR)
+        GTV = np.zeros((T + 1, self.r, self.nao, self.nao), np.complex128)
+        for t in range(T + 1):
+            gr, gl = self.row(inst, t)
+            GR[t, :t + 1] = gr
+            GL[t, :t + 1] = gl
+            GTV[t] = self.tv(inst, t)
+        return GR, GL, GTV
+
+
+def model_params_for(workload_dict):
+    """Model id and parameter array of a workload from ``kbe_workloads``."""
+    wl = workload_dict["wl"]
+    if wl.model == "bethe":
+        return MODEL_BETHE, np.asarray(workload_dict["model_params"], dtype=float)
+    if wl.model == "none":
+        return MODEL_NONE, None
+    raise ValueError(wl.model)

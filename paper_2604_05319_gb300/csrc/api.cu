@@ -1,0 +1,533 @@
+// C ABI of the Kadanoff-Baym stepper (declared in include/hkbe.h).
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hkbe.h"
+#include "host_numerics.h"
+#include "state.h"
+
+using hk::Dev;
+using zc = std::complex<double>;
+
+struct hkbe_s {
+  Dev d{};
+  hkbe_params p{};
+  cudaStream_t s = nullptr;
+  std::string err;
+  int cur = -1;
+  bool have_dlr = false, have_gm = false, have_eps = false, have_model = false;
+  bool self_consistent = true;
+  std::vector<double> tau, om, gm_host, eps_host;
+  hk::DLRMats dm;
+  int* any_dev = nullptr;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+static std::string g_create_error;
+
+namespace {
+
+int fail(hkbe_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define HK_CUDA(h, call)                                                            \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(h, HKBE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(hkbe_t* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return fail(h, HKBE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(*p);
+  h->bytes += count * sizeof(T);
+  cudaMemsetAsync(*p, 0, count * sizeof(T), h->s);
+  return HKBE_OK;
+}
+
+int no2(const hkbe_t* h) { return h->p.nao * h->p.nao; }
+
+}  // namespace
+
+extern "C" {
+
+const char* hkbe_last_error(const hkbe_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
+  if (!p || !out) return fail(nullptr, HKBE_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (p->k < 1 || p->k > 5) return fail(nullptr, HKBE_ERR_ARG, "k must be in 1..5");
+  if (p->nt < p->k + 2) return fail(nullptr, HKBE_ERR_ARG, "nt must be >= k + 2");
+  if (p->nao < 1 || p->nao > 4) return fail(nullptr, HKBE_ERR_ARG, "nao must be in 1..4");
+  if (p->xi != -1) return fail(nullptr, HKBE_ERR_ARG, "only fermions (xi = -1) are supported");
+  if (p->n_inst < 1) return fail(nullptr, HKBE_ERR_ARG, "n_inst must be >= 1");
+  if (!(p->h > 0) || !(p->beta > 0)) return fail(nullptr, HKBE_ERR_ARG, "h and beta must be > 0");
+  if (p->rho_mode != 0 && p->rho_mode != 1) return fail(nullptr, HKBE_ERR_ARG, "rho_mode must be 0 or 1");
+  if (p->precision != HKBE_PREC_FP64) return fail(nullptr, HKBE_ERR_ARG, "unsupported precision");
+  if (p->max_iter < 1) return fail(nullptr, HKBE_ERR_ARG, "max_iter must be >= 1");
+  hkbe_t* h = new hkbe_t();
+  h->p = *p;
+  h->s = (cudaStream_t)stream;
+  Dev& d = h->d;
+  d.nt = p->nt; d.k = p->k; d.no = p->nao; d.n_inst = p->n_inst; d.xi = p->xi;
+  d.rho_mode = p->rho_mode; d.h = p->h; d.beta = p->beta; d.r = 0; d.model = 0;
+  d.ntri = (long long)p->nt * (p->nt + 1) / 2;
+  hk::Weights w;
+  hk::weights_build(p->k, &w);
+  d.w.k = w.k;
+  std::memcpy(d.w.a, w.a, sizeof(w.a));
+  std::memcpy(d.w.omega, w.omega, sizeof(w.omega));
+  std::memcpy(d.w.D, w.D, sizeof(w.D));
+  std::memcpy(d.w.I0, w.I0, sizeof(w.I0));
+  const size_t tri = (size_t)d.n_inst * d.ntri * d.no * d.no;
+  int rc = HKBE_OK;
+  if ((rc = dalloc(h, &d.GR, tri)) || (rc = dalloc(h, &d.GL, tri)) || (rc = dalloc(h, &d.SR, tri)) ||
+      (rc = dalloc(h, &d.SL, tri)) ||
+      (rc = dalloc(h, &d.eps, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
+      (rc = dalloc(h, &d.mpar, (size_t)d.n_inst * hk::MP)) ||
+      (rc = dalloc(h, &d.qsrc, (size_t)d.n_inst * d.nt * d.no * d.no)) ||
+      (rc = dalloc(h, &d.x0, (size_t)d.n_inst * d.no * d.no)) || (rc = dalloc(h, &d.err, (size_t)d.n_inst)) ||
+      (rc = dalloc(h, &d.active, (size_t)d.n_inst)) || (rc = dalloc(h, &h->any_dev, 1))) {
+    g_create_error = h->err;
+    hkbe_destroy(h);
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->s);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e);
+    hkbe_destroy(h);
+    return HKBE_ERR_CUDA;
+  }
+  *out = h;
+  return HKBE_OK;
+}
+
+int hkbe_destroy(hkbe_t* h) {
+  if (!h) return HKBE_OK;
+  if (h->s) cudaStreamSynchronize(h->s);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+  return HKBE_OK;
+}
+
+int hkbe_set_dlr(hkbe_t* h, int r, const double* tau, const double* omega) {
+  if (!h || !tau || !omega) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (h->have_dlr) return fail(h, HKBE_ERR_ARG, "DLR grid already set");
+  if (r < 1 || r > 128) return fail(h, HKBE_ERR_ARG, "r must be in 1..128");
+  for (int i = 0; i < r; ++i)
+    if (!(tau[i] > 0.0 && tau[i] < h->p.beta)) return fail(h, HKBE_ERR_ARG, "DLR nodes must lie in (0, beta)");
+  h->tau.assign(tau, tau + r);
+  h->om.assign(omega, omega + r);
+  if (!hk::dlr_build(r, tau, omega, h->p.beta, h->p.xi, &h->dm))
+    return fail(h, HKBE_ERR_ARG, "singular DLR kernel matrix");
+  Dev& d = h->d;
+  d.r = r;
+  const size_t n2 = (size_t)d.no * d.no;
+  int rc;
+  if ((rc = dalloc(h, &d.tau, r)) || (rc = dalloc(h, &d.e0, r)) || (rc = dalloc(h, &d.ebeta, r)) ||
+      (rc = dalloc(h, &d.rev, (size_t)r * r)) || (rc = dalloc(h, &d.q, (size_t)r * r)) ||
+      (rc = dalloc(h, &d.GTV, (size_t)d.n_inst * d.nt * r * n2)) ||
+      (rc = dalloc(h, &d.STV, (size_t)d.n_inst * d.nt * r * n2)) ||
+      (rc = dalloc(h, &d.gm, (size_t)d.n_inst * r * n2)) ||
+      (rc = dalloc(h, &d.wconv, (size_t)d.n_inst * r * r * n2)) ||
+      (rc = dalloc(h, &d.vvec, (size_t)d.n_inst * r * n2)))
+    return rc;
+  HK_CUDA(h, cudaMemcpyAsync(d.tau, tau, r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.e0, h->dm.e0.data(), r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.ebeta, h->dm.ebeta.data(), r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.rev, h->dm.rev.data(), r * r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.q, h->dm.q.data(), r * r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->have_dlr = true;
+  return HKBE_OK;
+}
+
+int hkbe_set_matsubara(hkbe_t* h, const double* gm) {
+  if (!h || !gm) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (!h->have_dlr) return fail(h, HKBE_ERR_ARG, "hkbe_set_dlr must precede hkbe_set_matsubara");
+  Dev& d = h->d;
+  const int r = d.r, n2 = no2(h);
+  const size_t cnt = (size_t)d.n_inst * r * n2 * 2;
+  h->gm_host.assign(gm, gm + cnt);
+  // W[a][i] = sum_c phi[a][c][i] G^M(tau_c)   (convolution tensor of Eq. KBET)
+  std::vector<double> W((size_t)d.n_inst * r * r * n2 * 2, 0.0);
+  for (int n = 0; n < d.n_inst; ++n)
+    for (int a = 0; a < r; ++a)
+      for (int i = 0; i < r; ++i) {
+        double* w = &W[(((size_t)n * r + a) * r + i) * n2 * 2];
+        for (int c = 0; c < r; ++c) {
+          const double ph = h->dm.phi[((size_t)a * r + c) * r + i];
+          const double* g = gm + ((size_t)n * r + c) * n2 * 2;
+          for (int q = 0; q < 2 * n2; ++q) w[q] += ph * g[q];
+        }
+      }
+  HK_CUDA(h, cudaMemcpyAsync(d.gm, gm, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.wconv, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->have_gm = true;
+  return HKBE_OK;
+}
+
+int hkbe_set_hamiltonian(hkbe_t* h, const double* eps) {
+  if (!h || !eps) return fail(h, HKBE_ERR_ARG, "null argument");
+  Dev& d = h->d;
+  const size_t cnt = (size_t)d.n_inst * (d.nt + 1) * no2(h) * 2;
+  for (size_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(eps[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in eps");
+  h->eps_host.assign(eps, eps + cnt);
+  HK_CUDA(h, cudaMemcpyAsync(d.eps, eps, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->have_eps = true;
+  return HKBE_OK;
+}
+
+int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  Dev& d = h->d;
+  const int no = d.no;
+  std::vector<double> mp((size_t)d.n_inst * hk::MP, 0.0);
+  if (model == HKBE_MODEL_NONE) {
+    h->self_consistent = false;
+  } else if (model == HKBE_MODEL_BETHE) {
+    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "BETHE needs params[0] = v");
+    for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = params[(size_t)n * nparams];
+    h->self_consistent = true;
+  } else if (model == HKBE_MODEL_BATH) {
+    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "BATH needs parameters");
+    for (int n = 0; n < d.n_inst; ++n) {
+      const double* q = params + (size_t)n * nparams;
+      const int nb = (int)q[0];
+      if (nb < 1 || nb > 4 || nparams != 1 + nb + 2 * no * nb)
+        return fail(h, HKBE_ERR_ARG, "BATH params must be [nb, eps_b[nb], V[nao][nb] complex]");
+      std::memcpy(&mp[(size_t)n * hk::MP], q, nparams * sizeof(double));
+    }
+    h->self_consistent = false;
+  } else {
+    return fail(h, HKBE_ERR_ARG, "unknown model");
+  }
+  d.model = model;
+  HK_CUDA(h, cudaMemcpyAsync(d.mpar, mp.data(), mp.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->have_model = true;
+  return HKBE_OK;
+}
+
+// Mean-field guess of the start square (Sec. 3.3, green_from_H):
+// G^R = -i e^{-i e (t-t')}, G^<(t,t') = i e^{-i e t} rho e^{i e t'},
+// G^tv = -xi i e^{-i e t} rho e^{e tau}, e = eps(0_|), rho = -G^M(beta^-).
+static int hf_guess(hkbe_t* h) {
+  Dev& d = h->d;
+  const int no = d.no, n2 = no * no, k = d.k, r = d.r;
+  const double hh = d.h;
+  std::vector<double> gr((size_t)(k + 1) * (k + 2) / 2 * n2 * 2), gl(gr.size()), gtv((size_t)(k + 1) * r * n2 * 2);
+  for (int n = 0; n < d.n_inst; ++n) {
+    zc e[16], U[16];
+    double E[4];
+    const double* ep = &h->eps_host[(size_t)n * (d.nt + 1) * n2 * 2];
+    for (int q = 0; q < n2; ++q) e[q] = zc(ep[2 * q], ep[2 * q + 1]);
+    hk::herm_eig(no, e, E, U);
+    zc rho[16];
+    for (int q = 0; q < n2; ++q) {
+      zc s = 0;
+      for (int c = 0; c < r; ++c) {
+        const double* g = &h->gm_host[(((size_t)n * r + c) * n2 + q) * 2];
+        s += h->dm.ebeta[c] * zc(g[0], g[1]);
+      }
+      rho[q] = -s;
+    }
+    auto fun = [&](auto f, zc* out) {  // U diag(f(E)) U^dagger
+      for (int x = 0; x < no; ++x)
+        for (int y = 0; y < no; ++y) {
+          zc s = 0;
+          for (int a = 0; a < no; ++a) s += U[x * no + a] * f(E[a]) * std::conj(U[y * no + a]);
+          out[x * no + y] = s;
+        }
+    };
+    auto mm = [&](const zc* A, const zc* B, zc* C) {
+      for (int x = 0; x < no; ++x)
+        for (int y = 0; y < no; ++y) {
+          zc s = 0;
+          for (int a = 0; a < no; ++a) s += A[x * no + a] * B[a * no + y];
+          C[x * no + y] = s;
+        }
+    };
+    size_t off = 0;
+    for (int t = 0; t <= k; ++t)
+      for (int tp = 0; tp <= t; ++tp, ++off) {
+        zc A[16], B[16], C[16], D[16];
+        fun([&](double ee) { return zc(0, -1) * std::exp(zc(0, -ee * (t - tp) * hh)); }, A);
+        // GL(t, tp) = G^<(tp, t) = i e^{-i e tp} rho e^{i e t}
+        fun([&](double ee) { return std::exp(zc(0, -ee * tp * hh)); }, B);
+        fun([&](double ee) { return std::exp(zc(0, ee * t * hh)); }, C);
+        mm(B, rho, D);
+        mm(D, C, B);
+        for (int q = 0; q < n2; ++q) {
+          gr[(off * n2 + q) * 2] = A[q].real(); gr[(off * n2 + q) * 2 + 1] = A[q].imag();
+          zc v = zc(0, 1) * B[q];
+          gl[(off * n2 + q) * 2] = v.real(); gl[(off * n2 + q) * 2 + 1] = v.imag();
+        }
+      }
+    for (int t = 0; t <= k; ++t)
+      for (int i = 0; i < r; ++i) {
+        zc B[16], C[16], D[16];
+        fun([&](double ee) { return std::exp(zc(0, -ee * t * hh)); }, B);
+        fun([&](double ee) { return std::exp(ee * h->tau[i]); }, C);
+        mm(B, rho, D);
+        mm(D, C, B);
+        for (int q = 0; q < n2; ++q) {
+          zc v = zc(0, -(double)d.xi) * B[q];
+          gtv[(((size_t)t * r + i) * n2 + q) * 2] = v.real();
+          gtv[(((size_t)t * r + i) * n2 + q) * 2 + 1] = v.imag();
+        }
+      }
+    const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2;
+    HK_CUDA(h, cudaMemcpyAsync(d.GR + (size_t)n * d.ntri * n2, gr.data(), sq * sizeof(double2), cudaMemcpyHostToDevice, h->s));
+    HK_CUDA(h, cudaMemcpyAsync(d.GL + (size_t)n * d.ntri * n2, gl.data(), sq * sizeof(double2), cudaMemcpyHostToDevice, h->s));
+    HK_CUDA(h, cudaMemcpyAsync(d.GTV + (size_t)n * d.nt * r * n2, gtv.data(), (size_t)(k + 1) * r * n2 * sizeof(double2),
+                               cudaMemcpyHostToDevice, h->s));
+    HK_CUDA(h, cudaStreamSynchronize(h->s));
+  }
+  return HKBE_OK;
+}
+
+static int check_ready(hkbe_t* h) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (!h->have_dlr || !h->have_gm || !h->have_eps || !h->have_model)
+    return fail(h, HKBE_ERR_ARG, "set_dlr, set_matsubara, set_hamiltonian and set_model must precede stepping");
+  return HKBE_OK;
+}
+
+}  // extern "C"
+
+// Run the iteration loop of one bootstrap or one time step; `pass` launches
+// one iteration.  Records per-instance iteration counts and final errors.
+template <typename F>
+static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, double* errs, bool* any_failed) {
+  Dev& d = h->d;
+  const int N = d.n_inst;
+  std::vector<int> act(N, 1), it_of(N, 0);
+  std::vector<double> err(N, 0.0);
+  HK_CUDA(h, cudaMemcpyAsync(d.active, act.data(), N * sizeof(int), cudaMemcpyHostToDevice, h->s));
+  const double tol_eff = h->self_consistent ? tol : INFINITY;
+  const int min_iter = h->self_consistent ? 1 : 2;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    HK_CUDA(h, cudaMemsetAsync(d.err, 0, N * sizeof(double), h->s));
+    HK_CUDA(h, cudaMemsetAsync(h->any_dev, 0, sizeof(int), h->s));
+    HK_CUDA(h, pass());
+    HK_CUDA(h, hk::launch_set_active(d, tol_eff, it, min_iter, h->any_dev, h->s));
+    int any = 0;
+    HK_CUDA(h, cudaMemcpyAsync(err.data(), d.err, N * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaMemcpyAsync(&any, h->any_dev, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaStreamSynchronize(h->s));
+    for (int n = 0; n < N; ++n)
+      if (act[n]) {
+        it_of[n] = it;
+        if (errs) errs[n] = err[n];
+        if (!std::isfinite(err[n])) return fail(h, HKBE_ERR_NAN, "non-finite value during the self-consistency loop");
+      }
+    HK_CUDA(h, cudaMemcpyAsync(act.data(), d.active, N * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaStreamSynchronize(h->s));
+    if (!any) break;
+  }
+  *any_failed = false;
+  for (int n = 0; n < N; ++n) {
+    if (iters) iters[n] = it_of[n];
+    if (act[n] && h->self_consistent) *any_failed = true;
+  }
+  return HKBE_OK;
+}
+
+extern "C" {
+
+int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* err) {
+  int rc = check_ready(h);
+  if (rc) return rc;
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "bootstrap already done");
+  if (max_iter < 1) return fail(h, HKBE_ERR_ARG, "max_iter must be >= 1");
+  if ((rc = hf_guess(h))) return rc;
+  Dev& d = h->d;
+  bool failed = false;
+  rc = iterate(h, max_iter, tol, [&]() { return hk::launch_boot(d, h->s); }, iters, err, &failed);
+  if (rc) return rc;
+  // Sigma of the converged square (all instances)
+  std::vector<int> ones(d.n_inst, 1);
+  HK_CUDA(h, cudaMemcpyAsync(d.active, ones.data(), d.n_inst * sizeof(int), cudaMemcpyHostToDevice, h->s));
+  for (int t = 0; t <= d.k; ++t) HK_CUDA(h, hk::launch_sigma(d, t, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->cur = d.k;
+  if (failed) return fail(h, HKBE_ERR_NOCONV, "bootstrap did not converge");
+  return HKBE_OK;
+}
+
+int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
+  int rc = check_ready(h);
+  if (rc) return rc;
+  if (h->cur < 0) return fail(h, HKBE_ERR_ARG, "hkbe_bootstrap must precede hkbe_step");
+  if (n_steps < 0) return fail(h, HKBE_ERR_ARG, "n_steps must be >= 0");
+  Dev& d = h->d;
+  if (h->cur + n_steps > d.nt - 1) return fail(h, HKBE_ERR_RANGE, "stepping past nt - 1");
+  const int N = d.n_inst;
+  bool any_failed = false;
+  for (int st = 0; st < n_steps; ++st) {
+    const int T = h->cur + 1;
+    HK_CUDA(h, hk::launch_extrapolate(d, T, h->s));
+    bool failed = false;
+    rc = iterate(h, h->p.max_iter, h->p.tol,
+                 [&]() -> cudaError_t {
+                   cudaError_t e;
+                   if ((e = hk::launch_sigma(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = hk::launch_ret(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = hk::launch_mixed(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = hk::launch_vt(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = hk::launch_src(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = hk::launch_les(d, T, h->s)) != cudaSuccess) return e;
+                   if (d.rho_mode == 1 && (e = hk::launch_rho(d, T, h->s)) != cudaSuccess) return e;
+                   return cudaSuccess;
+                 },
+                 iters ? iters + (size_t)st * N : nullptr, err ? err + (size_t)st * N : nullptr, &failed);
+    if (rc) return rc;
+    any_failed |= failed;
+    h->cur = T;
+  }
+  if (any_failed) return fail(h, HKBE_ERR_NOCONV, "self-consistency did not converge within max_iter");
+  return HKBE_OK;
+}
+
+int hkbe_current_step(const hkbe_t* h, int32_t* T) {
+  if (!h || !T) return HKBE_ERR_ARG;
+  *T = h->cur;
+  return HKBE_OK;
+}
+
+static int copy_el(hkbe_t* h, const double2* base, int inst, int T, int t, double* out) {
+  const int n2 = no2(h);
+  const double2* src = base + ((size_t)inst * h->d.ntri + (size_t)T * (T + 1) / 2 + t) * n2;
+  HK_CUDA(h, cudaMemcpyAsync(out, src, n2 * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_get_ret(hkbe_t* h, int inst, int t, int tp, double* out) {
+  if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
+  if (tp < 0 || tp > t || t > h->cur) return fail(h, HKBE_ERR_RANGE, "need 0 <= t' <= t <= current step");
+  return copy_el(h, h->d.GR, inst, t, tp, out);
+}
+
+int hkbe_get_les(hkbe_t* h, int inst, int t, int tp, double* out) {
+  if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
+  if (t < 0 || tp < 0 || t > h->cur || tp > h->cur) return fail(h, HKBE_ERR_RANGE, "times must be in 0..current step");
+  if (t <= tp) return copy_el(h, h->d.GL, inst, tp, t, out);
+  const int no = h->d.no;
+  std::vector<double> tmp(2 * no * no);
+  int rc = copy_el(h, h->d.GL, inst, t, tp, tmp.data());
+  if (rc) return rc;
+  for (int x = 0; x < no; ++x)
+    for (int y = 0; y < no; ++y) {
+      out[2 * (x * no + y)] = -tmp[2 * (y * no + x)];
+      out[2 * (x * no + y) + 1] = tmp[2 * (y * no + x) + 1];
+    }
+  return HKBE_OK;
+}
+
+int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out) {
+  if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (!h->have_dlr) return fail(h, HKBE_ERR_ARG, "no DLR grid");
+  if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
+  if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
+  const size_t cnt = (size_t)h->d.r * no2(h);
+  HK_CUDA(h, cudaMemcpyAsync(out, h->d.GTV + ((size_t)inst * h->d.nt + t) * cnt, cnt * sizeof(double2),
+                             cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
+  if (T < 0 || T > h->cur) return fail(h, HKBE_ERR_RANGE, "T must be in 0..current step");
+  const size_t cnt = (size_t)(T + 1) * no2(h);
+  const size_t off = ((size_t)inst * h->d.ntri + (size_t)T * (T + 1) / 2) * no2(h);
+  if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, h->d.GR + off, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, h->d.GL + off, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_get_density(hkbe_t* h, double* rho) {
+  if (!h || !rho) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (h->cur < 0) return fail(h, HKBE_ERR_RANGE, "nothing computed yet");
+  const int n2 = no2(h), T = h->cur;
+  std::vector<double> tmp(2 * n2);
+  for (int n = 0; n < h->d.n_inst; ++n)
+    for (int t = 0; t <= T; ++t) {
+      int rc = copy_el(h, h->d.GL, n, t, t, tmp.data());
+      if (rc) return rc;
+      double* o = rho + (((size_t)n * (T + 1) + t) * n2) * 2;
+      for (int q = 0; q < n2; ++q) {  // rho = xi i G^<
+        const double re = tmp[2 * q], im = tmp[2 * q + 1];
+        o[2 * q] = -h->p.xi * im;
+        o[2 * q + 1] = h->p.xi * re;
+      }
+    }
+  return HKBE_OK;
+}
+
+int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes) {
+  if (!h || !device_bytes) return HKBE_ERR_ARG;
+  *device_bytes = h->bytes;
+  return HKBE_OK;
+}
+
+int hkbe_weights(int k, double* a, double* omega, double* D, double* I0) {
+  if (k < 1 || k > 5) return HKBE_ERR_ARG;
+  hk::Weights w;
+  hk::weights_build(k, &w);
+  for (int i = 0; i <= k; ++i) {
+    if (a) a[i] = w.a[i];
+    if (omega) omega[i] = w.omega[i];
+    for (int j = 0; j <= k; ++j) {
+      if (D) D[i * (k + 1) + j] = w.D[i][j];
+      if (I0) I0[i * (k + 1) + j] = w.I0[i][j];
+    }
+  }
+  return HKBE_OK;
+}
+
+int hkbe_rule(int k, int n, double* w) {
+  if (k < 1 || k > 5 || n < 0 || !w) return HKBE_ERR_ARG;
+  hk::Weights W;
+  hk::weights_build(k, &W);
+  const int L = (n > k ? n : k) + 1;
+  for (int l = 0; l < L; ++l) w[l] = hk::rule_weight(W, n, l);
+  return HKBE_OK;
+}
+
+int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta, int xi, double* e0,
+                      double* ebeta, double* rev, double* q, double* phi) {
+  if (r < 1 || r > 128 || !tau || !omega || !(beta > 0) || (xi != -1 && xi != 1)) return HKBE_ERR_ARG;
+  hk::DLRMats m;
+  if (!hk::dlr_build(r, tau, omega, beta, xi, &m)) return HKBE_ERR_ARG;
+  if (e0) std::memcpy(e0, m.e0.data(), r * sizeof(double));
+  if (ebeta) std::memcpy(ebeta, m.ebeta.data(), r * sizeof(double));
+  if (rev) std::memcpy(rev, m.rev.data(), (size_t)r * r * sizeof(double));
+  if (q) std::memcpy(q, m.q.data(), (size_t)r * r * sizeof(double));
+  if (phi) std::memcpy(phi, m.phi.data(), (size_t)r * r * r * sizeof(double));
+  return HKBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Shared device/host helpers: complex arithmetic on double2/float2 and small
+// N_o x N_o matrix algebra kept in registers (N_o <= 4).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HD __host__ __device__ __forceinline__
+
+namespace hk {
+
+template <typename R> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+
+template <typename R>
+struct cx {
+  R re, im;
+  cx() = default;
+  HD cx(R r, R i = 0) : re(r), im(i) {}
+  HD cx operator+(const cx& o) const { return cx(re + o.re, im + o.im); }
+  HD cx operator-(const cx& o) const { return cx(re - o.re, im - o.im); }
+  HD cx operator-() const { return cx(-re, -im); }
+  HD cx operator*(const cx& o) const { return cx(re * o.re - im * o.im, re * o.im + im * o.re); }
+  HD cx operator*(R s) const { return cx(re * s, im * s); }
+  HD cx& operator+=(const cx& o) { re += o.re; im += o.im; return *this; }
+  HD cx& operator-=(const cx& o) { re -= o.re; im -= o.im; return *this; }
+  HD cx conj() const { return cx(re, -im); }
+  HD R abs2() const { return re * re + im * im; }
+};
+
+using zd = cx<double>;
+using zf = cx<float>;
+
+template <typename R> HD cx<R> cfma(const cx<R>& a, const cx<R>& b, const cx<R>& c) {
+  // a*b + c
+  return cx<R>(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
+}
+
+HD zd ld(const double2* p) { double2 v = *p; return zd(v.x, v.y); }
+HD void st(double2* p, const zd& z) { *p = make_double2(z.re, z.im); }
+
+HD zd cdiv(const zd& a, const zd& b) {
+  double d = b.re * b.re + b.im * b.im;
+  return zd((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+
+// ---- N x N matrices in registers -----------------------------------------
+template <int N>
+struct M {
+  zd a[N][N];
+  HD M() {}
+  HD static M zero() { M m; for (int i = 0; i < N; ++i) for (int j = 0; j < N; ++j) m.a[i][j] = zd(); return m; }
+  HD static M eye(zd d) { M m = zero(); for (int i = 0; i < N; ++i) m.a[i][i] = d; return m; }
+  HD zd& operator()(int i, int j) { return a[i][j]; }
+  HD const zd& operator()(int i, int j) const { return a[i][j]; }
+};
+
+template <int N> HD M<N> load(const double2* p) {
+  M<N> m;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) m.a[i][j] = ld(p + i * N + j);
+  return m;
+}
+template <int N> HD void store(double2* p, const M<N>& m) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) st(p + i * N + j, m.a[i][j]);
+}
+template <int N> HD M<N> operator+(const M<N>& x, const M<N>& y) {
+  M<N> m;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) m.a[i][j] = x.a[i][j] + y.a[i][j];
+  return m;
+}
+template <int N> HD M<N> operator-(const M<N>& x, const M<N>& y) {
+  M<N> m;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) m.a[i][j] = x.a[i][j] - y.a[i][j];
+  return m;
+}
+template <int N> HD M<N> scale(const M<N>& x, zd s) {
+  M<N> m;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) m.a[i][j] = x.a[i][j] * s;
+  return m;
+}
+template <int N> HD M<N> mul(const M<N>& x, const M<N>& y) {
+  M<N> m = M<N>::zero();
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+#pragma unroll
+      for (int j = 0; j < N; ++j) m.a[i][j] = cfma(x.a[i][l], y.a[l][j], m.a[i][j]);
+  return m;
+}
+// acc += s * x * y
+template <int N> HD void mac(M<N>& acc, const M<N>& x, const M<N>& y, zd s) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      zd xs = x.a[i][l] * s;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.a[i][j] = cfma(xs, y.a[l][j], acc.a[i][j]);
+    }
+}
+template <int N> HD M<N> dag(const M<N>& x) {
+  M<N> m;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) m.a[i][j] = x.a[j][i].conj();
+  return m;
+}
+template <int N> HD double maxabs_diff(const M<N>& x, const M<N>& y) {
+  double e = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      zd d = x.a[i][j] - y.a[i][j];
+      e = fmax(e, sqrt(d.abs2()));
+    }
+  return e;
+}
+// Solve A X = B (left) by Gauss-Jordan with partial pivoting; A is copied.
+template <int N> HD M<N> solve_left(M<N> A, M<N> B) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    int p = c;
+    double best = A.a[c][c].abs2();
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      double v = A.a[r][c].abs2();
+      if (v > best) { best = v; p = r; }
+    }
+    if (p != c) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        zd t = A.a[c][j]; A.a[c][j] = A.a[p][j]; A.a[p][j] = t;
+        t = B.a[c][j]; B.a[c][j] = B.a[p][j]; B.a[p][j] = t;
+      }
+    }
+    zd inv = cdiv(zd(1.0), A.a[c][c]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) { A.a[c][j] = A.a[c][j] * inv; B.a[c][j] = B.a[c][j] * inv; }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      zd f = A.a[r][c];
+#pragma unroll
+      for (int j = 0; j < N; ++j) { A.a[r][j] -= f * A.a[c][j]; B.a[r][j] -= f * B.a[c][j]; }
+    }
+  }
+  return B;
+}
+// Solve X A = B (right): X = B A^-1  <=>  A^T X^T = B^T
+template <int N> HD M<N> solve_right(const M<N>& A, const M<N>& B) {
+  M<N> At, Bt;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) { At.a[i][j] = A.a[j][i]; Bt.a[i][j] = B.a[j][i]; }
+  M<N> Xt = solve_left<N>(At, Bt);
+  M<N> X;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) X.a[i][j] = Xt.a[j][i];
+  return X;
+}
+
+// ---- atomics ----------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // for non-negative doubles the IEEE bit pattern orders like unsigned ints
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace hk

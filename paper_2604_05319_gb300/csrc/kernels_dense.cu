@@ -1,0 +1,1115 @@
+// Dense FP64 kernels of one Kadanoff-Baym time step (Eqs. KBER, KBET, KBEL,
+// Appendix A weights) and of the bootstrap square (Sec. 3.3).
+//
+// Storage is lower-triangular per instance: element (T, t), t <= T, of the
+// N_o x N_o matrices lives at ((n*ntri + T(T+1)/2 + t) * N_o^2).  GL(T, t)
+// holds G^<(t, T) (the paper's G^<_{t1 t2} = G^<(t2, t1)).
+//
+// Per self-consistency iteration at step T the launches are
+//   k_sigma  Sigma^R(T, .), Sigma^<(., T), Sigma^tv(T, .) from the current G
+//   k_ret    retarded row, unknown y_s = G^R(T, T-s) (Eq. KBER), one CTA per
+//            (instance, orbital row); start block s <= k solved together, then
+//            chunks of 32 points: far-field history sums in parallel over the
+//            CTA, near field + point solve sequentially in one warp
+//   k_mixed  G^tv(T, tau_i) (Eq. KBET), one warp per (instance, node)
+//   k_vt     v_a = sum_b Q_ab G^vt(tau_b, T) and x_0 = -[G^tv(T, 0)]^dagger
+//   k_src    lesser source q(t), t = 0..T, one warp per (instance, t)
+//   k_les    lesser column x_t = G^<(t, T) (Eq. KBEL), one CTA per
+//            (instance, orbital column), same chunked structure as k_ret
+//   k_rho    diagonal density-matrix update (Sec. 3.3), when selected
+// Each kernel folds max |new - old| of what it writes into err[instance].
+#include "common.cuh"
+#include "state.h"
+
+namespace hk {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ long long tri(int T) { return (long long)T * (T + 1) / 2; }
+
+template <int NO>
+__device__ __forceinline__ double2* el(double2* base, const Dev& d, int n, int T, int t) {
+  return base + ((long long)n * d.ntri + tri(T) + t) * (NO * NO);
+}
+template <int NO>
+__device__ __forceinline__ double2* tv(double2* base, const Dev& d, int n, int T, int i) {
+  return base + (((long long)n * d.nt + T) * d.r + i) * (NO * NO);
+}
+template <int NO>
+__device__ __forceinline__ double2* epsp(const Dev& d, int n, int t) {  // eps(t), t >= -1
+  return d.eps + ((long long)n * (d.nt + 1) + (t + 1)) * (NO * NO);
+}
+
+__device__ double rule_w(const DevW& w, int n, int l) {
+  const int k = w.k;
+  if (n <= 0) return 0.0;
+  if (n <= k) return (l >= 0 && l <= k) ? w.I0[n][l] : 0.0;
+  if (n < 2 * k + 1) {
+    double s = 0.0;
+    if (l >= 0 && l <= k) s += w.I0[n - k][l];
+    if (l >= n - k && l <= n) s += w.I0[k][l - (n - k)];
+    return s;
+  }
+  if (l < 0 || l > n) return 0.0;
+  if (l <= k) return w.omega[l];
+  if (l >= n - k) return w.omega[n - l];
+  return 1.0;
+}
+
+__device__ __forceinline__ zd wshfl(zd v, int off) {
+  return zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));
+}
+template <int L>
+__device__ __forceinline__ void warp_sum(zd (&v)[L]) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] += wshfl(v[i], off);
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// Sigma^R(a, b) continued above the diagonal: -[Sigma^R(b, a)]^dagger for a < b.
+template <int NO>
+__device__ __forceinline__ zd srx(const Dev& d, int n, int a, int b, int x, int y) {
+  if (a >= b) return ld(el<NO>(d.SR, d, n, a, b) + x * NO + y);
+  return -ld(el<NO>(d.SR, d, n, b, a) + y * NO + x).conj();
+}
+// Sigma^<(t, l) anywhere (Eq. GLantiHerm)
+template <int NO>
+__device__ __forceinline__ zd sless(const Dev& d, int n, int t, int l, int x, int y) {
+  if (t <= l) return ld(el<NO>(d.SL, d, n, l, t) + x * NO + y);
+  return -ld(el<NO>(d.SL, d, n, t, l) + y * NO + x).conj();
+}
+
+// ---------------------------------------------------------------------------
+// Warp-parallel dense solve A X = B (n <= 32, nrhs <= 32), A and B in shared
+// memory, LU with partial pivoting; lane r owns row r during elimination.
+// With nrhs = 0 it only factors (L below the diagonal, row swaps in piv).
+// ---------------------------------------------------------------------------
+__device__ void warp_lu_solve(int n, zd* A, zd* B, int nrhs, int* piv) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < n; ++c) {
+    double v = (lane >= c && lane < n) ? A[lane * n + c].abs2() : -1.0;
+    int p = lane;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      double v2 = __shfl_xor_sync(FULL, v, off);
+      int p2 = __shfl_xor_sync(FULL, p, off);
+      if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+    }
+    if (piv && lane == 0) piv[c] = p;
+    if (p != c) {
+      for (int j = lane; j < n; j += 32) { zd t = A[c * n + j]; A[c * n + j] = A[p * n + j]; A[p * n + j] = t; }
+      for (int j = lane; j < nrhs; j += 32) { zd t = B[c * nrhs + j]; B[c * nrhs + j] = B[p * nrhs + j]; B[p * nrhs + j] = t; }
+    }
+    __syncwarp();
+    if (lane > c && lane < n) {
+      zd f = cdiv(A[lane * n + c], A[c * n + c]);
+      A[lane * n + c] = f;
+      for (int j = c + 1; j < n; ++j) A[lane * n + j] -= f * A[c * n + j];
+      for (int j = 0; j < nrhs; ++j) B[lane * nrhs + j] -= f * B[c * nrhs + j];
+    }
+    __syncwarp();
+  }
+  for (int j = lane; j < nrhs; j += 32)
+    for (int c = n - 1; c >= 0; --c) {
+      zd s = B[c * nrhs + j];
+      for (int m = c + 1; m < n; ++m) s -= A[c * n + m] * B[m * nrhs + j];
+      B[c * nrhs + j] = cdiv(s, A[c * n + c]);
+    }
+  __syncwarp();
+}
+// Solve with a factor from warp_lu_solve(nrhs = 0) for one right-hand side b.
+__device__ void lu_apply(int n, const zd* A, const int* piv, zd* b) {
+  for (int c = 0; c < n; ++c)
+    if (piv[c] != c) { zd t = b[c]; b[c] = b[piv[c]]; b[piv[c]] = t; }
+  for (int c = 0; c < n; ++c)
+    for (int r = c + 1; r < n; ++r) b[r] -= A[r * n + c] * b[c];
+  for (int c = n - 1; c >= 0; --c) {
+    zd s = b[c];
+    for (int m = c + 1; m < n; ++m) s -= A[c * n + m] * b[m];
+    b[c] = cdiv(s, A[c * n + c]);
+  }
+}
+
+// small vector solves: y M = r (row vector) and M x = r (column vector)
+template <int NO>
+__device__ void solve_row(const M<NO>& Mm, const zd* r, zd* y) {
+  M<NO> B = M<NO>::zero();
+#pragma unroll
+  for (int j = 0; j < NO; ++j) B.a[0][j] = r[j];
+  M<NO> X = solve_right<NO>(Mm, B);
+#pragma unroll
+  for (int j = 0; j < NO; ++j) y[j] = X.a[0][j];
+}
+template <int NO>
+__device__ void solve_col(const M<NO>& Mm, const zd* r, zd* x) {
+  M<NO> B = M<NO>::zero();
+#pragma unroll
+  for (int j = 0; j < NO; ++j) B.a[j][0] = r[j];
+  M<NO> X = solve_left<NO>(Mm, B);
+#pragma unroll
+  for (int j = 0; j < NO; ++j) x[j] = X.a[j][0];
+}
+
+// ---------------------------------------------------------------------------
+// Self-energy functionals (Sec. 3 / Eq. Hybrid; bath level model)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fermi(double e, double beta) { return 0.5 * (1.0 - tanh(0.5 * beta * e)); }
+
+template <int NO>
+__device__ void bath_sigma(const double* mp, zd g0, double eb_dt_sign, int which, const Dev& d,
+                           double tphase, double tauv, zd* out) {
+  // which: 0 retarded (-i e^{-i eb dt}), 1 lesser (i n_b e^{-i eb dt}),
+  //        2 mixed (-xi i n_b e^{-i eb t} e^{eb tau});  dt passed in tphase
+  const int nb = (int)mp[0];
+  for (int x = 0; x < NO; ++x)
+    for (int y = 0; y < NO; ++y) out[x * NO + y] = zd();
+  for (int b = 0; b < nb; ++b) {
+    const double eb = mp[1 + b];
+    zd g;
+    double s, c;
+    sincos(-eb * tphase, &s, &c);
+    zd ph(c, s);
+    if (which == 0) g = zd(0, -1) * ph;
+    else if (which == 1) g = zd(0, fermi(eb, d.beta)) * ph;
+    else g = zd(0, -(double)d.xi * fermi(eb, d.beta)) * ph * exp(eb * tauv);
+    const double* V = mp + 1 + nb;  // V[x][b] interleaved
+    for (int x = 0; x < NO; ++x) {
+      zd vx(V[2 * (x * nb + b)], V[2 * (x * nb + b) + 1]);
+      for (int y = 0; y < NO; ++y) {
+        zd vy(V[2 * (y * nb + b)], V[2 * (y * nb + b) + 1]);
+        out[x * NO + y] += vx * g * vy.conj();
+      }
+    }
+  }
+  (void)g0; (void)eb_dt_sign;
+}
+
+template <int NO>
+__global__ void k_sigma(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y;
+  if (!d.active[n]) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = 2 * (T + 1) + d.r;
+  if (idx >= total) return;
+  const double* mp = d.mpar + (long long)n * MP;
+  double2 *src, *dst;
+  int which;
+  double tph = 0.0, tauv = 0.0;
+  if (idx <= T) {
+    src = el<NO>(d.GR, d, n, T, idx); dst = el<NO>(d.SR, d, n, T, idx);
+    which = 0; tph = (T - idx) * d.h;
+  } else if (idx <= 2 * T + 1) {
+    const int t = idx - (T + 1);
+    src = el<NO>(d.GL, d, n, T, t); dst = el<NO>(d.SL, d, n, T, t);
+    which = 1; tph = (t - T) * d.h;
+  } else {
+    const int i = idx - 2 * (T + 1);
+    src = tv<NO>(d.GTV, d, n, T, i); dst = tv<NO>(d.STV, d, n, T, i);
+    which = 2; tph = T * d.h; tauv = d.tau[i];
+  }
+  if (d.model == 1) {  // Bethe: Sigma = v^2 G
+    const double v2 = mp[0] * mp[0];
+#pragma unroll
+    for (int e = 0; e < NO2; ++e) st(dst + e, ld(src + e) * v2);
+  } else if (d.model == 2) {
+    zd out[NO2];
+    bath_sigma<NO>(mp, zd(), 0.0, which, d, tph, tauv, out);
+#pragma unroll
+    for (int e = 0; e < NO2; ++e) st(dst + e, out[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < NO2; ++e) st(dst + e, zd());
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Extrapolated initial guess for step T (Sec. 3.4): degree-k polynomial along
+// the diagonal through the previous k+1 points, e_l = (-1)^l C(k+1, l+1).
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void k_extrap(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = d.k;
+  if (idx >= 2 * (T + 1) + d.r) return;
+  double e[6];
+  {
+    double c = 1.0;  // C(k+1, l+1) built incrementally
+    for (int l = 0; l <= k; ++l) {
+      c = (l == 0) ? (double)(k + 1) : c * (double)(k + 1 - l) / (double)(l + 1);
+      e[l] = (l & 1) ? -c : c;
+    }
+  }
+  zd acc[NO2];
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  double2* dst;
+  if (idx <= T) {
+    const int tp = idx;
+    dst = el<NO>(d.GR, d, n, T, tp);
+    if (tp == T) {
+      for (int x = 0; x < NO; ++x) acc[x * NO + x] = zd(0, -1);
+    } else if (tp >= k + 1 || tp == 0) {
+      for (int l = 0; l <= k; ++l) {
+        const double2* s = (tp == 0) ? el<NO>(d.GR, d, n, T - 1 - l, 0) : el<NO>(d.GR, d, n, T - 1 - l, tp - 1 - l);
+        for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
+      }
+    } else {
+      const double2* s = el<NO>(d.GR, d, n, T - 1, tp - 1);
+      for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
+    }
+  } else if (idx <= 2 * T + 1) {
+    const int t = idx - (T + 1);
+    dst = el<NO>(d.GL, d, n, T, t);
+    if (t >= k + 1 || t == 0) {
+      for (int l = 0; l <= k; ++l) {
+        const double2* s = (t == 0) ? el<NO>(d.GL, d, n, T - 1 - l, 0) : el<NO>(d.GL, d, n, T - 1 - l, t - 1 - l);
+        for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
+      }
+    } else {
+      const double2* s = el<NO>(d.GL, d, n, T - 1, t - 1);
+      for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
+    }
+  } else {
+    const int i = idx - 2 * (T + 1);
+    dst = tv<NO>(d.GTV, d, n, T, i);
+    for (int l = 0; l <= k; ++l) {
+      const double2* s = tv<NO>(d.GTV, d, n, T - 1 - l, i);
+      for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
+    }
+  }
+  for (int q = 0; q < NO2; ++q) st(dst + q, acc[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Retarded row, Eq. KBER: y_s = G^R(T, T-s), right-multiplying VIDE in s.
+// ---------------------------------------------------------------------------
+constexpr int CH = 32;     // chunk of the sequential sweeps
+constexpr int NWARP = 8;   // warps per sweep CTA
+
+template <int NO>
+__global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, irow = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd red[NWARP][CH][NO];
+  __shared__ zd ych[CH][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* rowp = el<NO>(d.GR, d, n, T, 0);  // G^R(T, t') at rowp + t' NO2
+  auto yptr = [&](int s) { return rowp + (long long)(T - s) * NO2 + irow * NO; };
+  double myerr = 0.0;
+  // ---- start block s = 1..k ----
+  const int ns = k * NO;
+  if (warp == 0) {
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;       // row (s, j), col (l, m)
+      const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
+      zd v = srx<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
+      if (m == j) v += zd(0, W.D[s][l] / h);
+      if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
+      sA[row * ns + col] = v;
+    }
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      // b_s[j] = -sum_m y0[m] C[0,s][m][j], y0 = -i e_irow  ->  i C[0,s][irow][j]
+      zd c = srx<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
+      if (irow == j) c += zd(0, W.D[s][0] / h);
+      sB[row] = zd(0, 1) * c;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, sB, 1, nullptr);
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      double2* p = yptr(s) + j;
+      zd old = ld(p);
+      st(p, sB[row]);
+      myerr = fmax(myerr, sqrt((sB[row] - old).abs2()));
+    }
+    if (lane == 0) {
+      double2* p = yptr(0);
+      for (int j = 0; j < NO; ++j) {
+        zd v = (j == irow) ? zd(0, -1) : zd();
+        myerr = fmax(myerr, sqrt((ld(p + j) - v).abs2()));
+        st(p + j, v);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- BDF region s = k+1..T in chunks ----
+  for (int s0 = k + 1; s0 <= T; s0 += CH) {
+    const int cn = min(CH, T + 1 - s0);
+    {  // far field: l < s0, lanes over s, warps over l
+      zd acc[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) acc[j] = zd();
+      const int s = s0 + lane;
+      if (lane < cn) {
+        for (int l = warp; l < s0; l += NWARP) {
+          const double wl = rule_w(W, s, l);
+          const double2* yl = yptr(l);
+          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ld(yl + m) * wl;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      zd far[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        far[j] = zd();
+        for (int w2 = 0; w2 < NWARP; ++w2) far[j] += red[w2][lane][j];
+        far[j] = far[j] * h;
+      }
+      for (int sl = 0; sl < cn; ++sl) {
+        const int s = s0 + sl;
+        zd part[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) part[j] = zd();
+        if (lane < sl) {  // near field, l in [s0, s)
+          const int l = s0 + lane;
+          const double wl = h * rule_w(W, s, l);
+          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ych[lane][m] * wl;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
+          }
+        }
+        if (lane >= 1 && lane <= k) {  // -(i/h) a_j y_{s-j}
+          const int sj = s - lane;
+          const zd c = zd(0, -W.a[lane] / h);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = (sj >= s0) ? ych[sj - s0][m] : ld(yptr(sj) + m);
+            part[m] += c * ym;
+          }
+        }
+        warp_sum<NO>(part);
+        if (lane == sl) {
+          zd rhs[NO], y[NO];
+#pragma unroll
+          for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
+          const double ws = h * rule_w(W, s, s);
+          const double2* sd = el<NO>(d.SR, d, n, T - s, T - s);
+          const double2* ep = epsp<NO>(d, n, T - s);
+          M<NO> Mm;
+#pragma unroll
+          for (int x = 0; x < NO; ++x)
+#pragma unroll
+            for (int y2 = 0; y2 < NO; ++y2)
+              Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
+          solve_row<NO>(Mm, rhs, y);
+          double2* p = yptr(s);
+#pragma unroll
+          for (int j = 0; j < NO; ++j) {
+            myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
+            st(p + j, y[j]);
+            ych[sl][j] = y[j];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  myerr = warp_max(myerr);
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed component at step T, Eq. KBET (one warp per (instance, node)).
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void k_mixed(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = gw / d.r, i = gw % d.r;
+  if (n >= d.n_inst || !d.active[n]) return;
+  const int k = d.k;
+  const double h = d.h;
+  const DevW& W = d.w;
+  zd acc[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  for (int l = lane; l < T; l += 32) {  // h sum_l w_l Sigma^R(T,l) G^tv(l, tau_i)
+    const double wl = h * rule_w(W, T, l);
+    M<NO> S = load<NO>(el<NO>(d.SR, d, n, T, l));
+    M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, l, i));
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int z = 0; z < NO; ++z) {
+        zd sx = S.a[x][z] * wl;
+#pragma unroll
+        for (int y = 0; y < NO; ++y) acc[x * NO + y] = cfma(sx, G.a[z][y], acc[x * NO + y]);
+      }
+  }
+  for (int a = lane; a < d.r; a += 32) {  // sum_a Sigma^tv(T, tau_a) W[a][i]
+    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, T, a));
+    M<NO> C = load<NO>(d.wconv + (((long long)n * d.r + a) * d.r + i) * NO2);
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, C, zd(1.0));
+  }
+  if (lane >= 1 && lane <= k) {
+    M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, T - lane, i));
+    const zd c(0, -W.a[lane] / h);
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) acc[q] += c * G.a[q / NO][q % NO];
+  }
+  warp_sum<NO2>(acc);
+  if (lane == 0) {
+    const double wt = h * rule_w(W, T, T);
+    M<NO> Mm, R;
+    const double2* sd = el<NO>(d.SR, d, n, T, T);
+    const double2* ep = epsp<NO>(d, n, T);
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int y = 0; y < NO; ++y) {
+        Mm.a[x][y] = (x == y ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y) - ld(sd + x * NO + y) * wt;
+        R.a[x][y] = acc[x * NO + y];
+      }
+    M<NO> X = solve_left<NO>(Mm, R);
+    double2* p = tv<NO>(d.GTV, d, n, T, i);
+    M<NO> old = load<NO>(p);
+    store<NO>(p, X);
+    atomic_max_nonneg(d.err + n, maxabs_diff<NO>(X, old));
+  }
+}
+
+// v_a = sum_b Q_ab G^vt(tau_b, T), G^vt(tau_b, T) = -xi [G^tv(T, beta - tau_b)]^dagger,
+// x_0 = -[G^tv(T, 0+)]^dagger.  One CTA per instance, thread per node.
+template <int NO>
+__global__ void k_vt(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  if (!d.active[n]) return;
+  extern __shared__ zd gvt[];  // [r][NO2]
+  const int r = d.r;
+  for (int b = threadIdx.x; b < r; b += blockDim.x) {
+    M<NO> acc = M<NO>::zero();
+    for (int c = 0; c < r; ++c) {
+      M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, T, c));
+      const double rv = d.rev[b * r + c];
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) acc.a[q / NO][q % NO] += G.a[q / NO][q % NO] * rv;
+    }
+    M<NO> g = scale<NO>(dag<NO>(acc), zd(-(double)d.xi));
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) gvt[b * NO2 + q] = g.a[q / NO][q % NO];
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    zd acc[NO2];
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) acc[q] = zd();
+    for (int b = 0; b < r; ++b) {
+      const double qv = d.q[a * r + b];
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) acc[q] += gvt[b * NO2 + q] * qv;
+    }
+    double2* p = d.vvec + ((long long)n * r + a) * NO2;
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) st(p + q, acc[q]);
+  }
+  if (threadIdx.x == 0) {
+    M<NO> acc = M<NO>::zero();
+    for (int c = 0; c < r; ++c) {
+      M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, T, c));
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) acc.a[q / NO][q % NO] += G.a[q / NO][q % NO] * d.e0[c];
+    }
+    store<NO>(d.x0 + (long long)n * NO2, scale<NO>(dag<NO>(acc), zd(-1.0)));
+  }
+}
+
+// Lesser source q(t) = h sum_l w^(T)_l Sigma^<(t,l) G^A(l,T) - i sum_a Sigma^tv(t,tau_a) v_a
+template <int NO>
+__global__ void k_src(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = gw / (T + 1), t = gw % (T + 1);
+  if (n >= d.n_inst || !d.active[n]) return;
+  const double h = d.h;
+  zd acc[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  for (int l = lane; l <= T; l += 32) {
+    const double wl = h * rule_w(d.w, T, l);
+    M<NO> S;
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int y = 0; y < NO; ++y) S.a[x][y] = sless<NO>(d, n, t, l, x, y);
+    M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+  }
+  for (int a = lane; a < d.r; a += 32) {
+    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, t, a));
+    M<NO> V = load<NO>(d.vvec + ((long long)n * d.r + a) * NO2);
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, V, zd(0, -1));
+  }
+  warp_sum<NO2>(acc);
+  if (lane == 0) {
+    double2* p = d.qsrc + ((long long)n * d.nt + t) * NO2;
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) st(p + q, acc[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lesser column, Eq. KBEL: x_t = G^<(t, T), left-multiplying VIDE in t.
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_les(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, jc = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd farsh[CH][NO];
+  __shared__ zd xch[CH][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* colp = el<NO>(d.GL, d, n, T, 0);  // G^<(t, T) at colp + t NO2
+  auto xptr = [&](int t) { return colp + (long long)t * NO2; };   // element [m][jc] at + m*NO + jc
+  const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
+  double myerr = 0.0;
+  const int last = (d.rho_mode == 1) ? T - 1 : T;
+  if (warp == 0) {
+    // x_0
+    if (lane < NO) {
+      const int m = lane;
+      zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
+      double2* p = xptr(0) + m * NO + jc;
+      myerr = fmax(myerr, sqrt((v - ld(p)).abs2()));
+      st(p, v);
+    }
+    __syncwarp();
+    const int ns = k * NO;
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;       // row (t, m), col (l, y)
+      const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
+      zd v = srx<NO>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
+      if (m == y) v += zd(0, W.D[t][l] / h);
+      if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
+      sA[row * ns + col] = v;
+    }
+    for (int row = lane; row < ns; row += 32) {
+      const int t = row / NO + 1, m = row % NO;
+      zd b = ld(qs + t * NO2 + m * NO + jc);
+      for (int y = 0; y < NO; ++y) {
+        zd c = srx<NO>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
+        if (m == y) c += zd(0, W.D[t][0] / h);
+        if (t == 0) c -= ld(epsp<NO>(d, n, t) + m * NO + y);
+        b -= c * ld(xptr(0) + y * NO + jc);
+      }
+      sB[row] = b;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, sB, 1, nullptr);
+    for (int row = lane; row < ns; row += 32) {
+      const int t = row / NO + 1, m = row % NO;
+      if (t > last) continue;
+      double2* p = xptr(t) + m * NO + jc;
+      myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
+      st(p, sB[row]);
+    }
+  }
+  __syncthreads();
+  for (int t0 = k + 1; t0 <= last; t0 += CH) {
+    const int cn = min(CH, last + 1 - t0);
+    // far field: warp w handles rows t = t0 + w + 8 i, lanes over l < t0
+    for (int tl = warp; tl < cn; tl += NWARP) {
+      const int t = t0 + tl;
+      zd acc[NO];
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[m] = zd();
+      const double2* srow = el<NO>(d.SR, d, n, t, 0);
+      for (int l = lane; l < t0; l += 32) {
+        const double wl = rule_w(W, t, l);
+        const double2* sr = srow + (long long)l * NO2;
+        const double2* xl = xptr(l);
+#pragma unroll
+        for (int y = 0; y < NO; ++y) {
+          const zd xy = ld(xl + y * NO + jc) * wl;
+#pragma unroll
+          for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
+        }
+      }
+      warp_sum<NO>(acc);
+      if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NO; ++m) farsh[tl][m] = acc[m] * h;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int tl = 0; tl < cn; ++tl) {
+        const int t = t0 + tl;
+        zd part[NO];
+#pragma unroll
+        for (int m = 0; m < NO; ++m) part[m] = zd();
+        if (lane < tl) {
+          const int l = t0 + lane;
+          const double wl = h * rule_w(W, t, l);
+          const double2* sr = el<NO>(d.SR, d, n, t, l);
+#pragma unroll
+          for (int y = 0; y < NO; ++y) {
+            const zd xy = xch[lane][y] * wl;
+#pragma unroll
+            for (int m = 0; m < NO; ++m) part[m] = cfma(ld(sr + m * NO + y), xy, part[m]);
+          }
+        }
+        if (lane >= 1 && lane <= k) {
+          const int tj = t - lane;
+          const zd c = zd(0, -W.a[lane] / h);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd xm = (tj >= t0) ? xch[tj - t0][m] : ld(xptr(tj) + m * NO + jc);
+            part[m] += c * xm;
+          }
+        }
+        warp_sum<NO>(part);
+        if (lane == 0) {
+          zd rhs[NO], x[NO];
+#pragma unroll
+          for (int m = 0; m < NO; ++m) rhs[m] = part[m] + farsh[tl][m] + ld(qs + (long long)t * NO2 + m * NO + jc);
+          const double wt = h * rule_w(W, t, t);
+          const double2* sd = el<NO>(d.SR, d, n, t, t);
+          const double2* ep = epsp<NO>(d, n, t);
+          M<NO> Mm;
+#pragma unroll
+          for (int x2 = 0; x2 < NO; ++x2)
+#pragma unroll
+            for (int y = 0; y < NO; ++y)
+              Mm.a[x2][y] = (x2 == y ? zd(0, W.a[0] / h) : zd()) - ld(ep + x2 * NO + y) - ld(sd + x2 * NO + y) * wt;
+          solve_col<NO>(Mm, rhs, x);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            double2* p = xptr(t) + m * NO + jc;
+            myerr = fmax(myerr, sqrt((x[m] - ld(p)).abs2()));
+            st(p, x[m]);
+            xch[tl][m] = x[m];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  myerr = warp_max(myerr);
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal density matrix (Sec. 3.3): (a_0/h) rho + i (A rho - rho A^dag) =
+//   -(1/h) sum_{j>=1} a_j rho(T-j) + xi (r0 + r0^dag),
+// A = eps(T) + h w_T Sigma^R(T,T), r0 = h sum_{l<T} w_l Sigma^R(T,l) x_l + q(T).
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void k_rho(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  if (!d.active[n]) return;
+  const double h = d.h;
+  __shared__ zd part[8][NO2];
+  zd acc[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  for (int l = threadIdx.x; l < T; l += blockDim.x) {
+    const double wl = h * rule_w(d.w, T, l);
+    M<NO> S = load<NO>(el<NO>(d.SR, d, n, T, l));
+    M<NO> X = load<NO>(el<NO>(d.GL, d, n, T, l));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, X, zd(wl));
+  }
+  warp_sum<NO2>(acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < NO2; ++q) part[warp][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  zd r0[NO2];
+  for (int q = 0; q < NO2; ++q) {
+    r0[q] = ld(d.qsrc + ((long long)n * d.nt + T) * NO2 + q);
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) r0[q] += part[w2][q];
+  }
+  const double xi = d.xi;
+  const double wt = h * rule_w(d.w, T, T);
+  M<NO> A, rhs;
+  const double2* sd = el<NO>(d.SR, d, n, T, T);
+  const double2* ep = epsp<NO>(d, n, T);
+  for (int x = 0; x < NO; ++x)
+    for (int y = 0; y < NO; ++y) {
+      A.a[x][y] = ld(ep + x * NO + y) + ld(sd + x * NO + y) * wt;
+      rhs.a[x][y] = (r0[x * NO + y] + r0[y * NO + x].conj()) * xi;
+    }
+  for (int j = 1; j <= d.k; ++j) {
+    M<NO> rho = scale<NO>(load<NO>(el<NO>(d.GL, d, n, T - j, T - j)), zd(0, xi));
+    rhs = rhs - scale<NO>(rho, zd(d.w.a[j] / h));
+  }
+  // L vec(rho) = vec(rhs), vec row-major, L[(x,y),(u,v)]
+  zd L[NO2 * NO2], b[NO2];
+  for (int p = 0; p < NO2; ++p) {
+    const int u = p / NO, v = p % NO;
+    for (int q = 0; q < NO2; ++q) {
+      const int x = q / NO, y = q % NO;
+      // (a0/h) E + i (A E - E A^dag) with E = e_u e_v^T
+      zd val = (x == u && y == v) ? zd(d.w.a[0] / h) : zd();
+      if (y == v) val += zd(0, 1) * A.a[x][u];
+      if (x == u) val -= zd(0, 1) * A.a[y][v].conj();
+      L[q * NO2 + p] = val;
+    }
+    b[p] = rhs.a[u][v];
+  }
+  for (int c = 0; c < NO2; ++c) {  // Gaussian elimination with pivoting
+    int pv = c;
+    for (int r = c + 1; r < NO2; ++r)
+      if (L[r * NO2 + c].abs2() > L[pv * NO2 + c].abs2()) pv = r;
+    if (pv != c) {
+      for (int j = 0; j < NO2; ++j) { zd t = L[c * NO2 + j]; L[c * NO2 + j] = L[pv * NO2 + j]; L[pv * NO2 + j] = t; }
+      zd t = b[c]; b[c] = b[pv]; b[pv] = t;
+    }
+    for (int r = c + 1; r < NO2; ++r) {
+      zd f = cdiv(L[r * NO2 + c], L[c * NO2 + c]);
+      for (int j = c; j < NO2; ++j) L[r * NO2 + j] -= f * L[c * NO2 + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = NO2 - 1; c >= 0; --c) {
+    zd s = b[c];
+    for (int j = c + 1; j < NO2; ++j) s -= L[c * NO2 + j] * b[j];
+    b[c] = cdiv(s, L[c * NO2 + c]);
+  }
+  double2* p = el<NO>(d.GL, d, n, T, T);
+  double e = 0.0;
+  for (int q = 0; q < NO2; ++q) {
+    zd x = b[q] * zd(0, -xi);  // G^<(T,T) = -i xi rho
+    e = fmax(e, sqrt((x - ld(p + q)).abs2()));
+    st(p + q, x);
+  }
+  atomic_max_nonneg(d.err + n, e);
+}
+
+// ---------------------------------------------------------------------------
+// Bootstrap square t <= k (Sec. 3.3, polynomial weights of Appendix A).
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_boot_mixed(Dev d) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  if (!d.active[n]) return;
+  const int k = d.k, r = d.r, ns = k * NO;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ int piv[20];
+  // G^tv(0, tau_i) = i xi G^M(beta - tau_i)
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    M<NO> acc = M<NO>::zero();
+    for (int c = 0; c < r; ++c) {
+      M<NO> G = load<NO>(d.gm + ((long long)n * r + c) * NO2);
+      const double rv = d.rev[i * r + c];
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) acc.a[q / NO][q % NO] += G.a[q / NO][q % NO] * rv;
+    }
+    double2* p = tv<NO>(d.GTV, d, n, 0, i);
+    M<NO> v = scale<NO>(acc, zd(0, (double)d.xi));
+    atomic_max_nonneg(d.err + n, maxabs_diff<NO>(v, load<NO>(p)));
+    store<NO>(p, v);
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;
+      const int m = row / NO + 1, x = row % NO, l = col / NO + 1, y = col % NO;
+      zd v = srx<NO>(d, n, m, l, x, y) * (-h * W.I0[m][l]);
+      if (x == y) v += zd(0, W.D[m][l] / h);
+      if (l == m) v -= ld(epsp<NO>(d, n, m) + x * NO + y);
+      sA[row * ns + col] = v;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, nullptr, 0, piv);
+  }
+  __syncthreads();
+  // one right-hand side per (node i, column y)
+  for (int col = threadIdx.x; col < r * NO; col += blockDim.x) {
+    const int i = col / NO, y = col % NO;
+    zd b[20];
+    for (int m = 1; m <= k; ++m)
+      for (int x = 0; x < NO; ++x) {
+        zd s = zd();
+        for (int a = 0; a < r; ++a) {  // C(m, tau_i) = sum_a Sigma^tv(m, a) W[a][i]
+          const double2* S = tv<NO>(d.STV, d, n, m, a);
+          const double2* C = d.wconv + (((long long)n * r + a) * r + i) * NO2;
+          for (int z = 0; z < NO; ++z) s += ld(S + x * NO + z) * ld(C + z * NO + y);
+        }
+        for (int z = 0; z < NO; ++z) {
+          zd c0 = srx<NO>(d, n, m, 0, x, z) * (-h * W.I0[m][0]);
+          if (x == z) c0 += zd(0, W.D[m][0] / h);
+          s -= c0 * ld(tv<NO>(d.GTV, d, n, 0, i) + z * NO + y);
+        }
+        b[(m - 1) * NO + x] = s;
+      }
+    lu_apply(ns, sA, piv, b);
+    double e = 0.0;
+    for (int m = 1; m <= k; ++m)
+      for (int x = 0; x < NO; ++x) {
+        double2* p = tv<NO>(d.GTV, d, n, m, i) + x * NO + y;
+        e = fmax(e, sqrt((b[(m - 1) * NO + x] - ld(p)).abs2()));
+        st(p, b[(m - 1) * NO + x]);
+      }
+    atomic_max_nonneg(d.err + n, e);
+  }
+}
+
+template <int NO>
+__global__ void k_boot_ret(Dev d) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  if (!d.active[n]) return;
+  const int k = d.k, lane = threadIdx.x;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20 * 4];
+  for (int m = 0; m <= k; ++m)
+    if (lane < NO2) st(el<NO>(d.GR, d, n, m, m) + lane, (lane / NO == lane % NO) ? zd(0, -1) : zd());
+  __syncwarp();
+  double e = 0.0;
+  for (int c = 0; c < k; ++c) {  // column n' = c
+    const int nu = (k - c) * NO;
+    for (int idx = lane; idx < nu * nu; idx += 32) {
+      const int row = idx / nu, col = idx % nu;
+      const int m = row / NO + c + 1, x = row % NO, l = col / NO + c + 1, y = col % NO;
+      zd v = srx<NO>(d, n, m, l, x, y) * (-h * (W.I0[m][l] - W.I0[c][l]));
+      if (x == y) v += zd(0, W.D[m][l] / h);
+      if (l == m) v -= ld(epsp<NO>(d, n, m) + x * NO + y);
+      sA[row * nu + col] = v;
+    }
+    for (int idx = lane; idx < nu * NO; idx += 32) {
+      const int row = idx / NO, y = idx % NO;
+      const int m = row / NO + c + 1, x = row % NO;
+      zd s = zd();
+      for (int l = 0; l <= c; ++l)
+        for (int z = 0; z < NO; ++z) {
+          zd blk = srx<NO>(d, n, m, l, x, z) * (-h * (W.I0[m][l] - W.I0[c][l]));
+          if (x == z) blk += zd(0, W.D[m][l] / h);
+          // gx(l) = G^R(l, c) for l >= c, -[G^R(c, l)]^dagger for l < c
+          zd g = (l >= c) ? ld(el<NO>(d.GR, d, n, l, c) + z * NO + y)
+                          : -ld(el<NO>(d.GR, d, n, c, l) + y * NO + z).conj();
+          s -= blk * g;
+        }
+      sB[row * NO + y] = s;
+    }
+    __syncwarp();
+    warp_lu_solve(nu, sA, sB, NO, nullptr);
+    for (int idx = lane; idx < nu * NO; idx += 32) {
+      const int row = idx / NO, y = idx % NO;
+      const int m = row / NO + c + 1, x = row % NO;
+      double2* p = el<NO>(d.GR, d, n, m, c) + x * NO + y;
+      e = fmax(e, sqrt((sB[row * NO + y] - ld(p)).abs2()));
+      st(p, sB[row * NO + y]);
+    }
+    __syncwarp();
+  }
+  e = warp_max(e);
+  if (lane == 0) atomic_max_nonneg(d.err + n, e);
+}
+
+template <int NO>
+__global__ void k_boot_les(Dev d) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  if (!d.active[n]) return;
+  const int k = d.k, r = d.r, lane = threadIdx.x;
+  const double h = d.h, xi = d.xi;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20 * 4];
+  __shared__ zd x0s[NO2];
+  double2* vv = d.vvec + (long long)n * r * NO2;
+  double e = 0.0;
+  for (int m = k; m >= 0; --m) {
+    // x_0 = -[G^tv(m, 0)]^dagger ; v_a = sum_b Q_ab (-xi) [sum_c Rev_bc G^tv(m, c)]^dagger
+    if (lane < NO2) {
+      const int x = lane / NO, y = lane % NO;
+      zd s = zd();
+      for (int c = 0; c < r; ++c) s += ld(tv<NO>(d.GTV, d, n, m, c) + y * NO + x) * d.e0[c];
+      x0s[lane] = -s.conj();
+      double2* p = el<NO>(d.GL, d, n, m, 0) + lane;
+      e = fmax(e, sqrt((x0s[lane] - ld(p)).abs2()));
+      st(p, x0s[lane]);
+    }
+    for (int idx = lane; idx < r * NO2; idx += 32) {
+      const int a = idx / NO2, q = idx % NO2, x = q / NO, y = q % NO;
+      zd s = zd();
+      for (int b = 0; b < r; ++b) {
+        zd g = zd();
+        for (int c = 0; c < r; ++c) g += ld(tv<NO>(d.GTV, d, n, m, c) + y * NO + x) * d.rev[b * r + c];
+        s += g.conj() * (-xi * d.q[a * r + b]);
+      }
+      st(vv + idx, s);
+    }
+    __syncwarp();
+    if (m == 0) break;
+    const int nu = m * NO;
+    for (int idx = lane; idx < nu * nu; idx += 32) {
+      const int row = idx / nu, col = idx % nu;
+      const int t = row / NO + 1, x = row % NO, l = col / NO + 1, y = col % NO;
+      zd v = srx<NO>(d, n, t, l, x, y) * (-h * W.I0[t][l]);
+      if (x == y) v += zd(0, W.D[t][l] / h);
+      if (l == t) v -= ld(epsp<NO>(d, n, t) + x * NO + y);
+      sA[row * nu + col] = v;
+    }
+    for (int idx = lane; idx < nu * NO; idx += 32) {
+      const int row = idx / NO, y = idx % NO;
+      const int t = row / NO + 1, x = row % NO;
+      zd s = zd();
+      // q_m(t) = h sum_{l=0}^{k} I_{0,m,l} Sigma^<(t,l) G^A_x(l,m) - i sum_a Sigma^tv(t,a) v_a
+      for (int l = 0; l <= k; ++l) {
+        const double wl = h * W.I0[m][l];
+        for (int z = 0; z < NO; ++z) {
+          zd ga = (l <= m) ? ld(el<NO>(d.GR, d, n, m, l) + y * NO + z).conj()
+                           : -ld(el<NO>(d.GR, d, n, l, m) + z * NO + y);
+          s += sless<NO>(d, n, t, l, x, z) * ga * wl;
+        }
+      }
+      for (int a = 0; a < r; ++a)
+        for (int z = 0; z < NO; ++z)
+          s += ld(tv<NO>(d.STV, d, n, t, a) + x * NO + z) * ld(vv + a * NO2 + z * NO + y) * zd(0, -1);
+      // known points l = 0 and l > m
+      for (int l = 0; l <= k; ++l) {
+        if (l >= 1 && l <= m) continue;
+        for (int z = 0; z < NO; ++z) {
+          zd blk = srx<NO>(d, n, t, l, x, z) * (-h * W.I0[t][l]);
+          if (x == z) blk += zd(0, W.D[t][l] / h);
+          if (l == t) blk -= ld(epsp<NO>(d, n, t) + x * NO + z);
+          zd xl = (l == 0) ? x0s[z * NO + y] : -ld(el<NO>(d.GL, d, n, l, m) + y * NO + z).conj();
+          s -= blk * xl;
+        }
+      }
+      sB[row * NO + y] = s;
+    }
+    __syncwarp();
+    warp_lu_solve(nu, sA, sB, NO, nullptr);
+    for (int idx = lane; idx < nu * NO; idx += 32) {
+      const int row = idx / NO, y = idx % NO;
+      const int t = row / NO + 1, x = row % NO;
+      double2* p = el<NO>(d.GL, d, n, m, t) + x * NO + y;
+      e = fmax(e, sqrt((sB[row * NO + y] - ld(p)).abs2()));
+      st(p, sB[row * NO + y]);
+    }
+    __syncwarp();
+  }
+  e = warp_max(e);
+  if (lane == 0) atomic_max_nonneg(d.err + n, e);
+}
+
+// Per-instance convergence bookkeeping after an iteration.
+__global__ void k_set_active(Dev d, double tol, int iter, int min_iter, int* any) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.n_inst) return;
+  if (!d.active[n]) return;
+  const double e = d.err[n];
+  if ((e < tol && iter >= min_iter) || !(e == e)) d.active[n] = 0;
+  else atomicOr(any, 1);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define HK_DISPATCH(NOV, CALL)            \
+  switch (NOV) {                          \
+    case 1: { constexpr int NO = 1; CALL; break; } \
+    case 2: { constexpr int NO = 2; CALL; break; } \
+    case 3: { constexpr int NO = 3; CALL; break; } \
+    case 4: { constexpr int NO = 4; CALL; break; } \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_extrapolate(const Dev& d, int T, cudaStream_t s) {
+  dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
+  HK_DISPATCH(d.no, (k_extrap<NO><<<g, 128, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_sigma(const Dev& d, int T, cudaStream_t s) {
+  dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
+  HK_DISPATCH(d.no, (k_sigma<NO><<<g, 128, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_ret(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_ret<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_mixed(const Dev& d, int T, cudaStream_t s) {
+  const long long warps = (long long)d.n_inst * d.r;
+  HK_DISPATCH(d.no, (k_mixed<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_vt(const Dev& d, int T, cudaStream_t s) {
+  HK_DISPATCH(d.no, (k_vt<NO><<<d.n_inst, 128, d.r * NO * NO * sizeof(zd), s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_src(const Dev& d, int T, cudaStream_t s) {
+  const long long warps = (long long)d.n_inst * (T + 1);
+  HK_DISPATCH(d.no, (k_src<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_les(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_les<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_rho(const Dev& d, int T, cudaStream_t s) {
+  HK_DISPATCH(d.no, (k_rho<NO><<<d.n_inst, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_boot(const Dev& d, cudaStream_t s) {
+  for (int t = 0; t <= d.k; ++t) {
+    cudaError_t e = launch_sigma(d, t, s);
+    if (e != cudaSuccess) return e;
+  }
+  HK_DISPATCH(d.no, (k_boot_mixed<NO><<<d.n_inst, 256, 0, s>>>(d)));
+  HK_DISPATCH(d.no, (k_boot_ret<NO><<<d.n_inst, 32, 0, s>>>(d)));
+  HK_DISPATCH(d.no, (k_boot_les<NO><<<d.n_inst, 32, 0, s>>>(d)));
+  return cudaGetLastError();
+}
+cudaError_t launch_set_active(const Dev& d, double tol, int iter, int min_iter, int* any, cudaStream_t s) {
+  k_set_active<<<(d.n_inst + 127) / 128, 128, 0, s>>>(d, tol, iter, min_iter, any);
+  return cudaGetLastError();
+}
+
+}  // namespace hk
