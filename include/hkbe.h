@@ -151,6 +151,38 @@ int hkbe_get_density(hkbe_t* h, double* rho);
 /* Device bytes held by the handle. */
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);
 
+/* Return to the state right after hkbe_bootstrap (current step = k), so the
+ * time stepping can be run again from the same start (e.g. to time it, or
+ * to propagate again after changing eps(t) for t > k with hkbe_set_hamiltonian).
+ * Errors: HKBE_ERR_ARG before the bootstrap. */
+int hkbe_rewind(hkbe_t* h);
+
+/* ---- instrumentation (Sec. 3.5 write_timing / profiling) ---- */
+enum {
+  HKBE_PHASE_EXTRAP = 0,  /* initial guess of a step                           */
+  HKBE_PHASE_SIGMA = 1,   /* self-energy evaluation                            */
+  HKBE_PHASE_RET = 2,     /* retarded row (history integral + VIDE)            */
+  HKBE_PHASE_MIXED = 3,   /* mixed component                                   */
+  HKBE_PHASE_VT = 4,      /* mixed-product vector and lesser boundary value    */
+  HKBE_PHASE_SRC = 5,     /* lesser source (Sigma^< and Sigma^tv histories)     */
+  HKBE_PHASE_LES = 6,     /* lesser column (history integral + VIDE)           */
+  HKBE_PHASE_RHO = 7,     /* diagonal density matrix                           */
+  HKBE_PHASE_BOOT = 8,    /* bootstrap square                                  */
+  HKBE_PHASE_CTRL = 9,    /* convergence bookkeeping                           */
+  HKBE_NPHASE = 10
+};
+
+/* When on (nonzero), every kernel launch is bracketed by CUDA events on the
+ * handle's stream and its device time is accumulated per phase. */
+int hkbe_set_profiling(hkbe_t* h, int on);
+
+/* Accumulated device milliseconds and launch count of `phase` since the last
+ * hkbe_reset_counters (timing only while profiling is on; launches always). */
+int hkbe_get_timing(const hkbe_t* h, int phase, double* ms, int64_t* launches);
+
+/* Zero the per-phase times and launch counts. */
+int hkbe_reset_counters(hkbe_t* h);
+
 /* ---- host-only numerics, exported for inspection (no device work) ---- */
 
 /* Appendix A weights for order k (1..5): a[k+1] (BDF), omega[k+1] (Gregory),

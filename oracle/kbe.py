@@ -34,9 +34,8 @@ Bootstrap (T <= k) solves the (k+1) x (k+1) start square with the polynomial
 weights D and I (Appendix A), by global iteration with Sigma (Sec. 3.3):
 mixed rows 1..k together; retarded columns n = 0..k in increasing n with the
 left equation (derivative in the first argument), entries above the diagonal
-taken by continuation from the columns already solved; lesser columns m = k..0
-in decreasing m, entries below the diagonal taken by anti-Hermitian symmetry
-from the columns already solved.
+taken by continuation from the columns already solved; every lesser column m
+solves the full start block t = 1..k and keeps t <= m.
 """
 from __future__ import annotations
 
@@ -185,39 +184,38 @@ class KBEOracle:
                 self.GR[m, n] = X[mi * No:(mi + 1) * No]
 
     def _boot_les(self):
+        """Lesser columns m = 0..k of the start square.  Column m solves the
+        start block (the equations t = 1..k with D and I_{0,t,.}) for all
+        x(t) = G^<(t, m), t = 1..k, and keeps the entries t <= m; the entries
+        t > m are the lower triangle, owned by the columns t (anti-Hermitian
+        symmetry)."""
         k, h, No, W = self.k, self.h, self.no, self.W
-        for m in range(k, -1, -1):
+        E = np.zeros((k * No, k * No), complex)
+        for t in range(1, k + 1):
+            It = W.I(0, t)
+            for l in range(1, k + 1):
+                blk = (1j / h) * W.D[t, l] * self.I1 - h * It[l] * self.sR_x(t, l)
+                if l == t:
+                    blk = blk - self.ep(t)
+                E[(t - 1) * No:t * No, (l - 1) * No:l * No] = blk
+        for m in range(k + 1):
             x0 = -_dag(self.gtv_at0(m))
             self.GLs[m, 0] = x0
             if m == 0:
                 continue
             Im = W.I(0, m)
-            vt = self.gvt(m)                                     # (r, No, No)
-            v = np.einsum("ab,bxy->axy", self.Q, vt)
+            v = np.einsum("ab,bxy->axy", self.Q, self.gvt(m))
 
             def gA(l):   # G^A(l, m) continued: [G^R(m,l)]^dag, l<=m; -G^R(l,m), l>m
                 return _dag(self.GR[m, l]) if l <= m else -self.GR[l, m]
-
-            def xk(l):   # G^<(l, m), known for l = 0 and l > m
-                return x0 if l == 0 else -_dag(self.GLs[l, m])
-            E = np.zeros((m * No, m * No), complex)
-            B = np.zeros((m * No, No), complex)
-            for t in range(1, m + 1):
+            B = np.zeros((k * No, No), complex)
+            for t in range(1, k + 1):
                 q = np.zeros((No, No), complex)
                 for l in range(k + 1):
                     q += h * Im[l] * self.sL(t, l) @ gA(l)
                 q += -1j * np.einsum("axy,ayz->xz", self.STV[t], v)
-                It = W.I(0, t)
-                acc = q.copy()
-                for l in range(k + 1):
-                    blk = (1j / h) * W.D[t, l] * self.I1 - h * It[l] * self.sR_x(t, l)
-                    if l == t:
-                        blk = blk - self.ep(t)
-                    if 1 <= l <= m:
-                        E[(t - 1) * No:t * No, (l - 1) * No:l * No] = blk
-                    else:
-                        acc -= blk @ xk(l)
-                B[(t - 1) * No:t * No] = acc
+                c0 = (1j / h) * W.D[t, 0] * self.I1 - h * W.I(0, t)[0] * self.sR_x(t, 0)
+                B[(t - 1) * No:t * No] = q - c0 @ x0
             X = np.linalg.solve(E, B)
             for t in range(1, m + 1):
                 self.GLs[m, t] = X[(t - 1) * No:t * No]

@@ -74,6 +74,10 @@ def load(build_if_missing: bool = True):
         "hkbe_get_row": ([H, C.c_int, C.c_int, _D, _D], C.c_int),
         "hkbe_get_density": ([H, _D], C.c_int),
         "hkbe_get_stats": ([H, C.POINTER(C.c_size_t)], C.c_int),
+        "hkbe_rewind": ([H], C.c_int),
+        "hkbe_set_profiling": ([H, C.c_int], C.c_int),
+        "hkbe_get_timing": ([H, C.c_int, _D, C.POINTER(C.c_int64)], C.c_int),
+        "hkbe_reset_counters": ([H], C.c_int),
         "hkbe_weights": ([C.c_int, _D, _D, _D, _D], C.c_int),
         "hkbe_rule": ([C.c_int, C.c_int, _D], C.c_int),
         "hkbe_dlr_matrices": ([C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, _D, _D, _D], C.c_int),
@@ -203,6 +207,28 @@ def hkbe_get_stats(h):
     return int(b.value)
 
 
+def hkbe_rewind(h):
+    _check(load().hkbe_rewind(h), h)
+
+
+def hkbe_set_profiling(h, on):
+    _check(load().hkbe_set_profiling(h, int(bool(on))), h)
+
+
+PHASES = ["extrap", "sigma", "ret", "mixed", "vt", "src", "les", "rho", "boot", "ctrl"]
+
+
+def hkbe_get_timing(h, phase):
+    ms = np.zeros(1)
+    n = C.c_int64()
+    _check(load().hkbe_get_timing(h, int(phase), _dp(ms), C.byref(n)), h)
+    return float(ms[0]), int(n.value)
+
+
+def hkbe_reset_counters(h):
+    _check(load().hkbe_reset_counters(h), h)
+
+
 def hkbe_weights(k):
     a = np.zeros(k + 1)
     om = np.zeros(k + 1)
@@ -271,6 +297,10 @@ class Stepper:
         self.bootstrap()
         T = hkbe_current_step(self.h)
         return self.step(self.nt - 1 - T)
+
+    def timing(self):
+        """{phase: (device ms, launches)} accumulated since the last reset."""
+        return {name: hkbe_get_timing(self.h, i) for i, name in enumerate(PHASES)}
 
     def row(self, inst, T):
         return hkbe_get_row(self.h, self.nao, inst, T)

@@ -26,7 +26,51 @@ struct hkbe_s {
   int* any_dev = nullptr;
   size_t bytes = 0;
   std::vector<void*> allocs;
+  // instrumentation
+  bool profiling = false;
+  double phase_ms[HKBE_NPHASE] = {0};
+  int64_t phase_launches[HKBE_NPHASE] = {0};
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  // bootstrap snapshot for hkbe_rewind (rows 0..k of every component)
+  std::vector<double2> snap_gr, snap_gl, snap_sr, snap_sl, snap_tv, snap_stv;
 };
+
+namespace {
+// Launch one phase: counts its kernels and, when profiling, brackets it with
+// events whose elapsed time is collected at the next drain().
+template <typename F>
+cudaError_t run_phase(hkbe_t* h, int phase, int nkernels, F launch) {
+  h->phase_launches[phase] += nkernels;
+  if (!h->profiling) return launch();
+  cudaEvent_t ev[2];
+  for (int i = 0; i < 2; ++i) {
+    if (!h->event_pool.empty()) {
+      ev[i] = h->event_pool.back();
+      h->event_pool.pop_back();
+    } else {
+      cudaError_t e = cudaEventCreate(&ev[i]);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  cudaEventRecord(ev[0], h->s);
+  cudaError_t e = launch();
+  cudaEventRecord(ev[1], h->s);
+  h->pending.push_back({phase, ev[0], ev[1]});
+  return e;
+}
+// Collect elapsed times of completed phases (call after a stream sync).
+void drain(hkbe_t* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->phase_ms[p.phase] += ms;
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->pending.clear();
+}
+}  // namespace
 
 static std::string g_create_error;
 
@@ -116,7 +160,9 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
 
 int hkbe_destroy(hkbe_t* h) {
   if (!h) return HKBE_OK;
-  if (h->s) cudaStreamSynchronize(h->s);
+  cudaStreamSynchronize(h->s);
+  drain(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
   return HKBE_OK;
@@ -327,7 +373,8 @@ static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, 
     HK_CUDA(h, cudaMemsetAsync(d.err, 0, N * sizeof(double), h->s));
     HK_CUDA(h, cudaMemsetAsync(h->any_dev, 0, sizeof(int), h->s));
     HK_CUDA(h, pass());
-    HK_CUDA(h, hk::launch_set_active(d, tol_eff, it, min_iter, h->any_dev, h->s));
+    HK_CUDA(h, run_phase(h, HKBE_PHASE_CTRL, 1,
+                         [&]() { return hk::launch_set_active(d, tol_eff, it, min_iter, h->any_dev, h->s); }));
     int any = 0;
     HK_CUDA(h, cudaMemcpyAsync(err.data(), d.err, N * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     HK_CUDA(h, cudaMemcpyAsync(&any, h->any_dev, sizeof(int), cudaMemcpyDeviceToHost, h->s));
@@ -340,6 +387,7 @@ static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, 
       }
     HK_CUDA(h, cudaMemcpyAsync(act.data(), d.active, N * sizeof(int), cudaMemcpyDeviceToHost, h->s));
     HK_CUDA(h, cudaStreamSynchronize(h->s));
+    drain(h);
     if (!any) break;
   }
   *any_failed = false;
@@ -360,13 +408,37 @@ int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* 
   if ((rc = hf_guess(h))) return rc;
   Dev& d = h->d;
   bool failed = false;
-  rc = iterate(h, max_iter, tol, [&]() { return hk::launch_boot(d, h->s); }, iters, err, &failed);
+  rc = iterate(h, max_iter, tol,
+               [&]() { return run_phase(h, HKBE_PHASE_BOOT, d.k + 4, [&]() { return hk::launch_boot(d, h->s); }); },
+               iters, err, &failed);
   if (rc) return rc;
   // Sigma of the converged square (all instances)
   std::vector<int> ones(d.n_inst, 1);
   HK_CUDA(h, cudaMemcpyAsync(d.active, ones.data(), d.n_inst * sizeof(int), cudaMemcpyHostToDevice, h->s));
   for (int t = 0; t <= d.k; ++t) HK_CUDA(h, hk::launch_sigma(d, t, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
+  drain(h);
+  // snapshot of the start square for hkbe_rewind
+  {
+    const int n2 = no2(h), k = d.k;
+    const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
+    auto grab = [&](std::vector<double2>& dst, const double2* src, size_t per, size_t stride) -> cudaError_t {
+      dst.resize(per * d.n_inst);
+      for (int n = 0; n < d.n_inst; ++n) {
+        cudaError_t e = cudaMemcpyAsync(dst.data() + per * n, src + stride * n, per * sizeof(double2),
+                                        cudaMemcpyDeviceToHost, h->s);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaStreamSynchronize(h->s);
+    };
+    const size_t trs = (size_t)d.ntri * n2, tvs = (size_t)d.nt * d.r * n2;
+    HK_CUDA(h, grab(h->snap_gr, d.GR, sq, trs));
+    HK_CUDA(h, grab(h->snap_gl, d.GL, sq, trs));
+    HK_CUDA(h, grab(h->snap_sr, d.SR, sq, trs));
+    HK_CUDA(h, grab(h->snap_sl, d.SL, sq, trs));
+    HK_CUDA(h, grab(h->snap_tv, d.GTV, tvn, tvs));
+    HK_CUDA(h, grab(h->snap_stv, d.STV, tvn, tvs));
+  }
   h->cur = d.k;
   if (failed) return fail(h, HKBE_ERR_NOCONV, "bootstrap did not converge");
   return HKBE_OK;
@@ -383,18 +455,22 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
   bool any_failed = false;
   for (int st = 0; st < n_steps; ++st) {
     const int T = h->cur + 1;
-    HK_CUDA(h, hk::launch_extrapolate(d, T, h->s));
+    HK_CUDA(h, run_phase(h, HKBE_PHASE_EXTRAP, 1, [&]() { return hk::launch_extrapolate(d, T, h->s); }));
     bool failed = false;
     rc = iterate(h, h->p.max_iter, h->p.tol,
                  [&]() -> cudaError_t {
                    cudaError_t e;
-                   if ((e = hk::launch_sigma(d, T, h->s)) != cudaSuccess) return e;
-                   if ((e = hk::launch_ret(d, T, h->s)) != cudaSuccess) return e;
-                   if ((e = hk::launch_mixed(d, T, h->s)) != cudaSuccess) return e;
-                   if ((e = hk::launch_vt(d, T, h->s)) != cudaSuccess) return e;
-                   if ((e = hk::launch_src(d, T, h->s)) != cudaSuccess) return e;
-                   if ((e = hk::launch_les(d, T, h->s)) != cudaSuccess) return e;
-                   if (d.rho_mode == 1 && (e = hk::launch_rho(d, T, h->s)) != cudaSuccess) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_SIGMA, 1, [&]() { return hk::launch_sigma(d, T, h->s); })))
+                     return e;
+                   if ((e = run_phase(h, HKBE_PHASE_RET, 1, [&]() { return hk::launch_ret(d, T, h->s); }))) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_MIXED, 1, [&]() { return hk::launch_mixed(d, T, h->s); })))
+                     return e;
+                   if ((e = run_phase(h, HKBE_PHASE_VT, 1, [&]() { return hk::launch_vt(d, T, h->s); }))) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_SRC, 1, [&]() { return hk::launch_src(d, T, h->s); }))) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_LES, 1, [&]() { return hk::launch_les(d, T, h->s); }))) return e;
+                   if (d.rho_mode == 1 &&
+                       (e = run_phase(h, HKBE_PHASE_RHO, 1, [&]() { return hk::launch_rho(d, T, h->s); })))
+                     return e;
                    return cudaSuccess;
                  },
                  iters ? iters + (size_t)st * N : nullptr, err ? err + (size_t)st * N : nullptr, &failed);
@@ -490,6 +566,58 @@ int hkbe_get_density(hkbe_t* h, double* rho) {
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes) {
   if (!h || !device_bytes) return HKBE_ERR_ARG;
   *device_bytes = h->bytes;
+  return HKBE_OK;
+}
+
+int hkbe_rewind(hkbe_t* h) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (h->cur < 0 || h->snap_gr.empty()) return fail(h, HKBE_ERR_ARG, "hkbe_bootstrap must precede hkbe_rewind");
+  Dev& d = h->d;
+  const int n2 = no2(h), k = d.k;
+  const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
+  const size_t trs = (size_t)d.ntri * n2, tvs = (size_t)d.nt * d.r * n2;
+  auto put = [&](const std::vector<double2>& src, double2* dst, size_t per, size_t stride) -> cudaError_t {
+    for (int n = 0; n < d.n_inst; ++n) {
+      cudaError_t e = cudaMemcpyAsync(dst + stride * n, src.data() + per * n, per * sizeof(double2),
+                                      cudaMemcpyHostToDevice, h->s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  HK_CUDA(h, put(h->snap_gr, d.GR, sq, trs));
+  HK_CUDA(h, put(h->snap_gl, d.GL, sq, trs));
+  HK_CUDA(h, put(h->snap_sr, d.SR, sq, trs));
+  HK_CUDA(h, put(h->snap_sl, d.SL, sq, trs));
+  HK_CUDA(h, put(h->snap_tv, d.GTV, tvn, tvs));
+  HK_CUDA(h, put(h->snap_stv, d.STV, tvn, tvs));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->cur = k;
+  return HKBE_OK;
+}
+
+int hkbe_set_profiling(hkbe_t* h, int on) {
+  if (!h) return HKBE_ERR_ARG;
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  drain(h);
+  h->profiling = (on != 0);
+  return HKBE_OK;
+}
+
+int hkbe_get_timing(const hkbe_t* h, int phase, double* ms, int64_t* launches) {
+  if (!h || phase < 0 || phase >= HKBE_NPHASE) return HKBE_ERR_ARG;
+  if (ms) *ms = h->phase_ms[phase];
+  if (launches) *launches = h->phase_launches[phase];
+  return HKBE_OK;
+}
+
+int hkbe_reset_counters(hkbe_t* h) {
+  if (!h) return HKBE_ERR_ARG;
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  drain(h);
+  for (int i = 0; i < HKBE_NPHASE; ++i) {
+    h->phase_ms[i] = 0.0;
+    h->phase_launches[i] = 0;
+  }
   return HKBE_OK;
 }
 

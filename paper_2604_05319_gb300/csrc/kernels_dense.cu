@@ -961,7 +961,7 @@ __global__ void k_boot_les(Dev d) {
   __shared__ zd x0s[NO2];
   double2* vv = d.vvec + (long long)n * r * NO2;
   double e = 0.0;
-  for (int m = k; m >= 0; --m) {
+  for (int m = 0; m <= k; ++m) {
     // x_0 = -[G^tv(m, 0)]^dagger ; v_a = sum_b Q_ab (-xi) [sum_c Rev_bc G^tv(m, c)]^dagger
     if (lane < NO2) {
       const int x = lane / NO, y = lane % NO;
@@ -983,8 +983,10 @@ __global__ void k_boot_les(Dev d) {
       st(vv + idx, s);
     }
     __syncwarp();
-    if (m == 0) break;
-    const int nu = m * NO;
+    if (m == 0) continue;
+    // column m solves the start block t = 1..k for every x(t) = G^<(t, m) and
+    // keeps t <= m (entries t > m belong to the lower triangle of column t)
+    const int nu = k * NO;
     for (int idx = lane; idx < nu * nu; idx += 32) {
       const int row = idx / nu, col = idx % nu;
       const int t = row / NO + 1, x = row % NO, l = col / NO + 1, y = col % NO;
@@ -1009,16 +1011,10 @@ __global__ void k_boot_les(Dev d) {
       for (int a = 0; a < r; ++a)
         for (int z = 0; z < NO; ++z)
           s += ld(tv<NO>(d.STV, d, n, t, a) + x * NO + z) * ld(vv + a * NO2 + z * NO + y) * zd(0, -1);
-      // known points l = 0 and l > m
-      for (int l = 0; l <= k; ++l) {
-        if (l >= 1 && l <= m) continue;
-        for (int z = 0; z < NO; ++z) {
-          zd blk = srx<NO>(d, n, t, l, x, z) * (-h * W.I0[t][l]);
-          if (x == z) blk += zd(0, W.D[t][l] / h);
-          if (l == t) blk -= ld(epsp<NO>(d, n, t) + x * NO + z);
-          zd xl = (l == 0) ? x0s[z * NO + y] : -ld(el<NO>(d.GL, d, n, l, m) + y * NO + z).conj();
-          s -= blk * xl;
-        }
+      for (int z = 0; z < NO; ++z) {  // known point l = 0
+        zd blk = srx<NO>(d, n, t, 0, x, z) * (-h * W.I0[t][0]);
+        if (x == z) blk += zd(0, W.D[t][0] / h);
+        s -= blk * x0s[z * NO + y];
       }
       sB[row * NO + y] = s;
     }
@@ -1027,6 +1023,7 @@ __global__ void k_boot_les(Dev d) {
     for (int idx = lane; idx < nu * NO; idx += 32) {
       const int row = idx / NO, y = idx % NO;
       const int t = row / NO + 1, x = row % NO;
+      if (t > m) continue;
       double2* p = el<NO>(d.GL, d, n, m, t) + x * NO + y;
       e = fmax(e, sqrt((sB[row * NO + y] - ld(p)).abs2()));
       st(p, sB[row * NO + y]);

@@ -41,7 +41,7 @@ def _run_pair(nt, h, k, eps_d, model_name, model_params, gm, rho_mode=0, tau=TAU
     o = KBEOracle(nt, h, k, beta, eps, gm, tau, om, make_model(model_name, model_params), tol=1e-14,
                   rho_mode=rho_mode)
     o.run()
-    st = pk.Stepper(nt, h, k, beta, nao=no, n_inst=1, rho_mode=rho_mode, tol=1e-14, max_iter=60)
+    st = pk.Stepper(nt, h, k, beta, nao=no, n_inst=1, rho_mode=rho_mode, tol=1e-13, max_iter=60)
     mid = {"none": pk.MODEL_NONE, "bath": pk.MODEL_BATH}[model_name]
     mp = None if model_name == "none" else _bath_params(model_params["V"], model_params["eb"])[None]
     st.set_inputs(tau, om, gm[None], eps[None], mid, mp)
@@ -91,7 +91,7 @@ def test_minimal_and_ragged_lengths_bethe(k, nt):
     w = wk.bethe_workload(nt=nt, h=0.05, k=k, beta=BETA, seed=1, dlr_eps=1e-12)
     o = from_workload(w, tol=1e-14)
     o.run()
-    st = pk.Stepper(nt, 0.05, k, BETA, tol=1e-14, max_iter=60)
+    st = pk.Stepper(nt, 0.05, k, BETA, tol=1e-13, max_iter=60)
     mid, mp = pk.model_params_for(w)
     st.set_inputs(w["tau"], w["omega"], w["gm"], w["eps"], mid, mp)
     st.run()
