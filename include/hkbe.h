@@ -201,6 +201,52 @@ int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta
                       int xi, double* e0, double* ebeta, double* rev, double* q,
                       double* phi);
 
+/* ---- allocation-free variant (no counterpart in the paper) ---- */
+
+/* Capacity of the static device scratch array used by
+ * hkbe_lesser_column_noalloc, in complex doubles (16 bytes each): 1 MiB. */
+#define HKBE_NOALLOC_SCRATCH_CPLX 65536
+
+/* The lesser column of one time step, x_t = G^<(t, T) for t = 0..T (the
+ * source q of Eq. KBEL followed by the lesser VIDE, horizontal density
+ * matrix), computed from buffers the caller already owns and WITHOUT any
+ * device allocation.  It is meant for callers that cannot call cudaMalloc
+ * (for example code running inside a memory allocator's callbacks, or in a
+ * process whose device memory is all handed to another framework); they cannot
+ * use hkbe_create, which allocates the handle's arrays.  The same kernels as
+ * hkbe_step's lesser phase run here; their scratch (the mixed-product vector,
+ * the boundary value and the lesser source, r*nao^2 + nao^2 + nt*nao^2 + 2
+ * complex doubles) lives in one file-scope device array of
+ * HKBE_NOALLOC_SCRATCH_CPLX entries that every GPU loading the library holds
+ * until the process exits.  Sizes beyond it are rejected with HKBE_ERR_ARG
+ * and a message saying so.
+ *
+ * All array arguments are DEVICE pointers to one instance in the dense layout
+ * of the handle API: lower-triangular arrays of nt(nt+1)/2 N_o x N_o complex
+ * matrices where element (T', t) sits at T'(T'+1)/2 + t, holding
+ *   d_gr  G^R(T', t)        (row T is read)
+ *   d_sr  Sigma^R(T', t)    (rows 0..T read)
+ *   d_sl  Sigma^<(t, T')    (rows 0..T read)
+ *   d_gl  G^<(t, T')        (row T is written: the output)
+ * mixed arrays d_gtv = G^tv(T', tau_i), d_stv = Sigma^tv(T', tau_i) of
+ * nt x r matrices (row T of d_gtv and rows 0..T of d_stv read), d_eps the
+ * (nt+1) matrices eps(t), t = -1..nt-1, and the DLR matrices e0[r], rev[r*r],
+ * q[r*r] of hkbe_dlr_matrices.  k is the integration order, h the step, and
+ * T the step with k < T < nt.  Work is queued on `stream` (NULL: legacy
+ * default stream); the call returns without waiting for it.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array, which keeps the previous
+ * call's contents; calls that overlap on the GPU (other streams, other host
+ * threads) race on it, so serialise them.  On failure the message is copied
+ * into errbuf[errlen] (may be NULL). */
+int hkbe_lesser_column_noalloc(int nt, int k, int nao, int r, double h, int T,
+                               const void* d_gr, const void* d_sr, const void* d_sl,
+                               const void* d_gtv, const void* d_stv, const void* d_eps,
+                               const double* d_e0, const double* d_rev, const double* d_q,
+                               void* d_gl, void* stream, char* errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

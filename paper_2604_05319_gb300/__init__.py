@@ -81,6 +81,9 @@ def load(build_if_missing: bool = True):
         "hkbe_weights": ([C.c_int, _D, _D, _D, _D], C.c_int),
         "hkbe_rule": ([C.c_int, C.c_int, _D], C.c_int),
         "hkbe_dlr_matrices": ([C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, _D, _D, _D], C.c_int),
+        "hkbe_lesser_column_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]
+                                       + [C.c_void_p] * 6 + [C.c_void_p] * 3
+                                       + [C.c_void_p, C.c_void_p, C.c_char_p, C.c_size_t], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -253,6 +256,16 @@ def hkbe_dlr_matrices(tau, omega, beta, xi=-1):
     _check(load().hkbe_dlr_matrices(r, _dp(tau), _dp(om), float(beta), int(xi), _dp(e0), _dp(eb),
                                     _dp(rev), _dp(q), _dp(phi)))
     return e0, eb, rev.reshape(r, r), q.reshape(r, r), phi.reshape(r, r, r)
+
+
+def hkbe_lesser_column_noalloc(nt, k, nao, r, h, T, d_gr, d_sr, d_sl, d_gtv, d_stv, d_eps,
+                               d_e0, d_rev, d_q, d_gl, stream=None):
+    """Device pointers (ints) in, G^<(., T) written into d_gl; no allocation."""
+    buf = C.create_string_buffer(256)
+    rc = load().hkbe_lesser_column_noalloc(nt, k, nao, r, float(h), T, d_gr, d_sr, d_sl, d_gtv, d_stv,
+                                           d_eps, d_e0, d_rev, d_q, d_gl, stream, buf, 256)
+    if rc != HKBE_OK:
+        raise HKBEError(rc, buf.value.decode())
 
 
 # ---- convenience wrapper -----------------------------------------------------
