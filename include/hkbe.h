@@ -70,6 +70,10 @@ typedef struct {
   double h;           /* time step                                              */
   double beta;        /* inverse temperature of the thermal initial state       */
   double tol;         /* self-consistency tolerance on max |G^(i) - G^(i-1)|     */
+  double svd_tol;     /* > 0: HODLR storage with TSVD truncation at this absolute
+                         singular value (Sec. 2.2); 0: dense triangles          */
+  int32_t leaf;       /* HODLR leaf size, 32 or 64 (> 2k); blocks are leaf-aligned */
+  int32_t r_max;      /* rank capacity per block and orbital pair, 1..128       */
 } hkbe_params;
 
 typedef struct hkbe_s hkbe_t;
@@ -151,6 +155,19 @@ int hkbe_get_density(hkbe_t* h, double* rho);
 /* Device bytes held by the handle. */
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);
 
+/* HODLR geometry (Sec. 2.2, Fig. 2): *nblk blocks; each of the arrays (may be
+ * NULL, length >= *nblk when given) receives rows [r0, r1), columns [c0, c1)
+ * and level of every block.  Leaves are [j*leaf, (j+1)*leaf); the recursion
+ * splits ranges of leaves in halves.  HKBE_ERR_ARG for a dense handle. */
+int hkbe_get_blocks(const hkbe_t* h, int32_t* nblk, int32_t* r0, int32_t* r1, int32_t* c0,
+                    int32_t* c1, int32_t* level);
+
+/* Current epsilon-rank of every block and orbital pair of component `comp`
+ * (0 G^R, 1 G^<, 2 Sigma^R, 3 Sigma^<) of instance `inst`:
+ * ranks[nblk][N_o*N_o].  Also returns in *first_direct the first row not yet
+ * compressed (rows below it live in leaves and blocks). */
+int hkbe_get_ranks(hkbe_t* h, int inst, int comp, int32_t* ranks, int32_t* first_direct);
+
 /* Return to the state right after hkbe_bootstrap (current step = k), so the
  * time stepping can be run again from the same start (e.g. to time it, or
  * to propagate again after changing eps(t) for t > k with hkbe_set_hamiltonian).
@@ -169,7 +186,8 @@ enum {
   HKBE_PHASE_RHO = 7,     /* diagonal density matrix                           */
   HKBE_PHASE_BOOT = 8,    /* bootstrap square                                  */
   HKBE_PHASE_CTRL = 9,    /* convergence bookkeeping                           */
-  HKBE_NPHASE = 10
+  HKBE_PHASE_COMPRESS = 10, /* HODLR leaf copy + TSVD block updates (update_blocks) */
+  HKBE_NPHASE = 11
 };
 
 /* When on (nonzero), every kernel launch is bracketed by CUDA events on the

@@ -34,7 +34,8 @@ class HKBEError(RuntimeError):
 class hkbe_params(C.Structure):
     _fields_ = [("nt", C.c_int32), ("k", C.c_int32), ("nao", C.c_int32), ("xi", C.c_int32),
                 ("n_inst", C.c_int32), ("rho_mode", C.c_int32), ("precision", C.c_int32),
-                ("max_iter", C.c_int32), ("h", C.c_double), ("beta", C.c_double), ("tol", C.c_double)]
+                ("max_iter", C.c_int32), ("h", C.c_double), ("beta", C.c_double), ("tol", C.c_double),
+                ("svd_tol", C.c_double), ("leaf", C.c_int32), ("r_max", C.c_int32)]
 
 
 _lib = None
@@ -75,6 +76,8 @@ def load(build_if_missing: bool = True):
         "hkbe_get_density": ([H, _D], C.c_int),
         "hkbe_get_stats": ([H, C.POINTER(C.c_size_t)], C.c_int),
         "hkbe_rewind": ([H], C.c_int),
+        "hkbe_get_blocks": ([H, _I, _I, _I, _I, _I, _I], C.c_int),
+        "hkbe_get_ranks": ([H, C.c_int, C.c_int, _I, _I], C.c_int),
         "hkbe_set_profiling": ([H, C.c_int], C.c_int),
         "hkbe_get_timing": ([H, C.c_int, _D, C.POINTER(C.c_int64)], C.c_int),
         "hkbe_reset_counters": ([H], C.c_int),
@@ -214,11 +217,27 @@ def hkbe_rewind(h):
     _check(load().hkbe_rewind(h), h)
 
 
+def hkbe_get_blocks(h):
+    nb = np.zeros(1, np.int32)
+    _check(load().hkbe_get_blocks(h, _ip(nb), None, None, None, None, None), h)
+    n = int(nb[0])
+    a = [np.zeros(n, np.int32) for _ in range(5)]
+    _check(load().hkbe_get_blocks(h, _ip(nb), *[_ip(x) for x in a]), h)
+    return dict(zip(["r0", "r1", "c0", "c1", "level"], a))
+
+
+def hkbe_get_ranks(h, inst, comp, nblk, nao):
+    out = np.zeros(max(1, nblk * nao * nao), np.int32)
+    fd = np.zeros(1, np.int32)
+    _check(load().hkbe_get_ranks(h, inst, comp, _ip(out), _ip(fd)), h)
+    return out[:nblk * nao * nao].reshape(nblk, nao * nao), int(fd[0])
+
+
 def hkbe_set_profiling(h, on):
     _check(load().hkbe_set_profiling(h, int(bool(on))), h)
 
 
-PHASES = ["extrap", "sigma", "ret", "mixed", "vt", "src", "les", "rho", "boot", "ctrl"]
+PHASES = ["extrap", "sigma", "ret", "mixed", "vt", "src", "les", "rho", "boot", "ctrl", "compress"]
 
 
 def hkbe_get_timing(h, phase):
@@ -274,9 +293,10 @@ class Stepper:
     """Owns one handle; inputs are numpy arrays shaped as in include/hkbe.h."""
 
     def __init__(self, nt, h, k, beta, nao=1, n_inst=1, rho_mode=0, max_iter=50, tol=1e-12,
-                 precision=PREC_FP64, stream=None):
+                 precision=PREC_FP64, svd_tol=0.0, leaf=64, r_max=64, stream=None):
         self.p = hkbe_params(nt=nt, k=k, nao=nao, xi=-1, n_inst=n_inst, rho_mode=rho_mode,
-                             precision=precision, max_iter=max_iter, h=h, beta=beta, tol=tol)
+                             precision=precision, max_iter=max_iter, h=h, beta=beta, tol=tol,
+                             svd_tol=svd_tol, leaf=leaf, r_max=r_max)
         self.nao, self.n_inst, self.nt = nao, n_inst, nt
         self.h = hkbe_create(self.p, stream)
         self.r = 0

@@ -1,4 +1,5 @@
 // C ABI of the Kadanoff-Baym stepper (declared in include/hkbe.h).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -35,6 +36,12 @@ struct hkbe_s {
   std::vector<cudaEvent_t> event_pool;
   // bootstrap snapshot for hkbe_rewind (rows 0..k of every component)
   std::vector<double2> snap_gr, snap_gl, snap_sr, snap_sl, snap_tv, snap_stv;
+  // HODLR geometry (host copies) and row read-out buffers
+  bool hodlr = false;
+  std::vector<int> g_r0, g_r1, g_c0, g_c1, g_lvl, g_rowblk, g_colblk;
+  std::vector<long long> g_uoff, g_voff, g_leafoff;
+  double2 *rowbuf_r = nullptr, *rowbuf_l = nullptr;
+  int* status_dev = nullptr;
 };
 
 namespace {
@@ -103,6 +110,74 @@ int dalloc(hkbe_t* h, T** p, size_t count) {
 
 int no2(const hkbe_t* h) { return h->p.nao * h->p.nao; }
 
+// Offset (in matrices) of element (T, 0) of instance n in a two-time array.
+size_t row_off(const hkbe_t* h, int n, int T) {
+  const hk::Dev& d = h->d;
+  if (d.ring) return ((size_t)n * d.ring + (size_t)(T % d.ring)) * d.nt * no2(h);
+  return ((size_t)n * d.ntri + (size_t)T * (T + 1) / 2) * no2(h);
+}
+
+// HODLR partition (Sec. 2.2): leaves [j L, (j+1) L); a range of leaves [a, b)
+// is split at m = a + (b - a)/2 into the block rows [m L, b L) x cols [a L, m L)
+// and the two halves, recursively.
+void build_geometry(hkbe_t* h) {
+  const int nt = h->p.nt, L = h->p.leaf;
+  const int nleaf = (nt + L - 1) / L;
+  h->g_r0.clear(); h->g_r1.clear(); h->g_c0.clear(); h->g_c1.clear(); h->g_lvl.clear();
+  int maxdepth = 0;
+  struct Rng { int a, b, depth; };
+  std::vector<Rng> stack{{0, nleaf, 0}};
+  while (!stack.empty()) {
+    Rng g = stack.back();
+    stack.pop_back();
+    if (g.b - g.a <= 1) continue;
+    const int m = g.a + (g.b - g.a) / 2;
+    h->g_r0.push_back(m * L);
+    h->g_r1.push_back(std::min(g.b * L, nt));
+    h->g_c0.push_back(g.a * L);
+    h->g_c1.push_back(m * L);
+    h->g_lvl.push_back(g.depth);
+    maxdepth = std::max(maxdepth, g.depth);
+    stack.push_back({m, g.b, g.depth + 1});
+    stack.push_back({g.a, m, g.depth + 1});
+  }
+  const int nblk = (int)h->g_r0.size(), maxl = std::max(1, maxdepth + 1), n2 = no2(h);
+  h->g_rowblk.assign((size_t)nleaf * maxl, -1);
+  h->g_colblk.assign((size_t)nleaf * maxl, -1);
+  h->g_uoff.resize(nblk);
+  h->g_voff.resize(nblk);
+  long long uo = 0, vo = 0;
+  for (int b = 0; b < nblk; ++b) {
+    h->g_uoff[b] = uo;
+    h->g_voff[b] = vo;
+    uo += (long long)(h->g_r1[b] - h->g_r0[b]) * n2;
+    vo += (long long)(h->g_c1[b] - h->g_c0[b]) * n2;
+    for (int j = h->g_r0[b] / L; j * L < h->g_r1[b]; ++j) h->g_rowblk[(size_t)j * maxl + h->g_lvl[b]] = b;
+    for (int j = h->g_c0[b] / L; j * L < h->g_c1[b]; ++j) h->g_colblk[(size_t)j * maxl + h->g_lvl[b]] = b;
+  }
+  h->g_leafoff.resize(nleaf);
+  long long lo = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    h->g_leafoff[j] = lo;
+    const long long nj = std::min(L, nt - j * L);
+    lo += nj * (nj + 1) / 2;
+  }
+  hk::Dev& d = h->d;
+  d.L = L; d.nleaf = nleaf; d.nblk = nblk; d.maxl = maxl;
+  d.utot = uo; d.vtot = vo; d.leaftot = lo;
+}
+
+template <typename T>
+int upload(hkbe_t* h, const T** dst, const std::vector<T>& v) {
+  T* p = nullptr;
+  int rc = dalloc(h, &p, v.size());
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->s);
+  if (e != cudaSuccess) return fail(h, HKBE_ERR_CUDA, cudaGetErrorString(e));
+  *dst = p;
+  return HKBE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -121,6 +196,12 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   if (p->rho_mode != 0 && p->rho_mode != 1) return fail(nullptr, HKBE_ERR_ARG, "rho_mode must be 0 or 1");
   if (p->precision != HKBE_PREC_FP64) return fail(nullptr, HKBE_ERR_ARG, "unsupported precision");
   if (p->max_iter < 1) return fail(nullptr, HKBE_ERR_ARG, "max_iter must be >= 1");
+  if (p->svd_tol < 0) return fail(nullptr, HKBE_ERR_ARG, "svd_tol must be >= 0");
+  if (p->svd_tol > 0) {
+    if (p->leaf != 32 && p->leaf != 64) return fail(nullptr, HKBE_ERR_ARG, "leaf must be 32 or 64");
+    if (p->leaf <= 2 * p->k) return fail(nullptr, HKBE_ERR_ARG, "leaf must exceed 2k");
+    if (p->r_max < 1 || p->r_max > 128) return fail(nullptr, HKBE_ERR_ARG, "r_max must be in 1..128");
+  }
   hkbe_t* h = new hkbe_t();
   h->p = *p;
   h->s = (cudaStream_t)stream;
@@ -135,8 +216,46 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   std::memcpy(d.w.omega, w.omega, sizeof(w.omega));
   std::memcpy(d.w.D, w.D, sizeof(w.D));
   std::memcpy(d.w.I0, w.I0, sizeof(w.I0));
-  const size_t tri = (size_t)d.n_inst * d.ntri * d.no * d.no;
+  h->hodlr = p->svd_tol > 0;
+  size_t tri = (size_t)d.n_inst * d.ntri * d.no * d.no;
   int rc = HKBE_OK;
+  if (h->hodlr) {
+    build_geometry(h);
+    d.ring = p->leaf + 8;
+    d.cdir = 0;
+    d.rmax = p->r_max;
+    d.svd_tol = p->svd_tol;
+    tri = (size_t)d.n_inst * d.ring * d.nt * d.no * d.no;
+    const size_t n2 = (size_t)d.no * d.no, N = d.n_inst;
+    int ncolmax = 1;
+    for (size_t b = 0; b < h->g_c0.size(); ++b) ncolmax = std::max(ncolmax, h->g_c1[b] - h->g_c0[b]);
+    const int ldk = d.rmax + d.L;
+    d.tsvd_ws_per = 2LL * d.L * ncolmax + (long long)d.L * d.rmax + (long long)d.L * d.L + 2LL * ldk * ldk;
+    const size_t ctas = N * 4 * d.maxl * n2;
+    for (int X = 0; X < 4; ++X) {
+      if ((rc = dalloc(h, &d.hod[X].U, N * d.utot * d.rmax)) || (rc = dalloc(h, &d.hod[X].V, N * d.vtot * d.rmax)) ||
+          (rc = dalloc(h, &d.hod[X].S, N * d.nblk * n2 * d.rmax)) ||
+          (rc = dalloc(h, &d.hod[X].rank, N * d.nblk * n2)) || (rc = dalloc(h, &d.hod[X].leaf, N * d.leaftot * n2))) {
+        g_create_error = h->err;
+        hkbe_destroy(h);
+        return rc;
+      }
+    }
+    if ((rc = dalloc(h, &d.band, N * d.nt * d.k * n2)) ||
+        (rc = dalloc(h, &d.proj, N * d.no * d.maxl * n2 * d.rmax + N * d.nblk * n2 * d.no * 2 * d.rmax)) ||
+        (rc = dalloc(h, &d.tsvd_ws, ctas * d.tsvd_ws_per)) || (rc = dalloc(h, &h->status_dev, 2)) ||
+        (rc = dalloc(h, &h->rowbuf_r, (size_t)d.nt * n2)) || (rc = dalloc(h, &h->rowbuf_l, (size_t)d.nt * n2)) ||
+        (rc = upload(h, &d.b_r0, h->g_r0)) || (rc = upload(h, &d.b_r1, h->g_r1)) ||
+        (rc = upload(h, &d.b_c0, h->g_c0)) || (rc = upload(h, &d.b_c1, h->g_c1)) ||
+        (rc = upload(h, &d.b_lvl, h->g_lvl)) || (rc = upload(h, &d.b_uoff, h->g_uoff)) ||
+        (rc = upload(h, &d.b_voff, h->g_voff)) || (rc = upload(h, &d.leafoff, h->g_leafoff)) ||
+        (rc = upload(h, &d.rowblk, h->g_rowblk)) || (rc = upload(h, &d.colblk, h->g_colblk))) {
+      g_create_error = h->err;
+      hkbe_destroy(h);
+      return rc;
+    }
+    d.status = h->status_dev;
+  }
   if ((rc = dalloc(h, &d.GR, tri)) || (rc = dalloc(h, &d.GL, tri)) || (rc = dalloc(h, &d.SR, tri)) ||
       (rc = dalloc(h, &d.SL, tri)) ||
       (rc = dalloc(h, &d.eps, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
@@ -418,26 +537,36 @@ int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* 
   for (int t = 0; t <= d.k; ++t) HK_CUDA(h, hk::launch_sigma(d, t, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   drain(h);
-  // snapshot of the start square for hkbe_rewind
+  // snapshot of the start square for hkbe_rewind (rows 0..k of the two-time
+  // components, in either layout, and rows 0..k of the mixed components)
   {
     const int n2 = no2(h), k = d.k;
     const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
-    auto grab = [&](std::vector<double2>& dst, const double2* src, size_t per, size_t stride) -> cudaError_t {
-      dst.resize(per * d.n_inst);
+    auto grab = [&](std::vector<double2>& dst, const double2* src) -> cudaError_t {
+      dst.resize(sq * d.n_inst);
+      for (int n = 0; n < d.n_inst; ++n)
+        for (int t = 0; t <= k; ++t) {
+          cudaError_t e = cudaMemcpyAsync(dst.data() + sq * n + (size_t)t * (t + 1) / 2 * n2, src + row_off(h, n, t),
+                                          (size_t)(t + 1) * n2 * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
+          if (e != cudaSuccess) return e;
+        }
+      return cudaStreamSynchronize(h->s);
+    };
+    auto grab_tv = [&](std::vector<double2>& dst, const double2* src) -> cudaError_t {
+      dst.resize(tvn * d.n_inst);
       for (int n = 0; n < d.n_inst; ++n) {
-        cudaError_t e = cudaMemcpyAsync(dst.data() + per * n, src + stride * n, per * sizeof(double2),
-                                        cudaMemcpyDeviceToHost, h->s);
+        cudaError_t e = cudaMemcpyAsync(dst.data() + tvn * n, src + (size_t)n * d.nt * d.r * n2,
+                                        tvn * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
         if (e != cudaSuccess) return e;
       }
       return cudaStreamSynchronize(h->s);
     };
-    const size_t trs = (size_t)d.ntri * n2, tvs = (size_t)d.nt * d.r * n2;
-    HK_CUDA(h, grab(h->snap_gr, d.GR, sq, trs));
-    HK_CUDA(h, grab(h->snap_gl, d.GL, sq, trs));
-    HK_CUDA(h, grab(h->snap_sr, d.SR, sq, trs));
-    HK_CUDA(h, grab(h->snap_sl, d.SL, sq, trs));
-    HK_CUDA(h, grab(h->snap_tv, d.GTV, tvn, tvs));
-    HK_CUDA(h, grab(h->snap_stv, d.STV, tvn, tvs));
+    HK_CUDA(h, grab(h->snap_gr, d.GR));
+    HK_CUDA(h, grab(h->snap_gl, d.GL));
+    HK_CUDA(h, grab(h->snap_sr, d.SR));
+    HK_CUDA(h, grab(h->snap_sl, d.SL));
+    HK_CUDA(h, grab_tv(h->snap_tv, d.GTV));
+    HK_CUDA(h, grab_tv(h->snap_stv, d.STV));
   }
   h->cur = d.k;
   if (failed) return fail(h, HKBE_ERR_NOCONV, "bootstrap did not converge");
@@ -462,12 +591,21 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                    cudaError_t e;
                    if ((e = run_phase(h, HKBE_PHASE_SIGMA, 1, [&]() { return hk::launch_sigma(d, T, h->s); })))
                      return e;
-                   if ((e = run_phase(h, HKBE_PHASE_RET, 1, [&]() { return hk::launch_ret(d, T, h->s); }))) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_RET, 1, [&]() {
+                          return h->hodlr ? hk::launch_ret_h(d, T, h->s) : hk::launch_ret(d, T, h->s);
+                        })))
+                     return e;
                    if ((e = run_phase(h, HKBE_PHASE_MIXED, 1, [&]() { return hk::launch_mixed(d, T, h->s); })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_VT, 1, [&]() { return hk::launch_vt(d, T, h->s); }))) return e;
-                   if ((e = run_phase(h, HKBE_PHASE_SRC, 1, [&]() { return hk::launch_src(d, T, h->s); }))) return e;
-                   if ((e = run_phase(h, HKBE_PHASE_LES, 1, [&]() { return hk::launch_les(d, T, h->s); }))) return e;
+                   if ((e = run_phase(h, HKBE_PHASE_SRC, (h->hodlr && d.cdir > 0) ? 2 : 1, [&]() {
+                          return h->hodlr ? hk::launch_src_h(d, T, h->s) : hk::launch_src(d, T, h->s);
+                        })))
+                     return e;
+                   if ((e = run_phase(h, HKBE_PHASE_LES, 1, [&]() {
+                          return h->hodlr ? hk::launch_les_h(d, T, h->s) : hk::launch_les(d, T, h->s);
+                        })))
+                     return e;
                    if (d.rho_mode == 1 &&
                        (e = run_phase(h, HKBE_PHASE_RHO, 1, [&]() { return hk::launch_rho(d, T, h->s); })))
                      return e;
@@ -477,6 +615,19 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
     if (rc) return rc;
     any_failed |= failed;
     h->cur = T;
+    // update_blocks (Sec. 3.1): compress every whole leaf of rows older than k+1 steps
+    while (h->hodlr && d.cdir + d.L <= T - d.k) {
+      const int A = d.cdir;
+      HK_CUDA(h, run_phase(h, HKBE_PHASE_COMPRESS, 2, [&]() { return hk::launch_compress(d, A, d.L, h->s); }));
+      d.cdir += d.L;
+    }
+  }
+  if (h->hodlr) {
+    int st[2] = {0, 0};
+    HK_CUDA(h, cudaMemcpyAsync(st, h->status_dev, sizeof(st), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaStreamSynchronize(h->s));
+    drain(h);
+    if (st[0] > 0) return fail(h, HKBE_ERR_RANK, "a block's epsilon-rank exceeded r_max (truncated to r_max)");
   }
   if (any_failed) return fail(h, HKBE_ERR_NOCONV, "self-consistency did not converge within max_iter");
   return HKBE_OK;
@@ -488,11 +639,29 @@ int hkbe_current_step(const hkbe_t* h, int32_t* T) {
   return HKBE_OK;
 }
 
-static int copy_el(hkbe_t* h, const double2* base, int inst, int T, int t, double* out) {
-  const int n2 = no2(h);
-  const double2* src = base + ((size_t)inst * h->d.ntri + (size_t)T * (T + 1) / 2 + t) * n2;
-  HK_CUDA(h, cudaMemcpyAsync(out, src, n2 * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+// Copy rows T of G^R and G^< (t = 0..T) of an instance to host buffers
+// (either may be NULL); compressed rows are reconstructed on the device.
+static int fetch_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
+  const size_t cnt = (size_t)(T + 1) * no2(h);
+  const hk::Dev& d = h->d;
+  if (h->hodlr && T < d.cdir) {
+    HK_CUDA(h, hk::launch_row_out(d, inst, T, gr ? h->rowbuf_r : nullptr, gl ? h->rowbuf_l : nullptr, h->s));
+    if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, h->rowbuf_r, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+    if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, h->rowbuf_l, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  } else {
+    if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, d.GR + row_off(h, inst, T), cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+    if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, d.GL + row_off(h, inst, T), cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+static int copy_el(hkbe_t* h, int X, int inst, int T, int t, double* out) {
+  const int n2 = no2(h);
+  std::vector<double> row((size_t)(T + 1) * n2 * 2);
+  int rc = fetch_row(h, inst, T, X == 0 ? row.data() : nullptr, X == 1 ? row.data() : nullptr);
+  if (rc) return rc;
+  std::memcpy(out, row.data() + (size_t)t * n2 * 2, n2 * 2 * sizeof(double));
   return HKBE_OK;
 }
 
@@ -500,17 +669,17 @@ int hkbe_get_ret(hkbe_t* h, int inst, int t, int tp, double* out) {
   if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
   if (tp < 0 || tp > t || t > h->cur) return fail(h, HKBE_ERR_RANGE, "need 0 <= t' <= t <= current step");
-  return copy_el(h, h->d.GR, inst, t, tp, out);
+  return copy_el(h, 0, inst, t, tp, out);
 }
 
 int hkbe_get_les(hkbe_t* h, int inst, int t, int tp, double* out) {
   if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
   if (t < 0 || tp < 0 || t > h->cur || tp > h->cur) return fail(h, HKBE_ERR_RANGE, "times must be in 0..current step");
-  if (t <= tp) return copy_el(h, h->d.GL, inst, tp, t, out);
+  if (t <= tp) return copy_el(h, 1, inst, tp, t, out);
   const int no = h->d.no;
   std::vector<double> tmp(2 * no * no);
-  int rc = copy_el(h, h->d.GL, inst, t, tp, tmp.data());
+  int rc = copy_el(h, 1, inst, t, tp, tmp.data());
   if (rc) return rc;
   for (int x = 0; x < no; ++x)
     for (int y = 0; y < no; ++y) {
@@ -536,11 +705,31 @@ int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
   if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
   if (T < 0 || T > h->cur) return fail(h, HKBE_ERR_RANGE, "T must be in 0..current step");
-  const size_t cnt = (size_t)(T + 1) * no2(h);
-  const size_t off = ((size_t)inst * h->d.ntri + (size_t)T * (T + 1) / 2) * no2(h);
-  if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, h->d.GR + off, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
-  if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, h->d.GL + off, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  return fetch_row(h, inst, T, gr, gl);
+}
+
+int hkbe_get_blocks(const hkbe_t* h, int32_t* nblk, int32_t* r0, int32_t* r1, int32_t* c0, int32_t* c1,
+                    int32_t* level) {
+  if (!h || !nblk || !h->hodlr) return HKBE_ERR_ARG;
+  *nblk = (int32_t)h->g_r0.size();
+  for (size_t b = 0; b < h->g_r0.size(); ++b) {
+    if (r0) r0[b] = h->g_r0[b];
+    if (r1) r1[b] = h->g_r1[b];
+    if (c0) c0[b] = h->g_c0[b];
+    if (c1) c1[b] = h->g_c1[b];
+    if (level) level[b] = h->g_lvl[b];
+  }
+  return HKBE_OK;
+}
+
+int hkbe_get_ranks(hkbe_t* h, int inst, int comp, int32_t* ranks, int32_t* first_direct) {
+  if (!h || !h->hodlr) return fail(h, HKBE_ERR_ARG, "not a HODLR handle");
+  if (inst < 0 || inst >= h->d.n_inst || comp < 0 || comp > 3) return fail(h, HKBE_ERR_ARG, "bad instance or component");
+  const size_t cnt = (size_t)h->d.nblk * no2(h);
+  if (ranks)
+    HK_CUDA(h, cudaMemcpyAsync(ranks, h->d.hod[comp].rank + (size_t)inst * cnt, cnt * sizeof(int), cudaMemcpyDeviceToHost, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
+  if (first_direct) *first_direct = h->d.cdir;
   return HKBE_OK;
 }
 
@@ -551,7 +740,7 @@ int hkbe_get_density(hkbe_t* h, double* rho) {
   std::vector<double> tmp(2 * n2);
   for (int n = 0; n < h->d.n_inst; ++n)
     for (int t = 0; t <= T; ++t) {
-      int rc = copy_el(h, h->d.GL, n, t, t, tmp.data());
+      int rc = copy_el(h, 1, n, t, t, tmp.data());
       if (rc) return rc;
       double* o = rho + (((size_t)n * (T + 1) + t) * n2) * 2;
       for (int q = 0; q < n2; ++q) {  // rho = xi i G^<
@@ -575,21 +764,34 @@ int hkbe_rewind(hkbe_t* h) {
   Dev& d = h->d;
   const int n2 = no2(h), k = d.k;
   const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
-  const size_t trs = (size_t)d.ntri * n2, tvs = (size_t)d.nt * d.r * n2;
-  auto put = [&](const std::vector<double2>& src, double2* dst, size_t per, size_t stride) -> cudaError_t {
+  auto put = [&](const std::vector<double2>& src, double2* dst) -> cudaError_t {
+    for (int n = 0; n < d.n_inst; ++n)
+      for (int t = 0; t <= k; ++t) {
+        cudaError_t e = cudaMemcpyAsync(dst + row_off(h, n, t), src.data() + sq * n + (size_t)t * (t + 1) / 2 * n2,
+                                        (size_t)(t + 1) * n2 * sizeof(double2), cudaMemcpyHostToDevice, h->s);
+        if (e != cudaSuccess) return e;
+      }
+    return cudaSuccess;
+  };
+  auto put_tv = [&](const std::vector<double2>& src, double2* dst) -> cudaError_t {
     for (int n = 0; n < d.n_inst; ++n) {
-      cudaError_t e = cudaMemcpyAsync(dst + stride * n, src.data() + per * n, per * sizeof(double2),
+      cudaError_t e = cudaMemcpyAsync(dst + (size_t)n * d.nt * d.r * n2, src.data() + tvn * n, tvn * sizeof(double2),
                                       cudaMemcpyHostToDevice, h->s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
-  HK_CUDA(h, put(h->snap_gr, d.GR, sq, trs));
-  HK_CUDA(h, put(h->snap_gl, d.GL, sq, trs));
-  HK_CUDA(h, put(h->snap_sr, d.SR, sq, trs));
-  HK_CUDA(h, put(h->snap_sl, d.SL, sq, trs));
-  HK_CUDA(h, put(h->snap_tv, d.GTV, tvn, tvs));
-  HK_CUDA(h, put(h->snap_stv, d.STV, tvn, tvs));
+  HK_CUDA(h, put(h->snap_gr, d.GR));
+  HK_CUDA(h, put(h->snap_gl, d.GL));
+  HK_CUDA(h, put(h->snap_sr, d.SR));
+  HK_CUDA(h, put(h->snap_sl, d.SL));
+  HK_CUDA(h, put_tv(h->snap_tv, d.GTV));
+  HK_CUDA(h, put_tv(h->snap_stv, d.STV));
+  if (h->hodlr) {
+    d.cdir = 0;
+    for (int X = 0; X < 4; ++X)
+      HK_CUDA(h, cudaMemsetAsync(d.hod[X].rank, 0, (size_t)d.n_inst * d.nblk * n2 * sizeof(int), h->s));
+  }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->cur = k;
   return HKBE_OK;

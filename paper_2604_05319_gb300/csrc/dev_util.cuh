@@ -1,0 +1,147 @@
+// Device helpers shared by the dense and the compressed (HODLR) kernels:
+// indexing, Appendix A integration rule, warp reductions, small solves.
+#pragma once
+#include "common.cuh"
+#include "state.h"
+
+namespace hk {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ long long tri(int T) { return (long long)T * (T + 1) / 2; }
+
+// Row T of a two-time component: the dense lower triangle, or (compressed
+// storage) the ring of uncompressed rows, slot T mod ring.
+template <int NO>
+__device__ __forceinline__ double2* el(double2* base, const Dev& d, int n, int T, int t) {
+  if (d.ring) return base + (((long long)n * d.ring + (T % d.ring)) * d.nt + t) * (NO * NO);
+  return base + ((long long)n * d.ntri + tri(T) + t) * (NO * NO);
+}
+template <int NO>
+__device__ __forceinline__ double2* tv(double2* base, const Dev& d, int n, int T, int i) {
+  return base + (((long long)n * d.nt + T) * d.r + i) * (NO * NO);
+}
+template <int NO>
+__device__ __forceinline__ double2* epsp(const Dev& d, int n, int t) {  // eps(t), t >= -1
+  return d.eps + ((long long)n * (d.nt + 1) + (t + 1)) * (NO * NO);
+}
+
+__device__ __forceinline__ double rule_w(const DevW& w, int n, int l) {
+  const int k = w.k;
+  if (n <= 0) return 0.0;
+  if (n <= k) return (l >= 0 && l <= k) ? w.I0[n][l] : 0.0;
+  if (n < 2 * k + 1) {
+    double s = 0.0;
+    if (l >= 0 && l <= k) s += w.I0[n - k][l];
+    if (l >= n - k && l <= n) s += w.I0[k][l - (n - k)];
+    return s;
+  }
+  if (l < 0 || l > n) return 0.0;
+  if (l <= k) return w.omega[l];
+  if (l >= n - k) return w.omega[n - l];
+  return 1.0;
+}
+
+__device__ __forceinline__ zd wshfl(zd v, int off) {
+  return zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));
+}
+template <int L>
+__device__ __forceinline__ void warp_sum(zd (&v)[L]) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] += wshfl(v[i], off);
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// Sigma^R(a, b) continued above the diagonal: -[Sigma^R(b, a)]^dagger for a < b.
+template <int NO>
+__device__ __forceinline__ zd srx(const Dev& d, int n, int a, int b, int x, int y) {
+  if (a >= b) return ld(el<NO>(d.SR, d, n, a, b) + x * NO + y);
+  return -ld(el<NO>(d.SR, d, n, b, a) + y * NO + x).conj();
+}
+// Sigma^<(t, l) anywhere (Eq. GLantiHerm)
+template <int NO>
+__device__ __forceinline__ zd sless(const Dev& d, int n, int t, int l, int x, int y) {
+  if (t <= l) return ld(el<NO>(d.SL, d, n, l, t) + x * NO + y);
+  return -ld(el<NO>(d.SL, d, n, t, l) + y * NO + x).conj();
+}
+
+// ---------------------------------------------------------------------------
+// Warp-parallel dense solve A X = B (n <= 32, nrhs <= 32), A and B in shared
+// memory, LU with partial pivoting; lane r owns row r during elimination.
+// With nrhs = 0 it only factors (L below the diagonal, row swaps in piv).
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ void warp_lu_solve(int n, zd* A, zd* B, int nrhs, int* piv) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < n; ++c) {
+    double v = (lane >= c && lane < n) ? A[lane * n + c].abs2() : -1.0;
+    int p = lane;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      double v2 = __shfl_xor_sync(FULL, v, off);
+      int p2 = __shfl_xor_sync(FULL, p, off);
+      if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+    }
+    if (piv && lane == 0) piv[c] = p;
+    if (p != c) {
+      for (int j = lane; j < n; j += 32) { zd t = A[c * n + j]; A[c * n + j] = A[p * n + j]; A[p * n + j] = t; }
+      for (int j = lane; j < nrhs; j += 32) { zd t = B[c * nrhs + j]; B[c * nrhs + j] = B[p * nrhs + j]; B[p * nrhs + j] = t; }
+    }
+    __syncwarp();
+    if (lane > c && lane < n) {
+      zd f = cdiv(A[lane * n + c], A[c * n + c]);
+      A[lane * n + c] = f;
+      for (int j = c + 1; j < n; ++j) A[lane * n + j] -= f * A[c * n + j];
+      for (int j = 0; j < nrhs; ++j) B[lane * nrhs + j] -= f * B[c * nrhs + j];
+    }
+    __syncwarp();
+  }
+  for (int j = lane; j < nrhs; j += 32)
+    for (int c = n - 1; c >= 0; --c) {
+      zd s = B[c * nrhs + j];
+      for (int m = c + 1; m < n; ++m) s -= A[c * n + m] * B[m * nrhs + j];
+      B[c * nrhs + j] = cdiv(s, A[c * n + c]);
+    }
+  __syncwarp();
+}
+// Solve with a factor from warp_lu_solve(nrhs = 0) for one right-hand side b.
+__device__ __forceinline__ void lu_apply(int n, const zd* A, const int* piv, zd* b) {
+  for (int c = 0; c < n; ++c)
+    if (piv[c] != c) { zd t = b[c]; b[c] = b[piv[c]]; b[piv[c]] = t; }
+  for (int c = 0; c < n; ++c)
+    for (int r = c + 1; r < n; ++r) b[r] -= A[r * n + c] * b[c];
+  for (int c = n - 1; c >= 0; --c) {
+    zd s = b[c];
+    for (int m = c + 1; m < n; ++m) s -= A[c * n + m] * b[m];
+    b[c] = cdiv(s, A[c * n + c]);
+  }
+}
+
+// small vector solves: y M = r (row vector) and M x = r (column vector)
+template <int NO>
+__device__ void solve_row(const M<NO>& Mm, const zd* r, zd* y) {
+  M<NO> B = M<NO>::zero();
+#pragma unroll
+  for (int j = 0; j < NO; ++j) B.a[0][j] = r[j];
+  M<NO> X = solve_right<NO>(Mm, B);
+#pragma unroll
+  for (int j = 0; j < NO; ++j) y[j] = X.a[0][j];
+}
+template <int NO>
+__device__ void solve_col(const M<NO>& Mm, const zd* r, zd* x) {
+  M<NO> B = M<NO>::zero();
+#pragma unroll
+  for (int j = 0; j < NO; ++j) B.a[j][0] = r[j];
+  M<NO> X = solve_left<NO>(Mm, B);
+#pragma unroll
+  for (int j = 0; j < NO; ++j) x[j] = X.a[j][0];
+}
+
+__device__ __forceinline__ double fermi(double e, double beta) { return 0.5 * (1.0 - tanh(0.5 * beta * e)); }
+
+}  // namespace hk

@@ -1,0 +1,1116 @@
+// Compressed (HODLR) form of the time step (Sec. 2.2, Fig. 2): the two-time
+// components are stored as dense leaf triangles on the diagonal, U S V^dagger
+// blocks below them (one scalar TSVD per orbital pair, Sec. 2.3), and a ring
+// of the most recent uncompressed rows (the red and green regions: the
+// current row and the rows not yet old enough to compress).
+//
+// History integrals over compressed rows use block projections:
+//   retarded row (columns t' of Sigma^R):  pi_B = sum_s y(s) U_B(s,:) S_B,
+//     contribution to t' = pi_B . conj(V_B(t',:))
+//   lesser column (rows t of Sigma^R):     rho_B = S_B sum_l w_l conj(V_B(l,:)) x(l),
+//     contribution to t = U_B(t,:) . rho_B
+//   lesser source (Sigma^<, both triangles): each block is used as B and -B^dagger.
+// Gregory weights differ from 1 only near the ends (App. A): lower-end weights
+// omega_l, l <= k, are folded into the projections; near-diagonal block entries
+// (|t - t'| <= k) get an explicit (w - 1) correction from a dense band copy.
+//
+// update_blocks (Sec. 3.1): whenever a whole leaf of rows is older than k+1
+// steps, its rows are appended to every block containing them by a batched
+// Brand update: P = R V, E = R - P V^dagger (projected twice), an orthonormal
+// basis Q of E's rows by two-pass Gram-Schmidt, the core
+// K = [[S, 0], [P, C]] (C = E Q^dagger), its SVD by one-sided Jacobi, truncation
+// of singular values below the SVD tolerance (Sec. 2.2), and rotation of U, V.
+#include "dev_util.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr int CHH = 32;     // sweep sub-chunk (the leaf size is a multiple)
+constexpr int NWH = 8;      // warps per sweep CTA
+
+__device__ __forceinline__ double2* ringX(const Dev& d, int X) {
+  return X == 0 ? d.GR : X == 1 ? d.GL : X == 2 ? d.SR : d.SL;
+}
+template <int NO>
+__device__ __forceinline__ double2* Up(const Dev& d, int X, int n, int b, int p) {
+  const long long rows = d.b_r1[b] - d.b_r0[b];
+  return d.hod[X].U + ((long long)n * d.utot + d.b_uoff[b] + p * rows) * d.rmax;
+}
+template <int NO>
+__device__ __forceinline__ double2* Vp(const Dev& d, int X, int n, int b, int p) {
+  const long long cols = d.b_c1[b] - d.b_c0[b];
+  return d.hod[X].V + ((long long)n * d.vtot + d.b_voff[b] + p * cols) * d.rmax;
+}
+template <int NO>
+__device__ __forceinline__ double* Sp(const Dev& d, int X, int n, int b, int p) {
+  return d.hod[X].S + (((long long)n * d.nblk + b) * (NO * NO) + p) * d.rmax;
+}
+template <int NO>
+__device__ __forceinline__ int* Rk(const Dev& d, int X, int n, int b, int p) {
+  return d.hod[X].rank + ((long long)n * d.nblk + b) * (NO * NO) + p;
+}
+// element (t, l) of leaf j of component X (t, l inside the leaf, l <= t)
+template <int NO>
+__device__ __forceinline__ double2* Lf(const Dev& d, int X, int n, int j, int t, int l) {
+  const int A = j * d.L;
+  return d.hod[X].leaf + ((long long)n * d.leaftot + d.leafoff[j] + tri(t - A) + (l - A)) * (NO * NO);
+}
+template <int NO>
+__device__ __forceinline__ double2* Bd(const Dev& d, int n, int t, int dd) {
+  return d.band + (((long long)n * d.nt + t) * d.k + (dd - 1)) * (NO * NO);
+}
+// sweep projection slots: [n][row/col][maxl][no2][rmax]
+template <int NO>
+__device__ __forceinline__ double2* Pj(const Dev& d, int n, int which, int lv, int p) {
+  return d.proj + ((((long long)n * NO + which) * d.maxl + lv) * (NO * NO) + p) * d.rmax;
+}
+
+// Sigma^R(t, l), l <= t, from whichever storage holds it.
+template <int NO>
+__device__ zd sr_any(const Dev& d, int n, int t, int l, int x, int y) {
+  if (t >= d.cdir) return ld(el<NO>(d.SR, d, n, t, l) + x * NO + y);
+  const int jt = t / d.L, jl = l / d.L;
+  if (jt == jl) return ld(Lf<NO>(d, 2, n, jt, t, l) + x * NO + y);
+  for (int lv = 0; lv < d.maxl; ++lv) {
+    const int b = d.rowblk[jt * d.maxl + lv];
+    if (b < 0 || l < d.b_c0[b] || l >= d.b_c1[b]) continue;
+    const int p = x * NO + y, rk = *Rk<NO>(d, 2, n, b, p);
+    const double2* U = Up<NO>(d, 2, n, b, p) + (long long)(t - d.b_r0[b]) * d.rmax;
+    const double2* V = Vp<NO>(d, 2, n, b, p) + (long long)(l - d.b_c0[b]) * d.rmax;
+    const double* S = Sp<NO>(d, 2, n, b, p);
+    zd s = zd();
+    for (int q = 0; q < rk; ++q) s += ld(U + q) * ld(V + q).conj() * S[q];
+    return s;
+  }
+  return zd();
+}
+template <int NO>
+__device__ zd srx_any(const Dev& d, int n, int a, int b, int x, int y) {
+  if (a >= b) return sr_any<NO>(d, n, a, b, x, y);
+  return -sr_any<NO>(d, n, b, a, y, x).conj();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Retarded row with compressed Sigma^R (Eq. KBER); one CTA per (row, instance)
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_ret_h(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, irow = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k, c = d.cdir, L = d.L;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd red[NWH][CHH][NO];
+  __shared__ zd ych[CHH][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* rowp = el<NO>(d.GR, d, n, T, 0);
+  auto yp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };   // G^R(T, t')
+  double myerr = 0.0;
+  // ---- start block s = 1..k (rows T-k..T, uncompressed) ----
+  const int ns = k * NO;
+  if (warp == 0) {
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;
+      const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
+      zd v = srx<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
+      if (m == j) v += zd(0, W.D[s][l] / h);
+      if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
+      sA[row * ns + col] = v;
+    }
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      zd cc = srx<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
+      if (irow == j) cc += zd(0, W.D[s][0] / h);
+      sB[row] = zd(0, 1) * cc;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, sB, 1, nullptr);
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      double2* p = yp(T - s) + j;
+      myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
+      st(p, sB[row]);
+    }
+    if (lane == 0) {
+      double2* p = yp(T);
+      for (int j = 0; j < NO; ++j) {
+        zd v = (j == irow) ? zd(0, -1) : zd();
+        myerr = fmax(myerr, sqrt((ld(p + j) - v).abs2()));
+        st(p + j, v);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- uncompressed columns t' in [c, T-k-1], chunks of 32 in s = T - t' ----
+  for (int s0 = k + 1; s0 <= T - c; s0 += CHH) {
+    const int cn = min(CHH, T - c + 1 - s0);
+    {
+      zd acc[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) acc[j] = zd();
+      const int s = s0 + lane;
+      if (lane < cn) {
+        for (int l = warp; l < s0; l += NWH) {
+          const double wl = rule_w(W, s, l);
+          const double2* yl = yp(T - l);
+          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ld(yl + m) * wl;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      zd far[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        far[j] = zd();
+        for (int w2 = 0; w2 < NWH; ++w2) far[j] += red[w2][lane][j];
+        far[j] = far[j] * h;
+      }
+      for (int sl = 0; sl < cn; ++sl) {
+        const int s = s0 + sl;
+        zd part[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) part[j] = zd();
+        if (lane < sl) {
+          const int l = s0 + lane;
+          const double wl = h * rule_w(W, s, l);
+          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ych[lane][m] * wl;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
+          }
+        }
+        if (lane >= 1 && lane <= k) {
+          const int sj = s - lane;
+          const zd cc = zd(0, -W.a[lane] / h);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) part[m] += cc * ((sj >= s0) ? ych[sj - s0][m] : ld(yp(T - sj) + m));
+        }
+        warp_sum<NO>(part);
+        if (lane == sl) {
+          zd rhs[NO], y[NO];
+#pragma unroll
+          for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
+          const double ws = h * rule_w(W, s, s);
+          const double2* sd = el<NO>(d.SR, d, n, T - s, T - s);
+          const double2* ep = epsp<NO>(d, n, T - s);
+          M<NO> Mm;
+#pragma unroll
+          for (int x = 0; x < NO; ++x)
+#pragma unroll
+            for (int y2 = 0; y2 < NO; ++y2)
+              Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
+          solve_row<NO>(Mm, rhs, y);
+          double2* p = yp(T - s);
+#pragma unroll
+          for (int j = 0; j < NO; ++j) {
+            myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
+            st(p + j, y[j]);
+            ych[sl][j] = y[j];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  // ---- compressed columns t' < c, leaf by leaf (descending) ----
+  for (int jl = c / L - 1; jl >= 0; --jl) {
+    const int A = jl * L, E = A + L;
+    // projections of the blocks whose column range ends at E
+    for (int lv = 0; lv < d.maxl; ++lv) {
+      const int b = d.colblk[jl * d.maxl + lv];
+      if (b < 0 || d.b_c1[b] != E) continue;
+      const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c);
+      for (int idx = tid; idx < NO2 * d.rmax; idx += blockDim.x) {
+        const int p = idx / d.rmax, q = idx % d.rmax, m = p / NO;
+        const int rk = *Rk<NO>(d, 2, n, b, p);
+        zd acc = zd();
+        if (q < rk && r0 < rl) {
+          const double2* U = Up<NO>(d, 2, n, b, p) + q;
+          for (int s = r0; s < rl; ++s) acc = cfma(ld(yp(s) + m), ld(U + (long long)(s - r0) * d.rmax), acc);
+          acc = acc * Sp<NO>(d, 2, n, b, p)[q];
+        }
+        st(Pj<NO>(d, n, irow, lv, p) + q, acc);
+      }
+    }
+    __syncthreads();
+    for (int bsub = E; bsub > A; bsub -= CHH) {
+      const int a0 = bsub - CHH;
+      const int tp = a0 + lane;  // this lane's column
+      zd acc[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) acc[j] = zd();
+      // uncompressed rows s in [c, T]
+      for (int s = c + warp; s <= T; s += NWH) {
+        const double ws = rule_w(W, T - tp, T - s);
+        const double2* yl = yp(s);
+        const double2* sr = el<NO>(d.SR, d, n, s, tp);
+#pragma unroll
+        for (int m = 0; m < NO; ++m) {
+          const zd ym = ld(yl + m) * ws;
+#pragma unroll
+          for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+        }
+      }
+      // rows of this leaf above the sub-chunk, s in [bsub, E)
+      for (int s = bsub + warp; s < E; s += NWH) {
+        const double ws = rule_w(W, T - tp, T - s);
+        const double2* yl = yp(s);
+        const double2* sr = Lf<NO>(d, 2, n, jl, s, tp);
+#pragma unroll
+        for (int m = 0; m < NO; ++m) {
+          const zd ym = ld(yl + m) * ws;
+#pragma unroll
+          for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+        }
+      }
+      // compressed blocks below the leaf (weight 1), one warp per level
+      for (int lv = warp; lv < d.maxl; lv += NWH) {
+        const int b = d.colblk[jl * d.maxl + lv];
+        if (b < 0 || d.b_r0[b] >= c) continue;
+        const int c0 = d.b_c0[b];
+#pragma unroll
+        for (int p = 0; p < NO2; ++p) {
+          const int m = p / NO, j = p % NO;
+          (void)m;
+          const int rk = *Rk<NO>(d, 2, n, b, p);
+          const double2* V = Vp<NO>(d, 2, n, b, p) + (long long)(tp - c0) * d.rmax;
+          const double2* P = Pj<NO>(d, n, irow, lv, p);
+          zd s = zd();
+          for (int q = 0; q < rk; ++q) s = cfma(ld(P + q), ld(V + q).conj(), s);
+          acc[j] += s;
+        }
+      }
+      // near-diagonal block entries: (w - 1) y(s) Sigma^R(s, t') for s in [E, t'+k], s < c
+      if (warp == NWH - 1) {
+        for (int s = E; s <= tp + k && s < c; ++s) {
+          const double ws = rule_w(W, T - tp, T - s) - 1.0;
+          const double2* bd = Bd<NO>(d, n, s, s - tp);
+          const double2* yl = yp(s);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ld(yl + m) * ws;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(bd + m * NO + j), acc[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
+      __syncthreads();
+      if (warp == 0) {
+        zd far[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          far[j] = zd();
+          for (int w2 = 0; w2 < NWH; ++w2) far[j] += red[w2][lane][j];
+          far[j] = far[j] * h;
+        }
+        for (int tl = CHH - 1; tl >= 0; --tl) {
+          const int t0 = a0 + tl;
+          zd part[NO];
+#pragma unroll
+          for (int j = 0; j < NO; ++j) part[j] = zd();
+          const int s = t0 + 1 + lane;  // near field, rows s in (t0, bsub)
+          if (s < bsub) {
+            const double wl = h * rule_w(W, T - t0, T - s);
+            const double2* sr = Lf<NO>(d, 2, n, jl, s, t0);
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              const zd ym = ych[s - a0][m] * wl;
+#pragma unroll
+              for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
+            }
+          }
+          if (lane >= 1 && lane <= k) {
+            const int sj = t0 + lane;
+            const zd cc = zd(0, -W.a[lane] / h);
+#pragma unroll
+            for (int m = 0; m < NO; ++m) part[m] += cc * ((sj < bsub) ? ych[sj - a0][m] : ld(yp(sj) + m));
+          }
+          warp_sum<NO>(part);
+          if (lane == tl) {
+            zd rhs[NO], y[NO];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
+            const double ws = h * rule_w(W, T - t0, T - t0);
+            const double2* sd = Lf<NO>(d, 2, n, jl, t0, t0);
+            const double2* ep = epsp<NO>(d, n, t0);
+            M<NO> Mm;
+#pragma unroll
+            for (int x = 0; x < NO; ++x)
+#pragma unroll
+              for (int y2 = 0; y2 < NO; ++y2)
+                Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
+            solve_row<NO>(Mm, rhs, y);
+            double2* p = yp(t0);
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+              myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
+              st(p + j, y[j]);
+              ych[tl][j] = y[j];
+            }
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+    }
+  }
+  myerr = warp_max(myerr);
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Lesser column with compressed Sigma^R (Eq. KBEL); one CTA per (column, instance)
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_les_h(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, jc = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k, c = d.cdir, L = d.L;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd farsh[CHH][NO];
+  __shared__ zd xch[CHH][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* colp = el<NO>(d.GL, d, n, T, 0);
+  auto xp = [&](int t) { return colp + (long long)t * NO2; };   // [m*NO + jc]
+  const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
+  double myerr = 0.0;
+  const int last = (d.rho_mode == 1) ? T - 1 : T;
+  // Sigma^R(t, l) anywhere in the stored triangle, and its continuation
+  auto S_at = [&](int t, int l, int x, int y) -> zd { return srx_any<NO>(d, n, t, l, x, y); };
+  if (warp == 0) {
+    if (lane < NO) {
+      const int m = lane;
+      zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
+      double2* p = xp(0) + m * NO + jc;
+      myerr = fmax(myerr, sqrt((v - ld(p)).abs2()));
+      st(p, v);
+    }
+    __syncwarp();
+    const int ns = k * NO;
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;
+      const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
+      zd v = S_at(t, l, m, y) * (-h * W.I0[t][l]);
+      if (m == y) v += zd(0, W.D[t][l] / h);
+      if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
+      sA[row * ns + col] = v;
+    }
+    for (int row = lane; row < ns; row += 32) {
+      const int t = row / NO + 1, m = row % NO;
+      zd bb = ld(qs + t * NO2 + m * NO + jc);
+      for (int y = 0; y < NO; ++y) {
+        zd cc = S_at(t, 0, m, y) * (-h * W.I0[t][0]);
+        if (m == y) cc += zd(0, W.D[t][0] / h);
+        bb -= cc * ld(xp(0) + y * NO + jc);
+      }
+      sB[row] = bb;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, sB, 1, nullptr);
+    for (int row = lane; row < ns; row += 32) {
+      const int t = row / NO + 1, m = row % NO;
+      if (t > last) continue;
+      double2* p = xp(t) + m * NO + jc;
+      myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
+      st(p, sB[row]);
+    }
+  }
+  __syncthreads();
+  for (int t0 = k + 1; t0 <= last;) {
+    const int t1 = min((t0 / CHH + 1) * CHH, last + 1);
+    const int cn = t1 - t0;
+    const int jl = t0 / L, A = jl * L;
+    const bool comp = (t0 < c);
+    if (comp && t0 == A && jl > 0) {
+      // rho projections of the blocks whose rows start at A
+      for (int lv = 0; lv < d.maxl; ++lv) {
+        const int b = d.rowblk[jl * d.maxl + lv];
+        if (b < 0 || d.b_r0[b] != A) continue;
+        const int c0 = d.b_c0[b], c1 = d.b_c1[b];
+        for (int idx = tid; idx < NO2 * d.rmax; idx += blockDim.x) {
+          const int p = idx / d.rmax, q = idx % d.rmax, nn = p % NO;
+          const int rk = *Rk<NO>(d, 2, n, b, p);
+          zd acc = zd();
+          if (q < rk) {
+            const double2* V = Vp<NO>(d, 2, n, b, p) + q;
+            for (int l = c0; l < c1; ++l) {
+              const double wl = (l <= k) ? W.omega[l] : 1.0;
+              acc = cfma(ld(V + (long long)(l - c0) * d.rmax).conj() * wl, ld(xp(l) + nn * NO + jc), acc);
+            }
+            acc = acc * Sp<NO>(d, 2, n, b, p)[q];
+          }
+          st(Pj<NO>(d, n, jc, lv, p) + q, acc);
+        }
+      }
+      __syncthreads();
+    }
+    // far field: warp per row t, lanes over l
+    for (int tl = warp; tl < cn; tl += NWH) {
+      const int t = t0 + tl;
+      zd acc[NO];
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[m] = zd();
+      if (!comp) {
+        const double2* srow = el<NO>(d.SR, d, n, t, 0);
+        for (int l = lane; l < t0; l += 32) {
+          const double wl = rule_w(W, t, l);
+          const double2* sr = srow + (long long)l * NO2;
+#pragma unroll
+          for (int y = 0; y < NO; ++y) {
+            const zd xy = ld(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
+          }
+        }
+      } else {
+        for (int l = A + lane; l < t0; l += 32) {  // same leaf
+          const double wl = rule_w(W, t, l);
+          const double2* sr = Lf<NO>(d, 2, n, jl, t, l);
+#pragma unroll
+          for (int y = 0; y < NO; ++y) {
+            const zd xy = ld(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
+          }
+        }
+        for (int lv = 0; lv < d.maxl; ++lv) {  // blocks left of the leaf
+          const int b = d.rowblk[jl * d.maxl + lv];
+          if (b < 0) continue;
+          const int r0 = d.b_r0[b];
+#pragma unroll
+          for (int p = 0; p < NO2; ++p) {
+            const int m = p / NO;
+            const int rk = *Rk<NO>(d, 2, n, b, p);
+            const double2* U = Up<NO>(d, 2, n, b, p) + (long long)(t - r0) * d.rmax;
+            const double2* P = Pj<NO>(d, n, jc, lv, p);
+            for (int q = lane; q < rk; q += 32) acc[m] = cfma(ld(U + q), ld(P + q), acc[m]);
+          }
+        }
+        for (int l = max(t - k, 0) + lane; l < A; l += 32) {  // near-diagonal block entries
+          const double wl = rule_w(W, t, l) - 1.0;
+          const double2* bd = Bd<NO>(d, n, t, t - l);
+#pragma unroll
+          for (int y = 0; y < NO; ++y) {
+            const zd xy = ld(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(bd + m * NO + y), xy, acc[m]);
+          }
+        }
+      }
+      warp_sum<NO>(acc);
+      if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NO; ++m) farsh[tl][m] = acc[m] * h;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int tl = 0; tl < cn; ++tl) {
+        const int t = t0 + tl;
+        zd part[NO];
+#pragma unroll
+        for (int m = 0; m < NO; ++m) part[m] = zd();
+        if (lane < tl) {
+          const int l = t0 + lane;
+          const double wl = h * rule_w(W, t, l);
+          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, t, l) : el<NO>(d.SR, d, n, t, l);
+#pragma unroll
+          for (int y = 0; y < NO; ++y) {
+            const zd xy = xch[lane][y] * wl;
+#pragma unroll
+            for (int m = 0; m < NO; ++m) part[m] = cfma(ld(sr + m * NO + y), xy, part[m]);
+          }
+        }
+        if (lane >= 1 && lane <= k) {
+          const int tj = t - lane;
+          const zd cc = zd(0, -W.a[lane] / h);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) part[m] += cc * ((tj >= t0) ? xch[tj - t0][m] : ld(xp(tj) + m * NO + jc));
+        }
+        warp_sum<NO>(part);
+        if (lane == 0) {
+          zd rhs[NO], x[NO];
+#pragma unroll
+          for (int m = 0; m < NO; ++m) rhs[m] = part[m] + farsh[tl][m] + ld(qs + (long long)t * NO2 + m * NO + jc);
+          const double wt = h * rule_w(W, t, t);
+          const double2* sd = comp ? Lf<NO>(d, 2, n, jl, t, t) : el<NO>(d.SR, d, n, t, t);
+          const double2* ep = epsp<NO>(d, n, t);
+          M<NO> Mm;
+#pragma unroll
+          for (int x2 = 0; x2 < NO; ++x2)
+#pragma unroll
+            for (int y = 0; y < NO; ++y)
+              Mm.a[x2][y] = (x2 == y ? zd(0, W.a[0] / h) : zd()) - ld(ep + x2 * NO + y) - ld(sd + x2 * NO + y) * wt;
+          solve_col<NO>(Mm, rhs, x);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            double2* p = xp(t) + m * NO + jc;
+            myerr = fmax(myerr, sqrt((x[m] - ld(p)).abs2()));
+            st(p, x[m]);
+            xch[tl][m] = x[m];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    t0 = t1;
+  }
+  myerr = warp_max(myerr);
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Lesser source with compressed Sigma^< (two-sided HODLR matvec).
+// Stored S[r][c] = Sigma^<(c, r), c <= r.  q(t) = h sum_l w_l Sigma^<(t,l) g_l,
+// g_l = [G^R(T,l)]^dagger:  l >= t uses S[l][t] (column t), l < t uses
+// -S[t][l]^dagger (row t).
+// Projections per (block, pair (x,z), y):
+//   P1 = S o sum_{rows l} w_l g_l[z][y] U(l,:),  q(t in cols) += P1 . conj(V(t,:))
+//   P2 = S o sum_{cols l} w_l g_l[z][y] V(l,:),  q(t in rows) -= conj(U(t,:)) . P2
+// ---------------------------------------------------------------------------
+template <int NO>
+__device__ __forceinline__ double2* Psrc(const Dev& d, int n, int b, int p, int y, int which) {
+  return d.proj + (long long)d.n_inst * NO * d.maxl * NO * NO * d.rmax +
+         (((((long long)n * d.nblk + b) * (NO * NO) + p) * NO + y) * 2 + which) * d.rmax;
+}
+
+template <int NO>
+__global__ void k_src_proj(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int b = blockIdx.x, n = blockIdx.y;
+  if (!d.active[n]) return;
+  const int c = d.cdir;
+  if (d.b_r0[b] >= c) return;
+  const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c), c0 = d.b_c0[b], c1 = d.b_c1[b];
+  const DevW& W = d.w;
+  for (int idx = threadIdx.x; idx < NO2 * NO * d.rmax; idx += blockDim.x) {
+    const int q = idx % d.rmax, y = (idx / d.rmax) % NO, p = idx / (d.rmax * NO), z = p % NO;
+    const int rk = *Rk<NO>(d, 3, n, b, p);
+    zd a1 = zd(), a2 = zd();
+    if (q < rk) {
+      const double2* U = Up<NO>(d, 3, n, b, p) + q;
+      const double2* V = Vp<NO>(d, 3, n, b, p) + q;
+      for (int l = r0; l < rl; ++l) {  // g_l[z][y] = conj(G^R(T,l)[y][z])
+        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+        a1 = cfma(g, ld(U + (long long)(l - r0) * d.rmax), a1);
+      }
+      for (int l = c0; l < c1; ++l) {
+        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+        a2 = cfma(g, ld(V + (long long)(l - c0) * d.rmax), a2);
+      }
+      const double sv = Sp<NO>(d, 3, n, b, p)[q];
+      a1 = a1 * sv;
+      a2 = a2 * sv;
+    }
+    st(Psrc<NO>(d, n, b, p, y, 0) + q, a1);
+    st(Psrc<NO>(d, n, b, p, y, 1) + q, a2);
+  }
+}
+
+template <int NO>
+__global__ void k_src_h(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = gw / (T + 1), t = gw % (T + 1);
+  if (n >= d.n_inst || !d.active[n]) return;
+  const int c = d.cdir, L = d.L;
+  const double h = d.h;
+  const DevW& W = d.w;
+  zd acc[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  const int jt = t / L, A = jt * L, E = min(A + L, d.nt);
+  // part 1, l >= t: S[l][t]
+  for (int l = max(t, c) + lane; l <= T; l += 32) {  // uncompressed rows
+    const double wl = rule_w(W, T, l);
+    M<NO> S = load<NO>(el<NO>(d.SL, d, n, l, t));
+    M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+  }
+  if (t < c) {
+    for (int l = t + lane; l < min(E, c); l += 32) {  // same leaf
+      const double wl = rule_w(W, T, l);
+      M<NO> S = load<NO>(Lf<NO>(d, 3, n, jt, l, t));
+      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+    }
+  }
+  for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their columns
+    const int b = d.colblk[jt * d.maxl + lv];
+    if (b < 0 || d.b_r0[b] >= c) continue;
+    const int c0 = d.b_c0[b];
+#pragma unroll
+    for (int p = 0; p < NO2; ++p) {
+      const int x = p / NO;
+      const int rk = *Rk<NO>(d, 3, n, b, p);
+      const double2* V = Vp<NO>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
+#pragma unroll
+      for (int y = 0; y < NO; ++y) {
+        const double2* P = Psrc<NO>(d, n, b, p, y, 0);
+        for (int q = lane; q < rk; q += 32) acc[x * NO + y] = cfma(ld(P + q), ld(V + q).conj(), acc[x * NO + y]);
+      }
+    }
+  }
+  // part 2, l < t: -S[t][l]^dagger
+  if (t >= c) {
+    for (int l = lane; l < t; l += 32) {
+      const double wl = rule_w(W, T, l);
+      M<NO> S = dag<NO>(load<NO>(el<NO>(d.SL, d, n, t, l)));
+      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(-wl));
+    }
+  } else {
+    for (int l = A + lane; l < t; l += 32) {
+      const double wl = rule_w(W, T, l);
+      M<NO> S = dag<NO>(load<NO>(Lf<NO>(d, 3, n, jt, t, l)));
+      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(-wl));
+    }
+    for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their rows
+      const int b = d.rowblk[jt * d.maxl + lv];
+      if (b < 0) continue;
+      const int r0 = d.b_r0[b];
+#pragma unroll
+      for (int p = 0; p < NO2; ++p) {  // p = (z, x): conj(U^{zx}(t,:)) . P2^{(zx), y} -> q_xy
+        const int x = p % NO;
+        const int rk = *Rk<NO>(d, 3, n, b, p);
+        const double2* U = Up<NO>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
+#pragma unroll
+        for (int y = 0; y < NO; ++y) {
+          const double2* P = Psrc<NO>(d, n, b, p, y, 1);
+          zd s = zd();
+          for (int q = lane; q < rk; q += 32) s = cfma(ld(U + q).conj(), ld(P + q), s);
+          acc[x * NO + y] -= s;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = acc[q] * h;
+  for (int a = lane; a < d.r; a += 32) {
+    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, t, a));
+    M<NO> V = load<NO>(d.vvec + ((long long)n * d.r + a) * NO2);
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, V, zd(0, -1));
+  }
+  warp_sum<NO2>(acc);
+  if (lane == 0) {
+    double2* p = d.qsrc + ((long long)n * d.nt + t) * NO2;
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) st(p + q, acc[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// update_blocks: compress the rows [A, A+nb) of every component
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void k_comp_copy(Dev d, int A, int nb) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y;
+  const int j = A / d.L;
+  const long long ntr = (long long)nb * (nb + 1) / 2;
+  const long long total = 4 * ntr + (long long)nb * d.k;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (idx < 4 * ntr) {
+      const int X = (int)(idx / ntr);
+      long long e = idx % ntr;
+      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((long long)i * (i + 1) / 2 > e) --i;
+      while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+      const int l = (int)(e - (long long)i * (i + 1) / 2);
+      const int t = A + i, col = A + l;
+      const double2* src = el<NO>(ringX(d, X), d, n, t, col);
+      double2* dst = Lf<NO>(d, X, n, j, t, col);
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) dst[q] = src[q];
+    } else {
+      const long long e = idx - 4 * ntr;
+      const int t = A + (int)(e / d.k), dd = (int)(e % d.k) + 1;
+      double2* dst = Bd<NO>(d, n, t, dd);
+      if (t - dd >= 0) {
+        const double2* src = el<NO>(d.SR, d, n, t, t - dd);
+#pragma unroll
+        for (int q = 0; q < NO2; ++q) dst[q] = src[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NO2; ++q) dst[q] = make_double2(0, 0);
+      }
+    }
+  }
+}
+
+// One CTA per (component X, level slot, pair p) x instance.  Workspace per
+// CTA (complex doubles): E [nb][ncol], Q [nb][ncol], P [nb][rmax], C [nb][nb],
+// K [(rmax+nb)][(rmax+nb)] column-major, Vh [(rmax+nb)][(rmax+nb)] column-major.
+template <int NO>
+__global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y;
+  const int X = blockIdx.x / (d.maxl * NO2);
+  const int lv = (blockIdx.x / NO2) % d.maxl;
+  const int p = blockIdx.x % NO2;
+  const int j = A / d.L;
+  const int b = d.rowblk[j * d.maxl + lv];
+  if (b < 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int r0 = d.b_r0[b], c0 = d.b_c0[b];
+  const int ncol = d.b_c1[b] - c0;
+  const int rmax = d.rmax;
+  const int ld_k = rmax + d.L;  // leading dimension of K and Vh
+  double2* ws = d.tsvd_ws + ((long long)n * gridDim.x + blockIdx.x) * d.tsvd_ws_per;
+  double2* Em = ws;                                   // [nb][ncol]
+  double2* Qm = Em + (long long)d.L * ncol;           // [nb][ncol]
+  double2* Pm = Qm + (long long)d.L * ncol;           // [nb][rmax]
+  double2* Cm = Pm + (long long)d.L * rmax;           // [nb][nb]
+  double2* Km = Cm + (long long)d.L * d.L;            // [ld_k cols][ld_k rows]
+  double2* Vh = Km + (long long)ld_k * ld_k;          // [ld_k cols][ld_k rows]
+  __shared__ int s_ke, s_rnew;
+  __shared__ double s_sig[256];
+  __shared__ int s_ord[256];
+  int* rkp = Rk<NO>(d, X, n, b, p);
+  const int r = *rkp;
+  double2* U = Up<NO>(d, X, n, b, p);
+  double2* V = Vp<NO>(d, X, n, b, p);
+  double* S = Sp<NO>(d, X, n, b, p);
+  const double2* ring = ringX(d, X);
+  // E <- new rows
+  for (long long e = tid; e < (long long)nb * ncol; e += blockDim.x) {
+    const int i = (int)(e / ncol), l = (int)(e % ncol);
+    Em[(long long)i * ncol + l] = el<NO>(const_cast<double2*>(ring), d, n, A + i, c0 + l)[p];
+  }
+  __syncthreads();
+  // P = E V, E -= P V^dagger, twice (the second pass restores orthogonality
+  // to V lost to rounding).  The per-pass coefficients are staged in Q's
+  // storage (r <= ncol), which is free until the Gram-Schmidt below.
+  for (long long e = tid; e < (long long)nb * rmax; e += blockDim.x) Pm[e] = make_double2(0, 0);
+  __syncthreads();
+  for (int pass = 0; pass < 2 && r > 0; ++pass) {
+    for (int e = tid; e < nb * r; e += blockDim.x) {
+      const int i = e / r, q = e % r;
+      zd sacc = zd();
+      for (int l = 0; l < ncol; ++l) sacc = cfma(ld(Em + (long long)i * ncol + l), ld(V + (long long)l * rmax + q), sacc);
+      st(Pm + (long long)i * rmax + q, ld(Pm + (long long)i * rmax + q) + sacc);
+      st(Qm + (long long)i * ncol + q, sacc);
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)nb * ncol; e += blockDim.x) {
+      const int i = (int)(e / ncol), l = (int)(e % ncol);
+      zd sacc = ld(Em + e);
+      for (int q = 0; q < r; ++q) sacc -= ld(Qm + (long long)i * ncol + q) * ld(V + (long long)l * rmax + q).conj();
+      st(Em + e, sacc);
+    }
+    __syncthreads();
+  }
+  for (long long e = tid; e < (long long)d.L * d.L; e += blockDim.x) Cm[e] = make_double2(0, 0);
+  if (tid == 0) s_ke = 0;
+  __syncthreads();
+  // Two-pass Gram-Schmidt on the rows of E: E = C Q, rows of Q orthonormal.
+  const double delta = 0.25 * d.svd_tol;
+  __shared__ zd s_coef[64];
+  __shared__ double s_nrm;
+  for (int i = 0; i < nb; ++i) {
+    double2* v = Em + (long long)i * ncol;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int ke = s_ke;
+      for (int e = warp; e < ke; e += nw) {  // coef_e = <Q_e, v>
+        const double2* qe = Qm + (long long)e * ncol;
+        zd s = zd();
+        for (int l = lane; l < ncol; l += 32) s = cfma(ld(qe + l).conj(), ld(v + l), s);
+        zd tmp[1] = {s};
+        warp_sum<1>(tmp);
+        if (lane == 0) s_coef[e] = tmp[0];
+      }
+      __syncthreads();
+      for (int l = tid; l < ncol; l += blockDim.x) {
+        zd s = ld(v + l);
+        for (int e = 0; e < ke; ++e) s -= s_coef[e] * ld(Qm + (long long)e * ncol + l);
+        st(v + l, s);
+      }
+      if (tid < ke) st(Cm + (long long)i * d.L + tid, ld(Cm + (long long)i * d.L + tid) + s_coef[tid]);
+      __syncthreads();
+    }
+    // norm of the residual
+    double part = 0.0;
+    for (int l = tid; l < ncol; l += blockDim.x) part += ld(v + l).abs2();
+#pragma unroll
+    for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (tid == 0) s_nrm = 0.0;
+    __syncthreads();
+    if (lane == 0) atomicAdd(&s_nrm, part);
+    __syncthreads();
+    const double nrm = sqrt(s_nrm);
+    const int ke = s_ke;
+    if (nrm > delta) {
+      for (int l = tid; l < ncol; l += blockDim.x) st(Qm + (long long)ke * ncol + l, ld(v + l) * (1.0 / nrm));
+      if (tid == 0) {
+        st(Cm + (long long)i * d.L + ke, zd(nrm));
+        s_ke = ke + 1;
+      }
+    }
+    __syncthreads();
+  }
+  const int ke = s_ke;
+  const int m = r + nb, nk = r + ke;  // core rows, columns
+  // K = [[diag(S), 0], [P, C]] column-major; Vh = I
+  for (long long e = tid; e < (long long)ld_k * ld_k; e += blockDim.x) {
+    Km[e] = make_double2(0, 0);
+    Vh[e] = make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int e = tid; e < nk * m; e += blockDim.x) {
+    const int col = e / m, row = e % m;
+    zd v = zd();
+    if (row < r) v = (col == row) ? zd(S[row]) : zd();
+    else if (col < r) v = ld(Pm + (long long)(row - r) * rmax + col);
+    else v = ld(Cm + (long long)(row - r) * d.L + (col - r));
+    st(Km + (long long)col * ld_k + row, v);
+  }
+  for (int e = tid; e < nk; e += blockDim.x) st(Vh + (long long)e * ld_k + e, zd(1.0));
+  __syncthreads();
+  // one-sided Jacobi (Hestenes) on the columns of K, round-robin pairing
+  const int npad = nk + (nk & 1);
+  __shared__ int s_rot;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < npad - 1; ++round) {
+      for (int pr = warp; pr < npad / 2; pr += nw) {
+        // round-robin tournament: position 0 fixed, positions 1..npad-1 rotate
+        auto at = [&](int i) { return i == 0 ? 0 : ((i - 1 + round) % (npad - 1)) + 1; };
+        int a = at(pr), bq = at(npad - 1 - pr);
+        if (a > bq) { const int t2 = a; a = bq; bq = t2; }
+        if (bq >= nk) continue;
+        double2* ka = Km + (long long)a * ld_k;
+        double2* kb = Km + (long long)bq * ld_k;
+        double al = 0, be = 0;
+        zd ga = zd();
+        for (int i = lane; i < m; i += 32) {
+          const zd x = ld(ka + i), y = ld(kb + i);
+          al += x.abs2();
+          be += y.abs2();
+          ga = cfma(x.conj(), y, ga);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, off);
+          be += __shfl_xor_sync(0xffffffffu, be, off);
+          ga.re += __shfl_xor_sync(0xffffffffu, ga.re, off);
+          ga.im += __shfl_xor_sync(0xffffffffu, ga.im, off);
+        }
+        const double g = sqrt(ga.abs2());
+        if (g <= 1e-14 * sqrt(al * be) || g == 0.0) continue;
+        if (lane == 0) s_rot = 1;
+        const zd ph(ga.re / g, -ga.im / g);  // e^{-i phi}
+        const double zeta = (be - al) / (2.0 * g);
+        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        for (int i = lane; i < m; i += 32) {
+          const zd x = ld(ka + i), y = ld(kb + i) * ph;
+          st(ka + i, x * cs - y * sn);
+          st(kb + i, x * sn + y * cs);
+        }
+        double2* va = Vh + (long long)a * ld_k;
+        double2* vb = Vh + (long long)bq * ld_k;
+        for (int i = lane; i < nk; i += 32) {
+          const zd x = ld(va + i), y = ld(vb + i) * ph;
+          st(va + i, x * cs - y * sn);
+          st(vb + i, x * sn + y * cs);
+        }
+      }
+      __syncthreads();
+    }
+    if (!s_rot) break;
+    if (sweep == 39 && tid == 0) atomicAdd(d.status + 1, 1);
+    __syncthreads();
+  }
+  // singular values, sorted, truncated
+  for (int col = warp; col < nk; col += nw) {
+    double s2 = 0;
+    for (int i = lane; i < m; i += 32) s2 += ld(Km + (long long)col * ld_k + i).abs2();
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    if (lane == 0) s_sig[col] = sqrt(s2);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < nk; ++i) s_ord[i] = i;
+    for (int i = 0; i < nk; ++i) {  // selection sort, descending
+      int best = i;
+      for (int q = i + 1; q < nk; ++q)
+        if (s_sig[s_ord[q]] > s_sig[s_ord[best]]) best = q;
+      int t2 = s_ord[i]; s_ord[i] = s_ord[best]; s_ord[best] = t2;
+    }
+    int rn = 0;
+    while (rn < nk && s_sig[s_ord[rn]] > d.svd_tol) ++rn;
+    if (rn > rmax) { atomicAdd(d.status, 1); rn = rmax; }
+    s_rnew = rn;
+  }
+  __syncthreads();
+  const int rn = s_rnew;
+  // U' = [[U, 0], [0, I]] Uhat : old rows r0..A-1, new rows A..A+nb-1
+  const int nold = A - r0;
+  for (int row = warp; row < nold + nb; row += nw) {
+    double2* urow = U + (long long)row * rmax;
+    // compute U'[row][j] for j = lane, lane+32, ...
+    zd res[4];
+    for (int t2 = 0; t2 < 4; ++t2) res[t2] = zd();
+    for (int t2 = 0; t2 < 4; ++t2) {
+      const int jj = lane + 32 * t2;
+      if (jj >= rn) continue;
+      const int col = s_ord[jj];
+      const double inv = 1.0 / s_sig[col];
+      zd s = zd();
+      if (row < nold) {
+        for (int q = 0; q < r; ++q) s = cfma(ld(urow + q), ld(Km + (long long)col * ld_k + q), s);
+      } else {
+        s = ld(Km + (long long)col * ld_k + r + (row - nold));
+      }
+      res[t2] = s * inv;
+    }
+    __syncwarp();
+    for (int t2 = 0; t2 < 4; ++t2) {
+      const int jj = lane + 32 * t2;
+      if (jj < rmax) st(urow + jj, jj < rn ? res[t2] : zd());
+    }
+    __syncwarp();
+  }
+  // V' = [V, Q^H] Vhat
+  for (int l = warp; l < ncol; l += nw) {
+    double2* vrow = V + (long long)l * rmax;
+    zd res[4];
+    for (int t2 = 0; t2 < 4; ++t2) {
+      res[t2] = zd();
+      const int jj = lane + 32 * t2;
+      if (jj >= rn) continue;
+      const int col = s_ord[jj];
+      const double2* vh = Vh + (long long)col * ld_k;
+      zd s = zd();
+      for (int q = 0; q < r; ++q) s = cfma(ld(vrow + q), ld(vh + q), s);
+      for (int e = 0; e < ke; ++e) s = cfma(ld(Qm + (long long)e * ncol + l).conj(), ld(vh + r + e), s);
+      res[t2] = s;
+    }
+    __syncwarp();
+    for (int t2 = 0; t2 < 4; ++t2) {
+      const int jj = lane + 32 * t2;
+      if (jj < rmax) st(vrow + jj, jj < rn ? res[t2] : zd());
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = tid; q < rmax; q += blockDim.x) S[q] = (q < rn) ? s_sig[s_ord[q]] : 0.0;
+  if (tid == 0) *rkp = rn;
+}
+
+// Reconstruct row T of G^R and G^< (any T <= current) into out_r, out_l
+// ([T+1][no2] each), from the ring, the leaves or the blocks.
+template <int NO>
+__global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
+  constexpr int NO2 = NO * NO;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > T) return;
+  for (int X = 0; X < 2; ++X) {
+    double2* out = (X == 0) ? out_r : out_l;
+    if (!out) continue;
+    for (int p = 0; p < NO2; ++p) {
+      zd v;
+      if (T >= d.cdir) {
+        v = ld(el<NO>(ringX(d, X), d, n, T, t) + p);
+      } else {
+        const int jT = T / d.L, jt = t / d.L;
+        if (jT == jt) {
+          v = ld(Lf<NO>(d, X, n, jT, T, t) + p);
+        } else {
+          v = zd();
+          for (int lv = 0; lv < d.maxl; ++lv) {
+            const int b = d.rowblk[jT * d.maxl + lv];
+            if (b < 0 || t < d.b_c0[b] || t >= d.b_c1[b]) continue;
+            const int rk = *Rk<NO>(d, X, n, b, p);
+            const double2* U = Up<NO>(d, X, n, b, p) + (long long)(T - d.b_r0[b]) * d.rmax;
+            const double2* V = Vp<NO>(d, X, n, b, p) + (long long)(t - d.b_c0[b]) * d.rmax;
+            const double* S = Sp<NO>(d, X, n, b, p);
+            for (int q = 0; q < rk; ++q) v += ld(U + q) * ld(V + q).conj() * S[q];
+          }
+        }
+      }
+      st(out + (long long)t * NO2 + p, v);
+    }
+  }
+}
+
+#define HK_DISPATCH(NOV, CALL)                       \
+  switch (NOV) {                                     \
+    case 1: { constexpr int NO = 1; CALL; break; }   \
+    case 2: { constexpr int NO = 2; CALL; break; }   \
+    case 3: { constexpr int NO = 3; CALL; break; }   \
+    case 4: { constexpr int NO = 4; CALL; break; }   \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_ret_h<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_les_h<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s) {
+  if (d.cdir > 0) {
+    dim3 g(d.nblk, d.n_inst);
+    HK_DISPATCH(d.no, (k_src_proj<NO><<<g, 256, 0, s>>>(d, T)));
+  }
+  const long long warps = (long long)d.n_inst * (T + 1);
+  HK_DISPATCH(d.no, (k_src_h<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s) {
+  {
+    dim3 g(64, d.n_inst);
+    HK_DISPATCH(d.no, (k_comp_copy<NO><<<g, 256, 0, s>>>(d, A, nb)));
+  }
+  dim3 g(4 * d.maxl * d.no * d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_tsvd<NO><<<g, 256, 0, s>>>(d, A, nb)));
+  return cudaGetLastError();
+}
+cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s) {
+  HK_DISPATCH(d.no, (k_row_out<NO><<<(T + 128) / 128, 128, 0, s>>>(d, n, T, out_r, out_l)));
+  return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -16,8 +16,33 @@ constexpr int MP = 64;  // doubles of model parameters per instance
 
 // Lower-triangular storage: element (T, t), t <= T, of instance n lives at
 // ((n * ntri + T*(T+1)/2 + t) * no*no).  Mixed arrays are [n][T][i][no*no].
+// Compressed (HODLR) storage of one two-time component (Sec. 2.2): dense
+// leaf triangles plus U S V^dagger blocks, one scalar TSVD per orbital pair.
+struct Hod {
+  double2* U;    // [n][utot][rmax]   U of block b, pair p at (uoff[b] + p*rows_b) * rmax
+  double2* V;    // [n][vtot][rmax]   V of block b, pair p at (voff[b] + p*cols_b) * rmax
+  double* S;     // [n][nblk][no2][rmax]
+  int* rank;     // [n][nblk][no2]
+  double2* leaf; // [n][leaftot][no2] lower triangles of the diagonal leaves
+};
+
 struct Dev {
   int nt, k, no, r, n_inst, xi, rho_mode, model;
+  // ---- compressed storage (ring == 0: dense triangles, no compression) ----
+  int ring;            // rows kept uncompressed in a ring of this many slots
+  int cdir;            // first uncompressed row (multiple of the leaf size)
+  int L, nleaf, nblk, rmax, maxl;
+  double svd_tol;
+  const int *b_r0, *b_r1, *b_c0, *b_c1, *b_lvl;   // block geometry
+  const long long *b_uoff, *b_voff, *leafoff;     // factor / leaf offsets
+  const int *rowblk, *colblk;                     // [nleaf][maxl] block ids or -1
+  long long utot, vtot, leaftot;
+  Hod hod[4];          // 0 G^R, 1 G^<, 2 Sigma^R, 3 Sigma^<
+  double2* band;       // [n][nt][k][no2] Sigma^R(t, t-d), d = 1..k
+  double2* proj;       // sweep projections [n][no][maxl][no2][rmax] (+ source: see kernels)
+  double2* tsvd_ws;    // TSVD workspace, tsvd_ws_per entries per CTA
+  long long tsvd_ws_per;
+  int* status;         // [0] rank overflow count, [1] Jacobi non-convergence count
   long long ntri;  // nt*(nt+1)/2
   double h, beta;
   DevW w;
@@ -48,5 +73,11 @@ cudaError_t launch_les(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_rho(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_boot(const Dev& d, cudaStream_t s);   // one bootstrap pass (Sigma + R/mixed/lesser)
 cudaError_t launch_set_active(const Dev& d, double tol, int iter, int min_iter, int* any_active_dev, cudaStream_t s);
+// compressed (HODLR) form
+cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s);
+cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s);
+cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s);
+cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s);
+cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s);
 
 }  // namespace hk
