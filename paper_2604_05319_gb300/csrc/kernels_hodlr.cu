@@ -616,18 +616,20 @@ __global__ void k_src_proj(Dev d, int T) {
   const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c), c0 = d.b_c0[b], c1 = d.b_c1[b];
   const DevW& W = d.w;
   for (int idx = threadIdx.x; idx < NO2 * NO * d.rmax; idx += blockDim.x) {
-    const int q = idx % d.rmax, y = (idx / d.rmax) % NO, p = idx / (d.rmax * NO), z = p % NO;
+    // P1 serves pair p = (x, z) (uses g[z]), P2 serves pair p = (z, x) (uses g[z])
+    const int q = idx % d.rmax, y = (idx / d.rmax) % NO, p = idx / (d.rmax * NO);
+    const int z1 = p % NO, z2 = p / NO;
     const int rk = *Rk<NO>(d, 3, n, b, p);
     zd a1 = zd(), a2 = zd();
     if (q < rk) {
       const double2* U = Up<NO>(d, 3, n, b, p) + q;
       const double2* V = Vp<NO>(d, 3, n, b, p) + q;
       for (int l = r0; l < rl; ++l) {  // g_l[z][y] = conj(G^R(T,l)[y][z])
-        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z1).conj() * rule_w(W, T, l);
         a1 = cfma(g, ld(U + (long long)(l - r0) * d.rmax), a1);
       }
       for (int l = c0; l < c1; ++l) {
-        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z2).conj() * rule_w(W, T, l);
         a2 = cfma(g, ld(V + (long long)(l - c0) * d.rmax), a2);
       }
       const double sv = Sp<NO>(d, 3, n, b, p)[q];
