@@ -187,7 +187,8 @@ enum {
   HKBE_PHASE_BOOT = 8,    /* bootstrap square                                  */
   HKBE_PHASE_CTRL = 9,    /* convergence bookkeeping                           */
   HKBE_PHASE_COMPRESS = 10, /* HODLR leaf copy + TSVD block updates (update_blocks) */
-  HKBE_NPHASE = 11
+  HKBE_PHASE_CHUNKINV = 11, /* inverses of frozen 32-point sweep chunks           */
+  HKBE_NPHASE = 12
 };
 
 /* When on (nonzero), every kernel launch is bracketed by CUDA events on the

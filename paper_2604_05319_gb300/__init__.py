@@ -237,7 +237,7 @@ def hkbe_set_profiling(h, on):
     _check(load().hkbe_set_profiling(h, int(bool(on))), h)
 
 
-PHASES = ["extrap", "sigma", "ret", "mixed", "vt", "src", "les", "rho", "boot", "ctrl", "compress"]
+PHASES = ["extrap", "sigma", "ret", "mixed", "vt", "src", "les", "rho", "boot", "ctrl", "compress", "chunkinv"]
 
 
 def hkbe_get_timing(h, phase):

@@ -256,6 +256,17 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
     }
     d.status = h->status_dev;
   }
+  d.nchunk = (d.nt + 31) / 32;
+  d.nfrozR = d.nfrozL = 0;
+  {
+    const size_t ld = 32 * (size_t)d.no;
+    if ((rc = dalloc(h, &d.cinv, (size_t)d.n_inst * d.nchunk * 2 * ld * ld)) ||
+        (rc = dalloc(h, &d.cinv_ws, (size_t)d.n_inst * ld * ld))) {
+      g_create_error = h->err;
+      hkbe_destroy(h);
+      return rc;
+    }
+  }
   if ((rc = dalloc(h, &d.GR, tri)) || (rc = dalloc(h, &d.GL, tri)) || (rc = dalloc(h, &d.SR, tri)) ||
       (rc = dalloc(h, &d.SL, tri)) ||
       (rc = dalloc(h, &d.eps, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
@@ -584,6 +595,20 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
   bool any_failed = false;
   for (int st = 0; st < n_steps; ++st) {
     const int T = h->cur + 1;
+    // inverses of the chunks that became frozen (their rows are final and far enough from T)
+    {
+      const int tR = std::max(0, (T - 2 * d.k) / 32), tL = std::max(0, T / 32);
+      if (tR > d.nfrozR) {
+        HK_CUDA(h, run_phase(h, HKBE_PHASE_CHUNKINV, tR - d.nfrozR,
+                             [&]() { return hk::launch_chunk_inv(d, 0, d.nfrozR, tR, h->s); }));
+        d.nfrozR = tR;
+      }
+      if (tL > d.nfrozL) {
+        HK_CUDA(h, run_phase(h, HKBE_PHASE_CHUNKINV, tL - d.nfrozL,
+                             [&]() { return hk::launch_chunk_inv(d, 1, d.nfrozL, tL, h->s); }));
+        d.nfrozL = tL;
+      }
+    }
     HK_CUDA(h, run_phase(h, HKBE_PHASE_EXTRAP, 1, [&]() { return hk::launch_extrapolate(d, T, h->s); }));
     bool failed = false;
     rc = iterate(h, h->p.max_iter, h->p.tol,
@@ -592,7 +617,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                    if ((e = run_phase(h, HKBE_PHASE_SIGMA, 1, [&]() { return hk::launch_sigma(d, T, h->s); })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_RET, 1, [&]() {
-                          return h->hodlr ? hk::launch_ret_h(d, T, h->s) : hk::launch_ret(d, T, h->s);
+                          return hk::launch_ret_h(d, T, h->s);
                         })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_MIXED, 1, [&]() { return hk::launch_mixed(d, T, h->s); })))
@@ -603,7 +628,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                         })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_LES, 1, [&]() {
-                          return h->hodlr ? hk::launch_les_h(d, T, h->s) : hk::launch_les(d, T, h->s);
+                          return hk::launch_les_h(d, T, h->s);
                         })))
                      return e;
                    if (d.rho_mode == 1 &&
@@ -787,6 +812,7 @@ int hkbe_rewind(hkbe_t* h) {
   HK_CUDA(h, put(h->snap_sl, d.SL));
   HK_CUDA(h, put_tv(h->snap_tv, d.GTV));
   HK_CUDA(h, put_tv(h->snap_stv, d.STV));
+  d.nfrozR = d.nfrozL = 0;
   if (h->hodlr) {
     d.cdir = 0;
     for (int X = 0; X < 4; ++X)

@@ -20,576 +20,10 @@
 // basis Q of E's rows by two-pass Gram-Schmidt, the core
 // K = [[S, 0], [P, C]] (C = E Q^dagger), its SVD by one-sided Jacobi, truncation
 // of singular values below the SVD tolerance (Sec. 2.2), and rotation of U, V.
-#include "dev_util.cuh"
+#include "hodlr_util.cuh"
 
 namespace hk {
 
-namespace {
-
-constexpr int CHH = 32;     // sweep sub-chunk (the leaf size is a multiple)
-constexpr int NWH = 8;      // warps per sweep CTA
-
-__device__ __forceinline__ double2* ringX(const Dev& d, int X) {
-  return X == 0 ? d.GR : X == 1 ? d.GL : X == 2 ? d.SR : d.SL;
-}
-template <int NO>
-__device__ __forceinline__ double2* Up(const Dev& d, int X, int n, int b, int p) {
-  const long long rows = d.b_r1[b] - d.b_r0[b];
-  return d.hod[X].U + ((long long)n * d.utot + d.b_uoff[b] + p * rows) * d.rmax;
-}
-template <int NO>
-__device__ __forceinline__ double2* Vp(const Dev& d, int X, int n, int b, int p) {
-  const long long cols = d.b_c1[b] - d.b_c0[b];
-  return d.hod[X].V + ((long long)n * d.vtot + d.b_voff[b] + p * cols) * d.rmax;
-}
-template <int NO>
-__device__ __forceinline__ double* Sp(const Dev& d, int X, int n, int b, int p) {
-  return d.hod[X].S + (((long long)n * d.nblk + b) * (NO * NO) + p) * d.rmax;
-}
-template <int NO>
-__device__ __forceinline__ int* Rk(const Dev& d, int X, int n, int b, int p) {
-  return d.hod[X].rank + ((long long)n * d.nblk + b) * (NO * NO) + p;
-}
-// element (t, l) of leaf j of component X (t, l inside the leaf, l <= t)
-template <int NO>
-__device__ __forceinline__ double2* Lf(const Dev& d, int X, int n, int j, int t, int l) {
-  const int A = j * d.L;
-  return d.hod[X].leaf + ((long long)n * d.leaftot + d.leafoff[j] + tri(t - A) + (l - A)) * (NO * NO);
-}
-template <int NO>
-__device__ __forceinline__ double2* Bd(const Dev& d, int n, int t, int dd) {
-  return d.band + (((long long)n * d.nt + t) * d.k + (dd - 1)) * (NO * NO);
-}
-// sweep projection slots: [n][row/col][maxl][no2][rmax]
-template <int NO>
-__device__ __forceinline__ double2* Pj(const Dev& d, int n, int which, int lv, int p) {
-  return d.proj + ((((long long)n * NO + which) * d.maxl + lv) * (NO * NO) + p) * d.rmax;
-}
-
-// Sigma^R(t, l), l <= t, from whichever storage holds it.
-template <int NO>
-__device__ zd sr_any(const Dev& d, int n, int t, int l, int x, int y) {
-  if (t >= d.cdir) return ld(el<NO>(d.SR, d, n, t, l) + x * NO + y);
-  const int jt = t / d.L, jl = l / d.L;
-  if (jt == jl) return ld(Lf<NO>(d, 2, n, jt, t, l) + x * NO + y);
-  for (int lv = 0; lv < d.maxl; ++lv) {
-    const int b = d.rowblk[jt * d.maxl + lv];
-    if (b < 0 || l < d.b_c0[b] || l >= d.b_c1[b]) continue;
-    const int p = x * NO + y, rk = *Rk<NO>(d, 2, n, b, p);
-    const double2* U = Up<NO>(d, 2, n, b, p) + (long long)(t - d.b_r0[b]) * d.rmax;
-    const double2* V = Vp<NO>(d, 2, n, b, p) + (long long)(l - d.b_c0[b]) * d.rmax;
-    const double* S = Sp<NO>(d, 2, n, b, p);
-    zd s = zd();
-    for (int q = 0; q < rk; ++q) s += ld(U + q) * ld(V + q).conj() * S[q];
-    return s;
-  }
-  return zd();
-}
-template <int NO>
-__device__ zd srx_any(const Dev& d, int n, int a, int b, int x, int y) {
-  if (a >= b) return sr_any<NO>(d, n, a, b, x, y);
-  return -sr_any<NO>(d, n, b, a, y, x).conj();
-}
-
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// Retarded row with compressed Sigma^R (Eq. KBER); one CTA per (row, instance)
-// ---------------------------------------------------------------------------
-template <int NO>
-__global__ void __launch_bounds__(256) k_ret_h(Dev d, int T) {
-  constexpr int NO2 = NO * NO;
-  const int n = blockIdx.y, irow = blockIdx.x;
-  if (!d.active[n]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = d.k, c = d.cdir, L = d.L;
-  const double h = d.h;
-  const DevW& W = d.w;
-  __shared__ zd sA[20 * 20];
-  __shared__ zd sB[20];
-  __shared__ zd red[NWH][CHH][NO];
-  __shared__ zd ych[CHH][NO];
-  __shared__ double serr;
-  if (tid == 0) serr = 0.0;
-  double2* rowp = el<NO>(d.GR, d, n, T, 0);
-  auto yp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };   // G^R(T, t')
-  double myerr = 0.0;
-  // ---- start block s = 1..k (rows T-k..T, uncompressed) ----
-  const int ns = k * NO;
-  if (warp == 0) {
-    for (int e = lane; e < ns * ns; e += 32) {
-      const int row = e / ns, col = e % ns;
-      const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
-      zd v = srx<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
-      if (m == j) v += zd(0, W.D[s][l] / h);
-      if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
-      sA[row * ns + col] = v;
-    }
-    for (int row = lane; row < ns; row += 32) {
-      const int s = row / NO + 1, j = row % NO;
-      zd cc = srx<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
-      if (irow == j) cc += zd(0, W.D[s][0] / h);
-      sB[row] = zd(0, 1) * cc;
-    }
-    __syncwarp();
-    warp_lu_solve(ns, sA, sB, 1, nullptr);
-    for (int row = lane; row < ns; row += 32) {
-      const int s = row / NO + 1, j = row % NO;
-      double2* p = yp(T - s) + j;
-      myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
-      st(p, sB[row]);
-    }
-    if (lane == 0) {
-      double2* p = yp(T);
-      for (int j = 0; j < NO; ++j) {
-        zd v = (j == irow) ? zd(0, -1) : zd();
-        myerr = fmax(myerr, sqrt((ld(p + j) - v).abs2()));
-        st(p + j, v);
-      }
-    }
-  }
-  __syncthreads();
-  // ---- uncompressed columns t' in [c, T-k-1], chunks of 32 in s = T - t' ----
-  for (int s0 = k + 1; s0 <= T - c; s0 += CHH) {
-    const int cn = min(CHH, T - c + 1 - s0);
-    {
-      zd acc[NO];
-#pragma unroll
-      for (int j = 0; j < NO; ++j) acc[j] = zd();
-      const int s = s0 + lane;
-      if (lane < cn) {
-        for (int l = warp; l < s0; l += NWH) {
-          const double wl = rule_w(W, s, l);
-          const double2* yl = yp(T - l);
-          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ld(yl + m) * wl;
-#pragma unroll
-            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      zd far[NO];
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        far[j] = zd();
-        for (int w2 = 0; w2 < NWH; ++w2) far[j] += red[w2][lane][j];
-        far[j] = far[j] * h;
-      }
-      for (int sl = 0; sl < cn; ++sl) {
-        const int s = s0 + sl;
-        zd part[NO];
-#pragma unroll
-        for (int j = 0; j < NO; ++j) part[j] = zd();
-        if (lane < sl) {
-          const int l = s0 + lane;
-          const double wl = h * rule_w(W, s, l);
-          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ych[lane][m] * wl;
-#pragma unroll
-            for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
-          }
-        }
-        if (lane >= 1 && lane <= k) {
-          const int sj = s - lane;
-          const zd cc = zd(0, -W.a[lane] / h);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) part[m] += cc * ((sj >= s0) ? ych[sj - s0][m] : ld(yp(T - sj) + m));
-        }
-        warp_sum<NO>(part);
-        if (lane == sl) {
-          zd rhs[NO], y[NO];
-#pragma unroll
-          for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
-          const double ws = h * rule_w(W, s, s);
-          const double2* sd = el<NO>(d.SR, d, n, T - s, T - s);
-          const double2* ep = epsp<NO>(d, n, T - s);
-          M<NO> Mm;
-#pragma unroll
-          for (int x = 0; x < NO; ++x)
-#pragma unroll
-            for (int y2 = 0; y2 < NO; ++y2)
-              Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
-          solve_row<NO>(Mm, rhs, y);
-          double2* p = yp(T - s);
-#pragma unroll
-          for (int j = 0; j < NO; ++j) {
-            myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
-            st(p + j, y[j]);
-            ych[sl][j] = y[j];
-          }
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-  // ---- compressed columns t' < c, leaf by leaf (descending) ----
-  for (int jl = c / L - 1; jl >= 0; --jl) {
-    const int A = jl * L, E = A + L;
-    // projections of the blocks whose column range ends at E
-    for (int lv = 0; lv < d.maxl; ++lv) {
-      const int b = d.colblk[jl * d.maxl + lv];
-      if (b < 0 || d.b_c1[b] != E) continue;
-      const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c);
-      for (int idx = tid; idx < NO2 * d.rmax; idx += blockDim.x) {
-        const int p = idx / d.rmax, q = idx % d.rmax, m = p / NO;
-        const int rk = *Rk<NO>(d, 2, n, b, p);
-        zd acc = zd();
-        if (q < rk && r0 < rl) {
-          const double2* U = Up<NO>(d, 2, n, b, p) + q;
-          for (int s = r0; s < rl; ++s) acc = cfma(ld(yp(s) + m), ld(U + (long long)(s - r0) * d.rmax), acc);
-          acc = acc * Sp<NO>(d, 2, n, b, p)[q];
-        }
-        st(Pj<NO>(d, n, irow, lv, p) + q, acc);
-      }
-    }
-    __syncthreads();
-    for (int bsub = E; bsub > A; bsub -= CHH) {
-      const int a0 = bsub - CHH;
-      const int tp = a0 + lane;  // this lane's column
-      zd acc[NO];
-#pragma unroll
-      for (int j = 0; j < NO; ++j) acc[j] = zd();
-      // uncompressed rows s in [c, T]
-      for (int s = c + warp; s <= T; s += NWH) {
-        const double ws = rule_w(W, T - tp, T - s);
-        const double2* yl = yp(s);
-        const double2* sr = el<NO>(d.SR, d, n, s, tp);
-#pragma unroll
-        for (int m = 0; m < NO; ++m) {
-          const zd ym = ld(yl + m) * ws;
-#pragma unroll
-          for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
-        }
-      }
-      // rows of this leaf above the sub-chunk, s in [bsub, E)
-      for (int s = bsub + warp; s < E; s += NWH) {
-        const double ws = rule_w(W, T - tp, T - s);
-        const double2* yl = yp(s);
-        const double2* sr = Lf<NO>(d, 2, n, jl, s, tp);
-#pragma unroll
-        for (int m = 0; m < NO; ++m) {
-          const zd ym = ld(yl + m) * ws;
-#pragma unroll
-          for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
-        }
-      }
-      // compressed blocks below the leaf (weight 1), one warp per level
-      for (int lv = warp; lv < d.maxl; lv += NWH) {
-        const int b = d.colblk[jl * d.maxl + lv];
-        if (b < 0 || d.b_r0[b] >= c) continue;
-        const int c0 = d.b_c0[b];
-#pragma unroll
-        for (int p = 0; p < NO2; ++p) {
-          const int m = p / NO, j = p % NO;
-          (void)m;
-          const int rk = *Rk<NO>(d, 2, n, b, p);
-          const double2* V = Vp<NO>(d, 2, n, b, p) + (long long)(tp - c0) * d.rmax;
-          const double2* P = Pj<NO>(d, n, irow, lv, p);
-          zd s = zd();
-          for (int q = 0; q < rk; ++q) s = cfma(ld(P + q), ld(V + q).conj(), s);
-          acc[j] += s;
-        }
-      }
-      // near-diagonal block entries: (w - 1) y(s) Sigma^R(s, t') for s in [E, t'+k], s < c
-      if (warp == NWH - 1) {
-        for (int s = E; s <= tp + k && s < c; ++s) {
-          const double ws = rule_w(W, T - tp, T - s) - 1.0;
-          const double2* bd = Bd<NO>(d, n, s, s - tp);
-          const double2* yl = yp(s);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ld(yl + m) * ws;
-#pragma unroll
-            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(bd + m * NO + j), acc[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
-      __syncthreads();
-      if (warp == 0) {
-        zd far[NO];
-#pragma unroll
-        for (int j = 0; j < NO; ++j) {
-          far[j] = zd();
-          for (int w2 = 0; w2 < NWH; ++w2) far[j] += red[w2][lane][j];
-          far[j] = far[j] * h;
-        }
-        for (int tl = CHH - 1; tl >= 0; --tl) {
-          const int t0 = a0 + tl;
-          zd part[NO];
-#pragma unroll
-          for (int j = 0; j < NO; ++j) part[j] = zd();
-          const int s = t0 + 1 + lane;  // near field, rows s in (t0, bsub)
-          if (s < bsub) {
-            const double wl = h * rule_w(W, T - t0, T - s);
-            const double2* sr = Lf<NO>(d, 2, n, jl, s, t0);
-#pragma unroll
-            for (int m = 0; m < NO; ++m) {
-              const zd ym = ych[s - a0][m] * wl;
-#pragma unroll
-              for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
-            }
-          }
-          if (lane >= 1 && lane <= k) {
-            const int sj = t0 + lane;
-            const zd cc = zd(0, -W.a[lane] / h);
-#pragma unroll
-            for (int m = 0; m < NO; ++m) part[m] += cc * ((sj < bsub) ? ych[sj - a0][m] : ld(yp(sj) + m));
-          }
-          warp_sum<NO>(part);
-          if (lane == tl) {
-            zd rhs[NO], y[NO];
-#pragma unroll
-            for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
-            const double ws = h * rule_w(W, T - t0, T - t0);
-            const double2* sd = Lf<NO>(d, 2, n, jl, t0, t0);
-            const double2* ep = epsp<NO>(d, n, t0);
-            M<NO> Mm;
-#pragma unroll
-            for (int x = 0; x < NO; ++x)
-#pragma unroll
-              for (int y2 = 0; y2 < NO; ++y2)
-                Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
-            solve_row<NO>(Mm, rhs, y);
-            double2* p = yp(t0);
-#pragma unroll
-            for (int j = 0; j < NO; ++j) {
-              myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
-              st(p + j, y[j]);
-              ych[tl][j] = y[j];
-            }
-          }
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-    }
-  }
-  myerr = warp_max(myerr);
-  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
-  __syncthreads();
-  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
-}
-
-// ---------------------------------------------------------------------------
-// Lesser column with compressed Sigma^R (Eq. KBEL); one CTA per (column, instance)
-// ---------------------------------------------------------------------------
-template <int NO>
-__global__ void __launch_bounds__(256) k_les_h(Dev d, int T) {
-  constexpr int NO2 = NO * NO;
-  const int n = blockIdx.y, jc = blockIdx.x;
-  if (!d.active[n]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = d.k, c = d.cdir, L = d.L;
-  const double h = d.h;
-  const DevW& W = d.w;
-  __shared__ zd sA[20 * 20];
-  __shared__ zd sB[20];
-  __shared__ zd farsh[CHH][NO];
-  __shared__ zd xch[CHH][NO];
-  __shared__ double serr;
-  if (tid == 0) serr = 0.0;
-  double2* colp = el<NO>(d.GL, d, n, T, 0);
-  auto xp = [&](int t) { return colp + (long long)t * NO2; };   // [m*NO + jc]
-  const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
-  double myerr = 0.0;
-  const int last = (d.rho_mode == 1) ? T - 1 : T;
-  // Sigma^R(t, l) anywhere in the stored triangle, and its continuation
-  auto S_at = [&](int t, int l, int x, int y) -> zd { return srx_any<NO>(d, n, t, l, x, y); };
-  if (warp == 0) {
-    if (lane < NO) {
-      const int m = lane;
-      zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
-      double2* p = xp(0) + m * NO + jc;
-      myerr = fmax(myerr, sqrt((v - ld(p)).abs2()));
-      st(p, v);
-    }
-    __syncwarp();
-    const int ns = k * NO;
-    for (int e = lane; e < ns * ns; e += 32) {
-      const int row = e / ns, col = e % ns;
-      const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
-      zd v = S_at(t, l, m, y) * (-h * W.I0[t][l]);
-      if (m == y) v += zd(0, W.D[t][l] / h);
-      if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
-      sA[row * ns + col] = v;
-    }
-    for (int row = lane; row < ns; row += 32) {
-      const int t = row / NO + 1, m = row % NO;
-      zd bb = ld(qs + t * NO2 + m * NO + jc);
-      for (int y = 0; y < NO; ++y) {
-        zd cc = S_at(t, 0, m, y) * (-h * W.I0[t][0]);
-        if (m == y) cc += zd(0, W.D[t][0] / h);
-        bb -= cc * ld(xp(0) + y * NO + jc);
-      }
-      sB[row] = bb;
-    }
-    __syncwarp();
-    warp_lu_solve(ns, sA, sB, 1, nullptr);
-    for (int row = lane; row < ns; row += 32) {
-      const int t = row / NO + 1, m = row % NO;
-      if (t > last) continue;
-      double2* p = xp(t) + m * NO + jc;
-      myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
-      st(p, sB[row]);
-    }
-  }
-  __syncthreads();
-  for (int t0 = k + 1; t0 <= last;) {
-    const int t1 = min((t0 / CHH + 1) * CHH, last + 1);
-    const int cn = t1 - t0;
-    const int jl = t0 / L, A = jl * L;
-    const bool comp = (t0 < c);
-    if (comp && t0 == A && jl > 0) {
-      // rho projections of the blocks whose rows start at A
-      for (int lv = 0; lv < d.maxl; ++lv) {
-        const int b = d.rowblk[jl * d.maxl + lv];
-        if (b < 0 || d.b_r0[b] != A) continue;
-        const int c0 = d.b_c0[b], c1 = d.b_c1[b];
-        for (int idx = tid; idx < NO2 * d.rmax; idx += blockDim.x) {
-          const int p = idx / d.rmax, q = idx % d.rmax, nn = p % NO;
-          const int rk = *Rk<NO>(d, 2, n, b, p);
-          zd acc = zd();
-          if (q < rk) {
-            const double2* V = Vp<NO>(d, 2, n, b, p) + q;
-            for (int l = c0; l < c1; ++l) {
-              const double wl = (l <= k) ? W.omega[l] : 1.0;
-              acc = cfma(ld(V + (long long)(l - c0) * d.rmax).conj() * wl, ld(xp(l) + nn * NO + jc), acc);
-            }
-            acc = acc * Sp<NO>(d, 2, n, b, p)[q];
-          }
-          st(Pj<NO>(d, n, jc, lv, p) + q, acc);
-        }
-      }
-      __syncthreads();
-    }
-    // far field: warp per row t, lanes over l
-    for (int tl = warp; tl < cn; tl += NWH) {
-      const int t = t0 + tl;
-      zd acc[NO];
-#pragma unroll
-      for (int m = 0; m < NO; ++m) acc[m] = zd();
-      if (!comp) {
-        const double2* srow = el<NO>(d.SR, d, n, t, 0);
-        for (int l = lane; l < t0; l += 32) {
-          const double wl = rule_w(W, t, l);
-          const double2* sr = srow + (long long)l * NO2;
-#pragma unroll
-          for (int y = 0; y < NO; ++y) {
-            const zd xy = ld(xp(l) + y * NO + jc) * wl;
-#pragma unroll
-            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
-          }
-        }
-      } else {
-        for (int l = A + lane; l < t0; l += 32) {  // same leaf
-          const double wl = rule_w(W, t, l);
-          const double2* sr = Lf<NO>(d, 2, n, jl, t, l);
-#pragma unroll
-          for (int y = 0; y < NO; ++y) {
-            const zd xy = ld(xp(l) + y * NO + jc) * wl;
-#pragma unroll
-            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
-          }
-        }
-        for (int lv = 0; lv < d.maxl; ++lv) {  // blocks left of the leaf
-          const int b = d.rowblk[jl * d.maxl + lv];
-          if (b < 0) continue;
-          const int r0 = d.b_r0[b];
-#pragma unroll
-          for (int p = 0; p < NO2; ++p) {
-            const int m = p / NO;
-            const int rk = *Rk<NO>(d, 2, n, b, p);
-            const double2* U = Up<NO>(d, 2, n, b, p) + (long long)(t - r0) * d.rmax;
-            const double2* P = Pj<NO>(d, n, jc, lv, p);
-            for (int q = lane; q < rk; q += 32) acc[m] = cfma(ld(U + q), ld(P + q), acc[m]);
-          }
-        }
-        for (int l = max(t - k, 0) + lane; l < A; l += 32) {  // near-diagonal block entries
-          const double wl = rule_w(W, t, l) - 1.0;
-          const double2* bd = Bd<NO>(d, n, t, t - l);
-#pragma unroll
-          for (int y = 0; y < NO; ++y) {
-            const zd xy = ld(xp(l) + y * NO + jc) * wl;
-#pragma unroll
-            for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(bd + m * NO + y), xy, acc[m]);
-          }
-        }
-      }
-      warp_sum<NO>(acc);
-      if (lane == 0)
-#pragma unroll
-        for (int m = 0; m < NO; ++m) farsh[tl][m] = acc[m] * h;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int tl = 0; tl < cn; ++tl) {
-        const int t = t0 + tl;
-        zd part[NO];
-#pragma unroll
-        for (int m = 0; m < NO; ++m) part[m] = zd();
-        if (lane < tl) {
-          const int l = t0 + lane;
-          const double wl = h * rule_w(W, t, l);
-          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, t, l) : el<NO>(d.SR, d, n, t, l);
-#pragma unroll
-          for (int y = 0; y < NO; ++y) {
-            const zd xy = xch[lane][y] * wl;
-#pragma unroll
-            for (int m = 0; m < NO; ++m) part[m] = cfma(ld(sr + m * NO + y), xy, part[m]);
-          }
-        }
-        if (lane >= 1 && lane <= k) {
-          const int tj = t - lane;
-          const zd cc = zd(0, -W.a[lane] / h);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) part[m] += cc * ((tj >= t0) ? xch[tj - t0][m] : ld(xp(tj) + m * NO + jc));
-        }
-        warp_sum<NO>(part);
-        if (lane == 0) {
-          zd rhs[NO], x[NO];
-#pragma unroll
-          for (int m = 0; m < NO; ++m) rhs[m] = part[m] + farsh[tl][m] + ld(qs + (long long)t * NO2 + m * NO + jc);
-          const double wt = h * rule_w(W, t, t);
-          const double2* sd = comp ? Lf<NO>(d, 2, n, jl, t, t) : el<NO>(d.SR, d, n, t, t);
-          const double2* ep = epsp<NO>(d, n, t);
-          M<NO> Mm;
-#pragma unroll
-          for (int x2 = 0; x2 < NO; ++x2)
-#pragma unroll
-            for (int y = 0; y < NO; ++y)
-              Mm.a[x2][y] = (x2 == y ? zd(0, W.a[0] / h) : zd()) - ld(ep + x2 * NO + y) - ld(sd + x2 * NO + y) * wt;
-          solve_col<NO>(Mm, rhs, x);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            double2* p = xp(t) + m * NO + jc;
-            myerr = fmax(myerr, sqrt((x[m] - ld(p)).abs2()));
-            st(p, x[m]);
-            xch[tl][m] = x[m];
-          }
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    t0 = t1;
-  }
-  myerr = warp_max(myerr);
-  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
-  __syncthreads();
-  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
-}
 
 // ---------------------------------------------------------------------------
 // Lesser source with compressed Sigma^< (two-sided HODLR matvec).
@@ -607,7 +41,7 @@ __device__ __forceinline__ double2* Psrc(const Dev& d, int n, int b, int p, int 
 }
 
 template <int NO>
-__global__ void k_src_proj(Dev d, int T) {
+__global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int b = blockIdx.x, n = blockIdx.y;
   if (!d.active[n]) return;
@@ -615,29 +49,35 @@ __global__ void k_src_proj(Dev d, int T) {
   if (d.b_r0[b] >= c) return;
   const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c), c0 = d.b_c0[b], c1 = d.b_c1[b];
   const DevW& W = d.w;
-  for (int idx = threadIdx.x; idx < NO2 * NO * d.rmax; idx += blockDim.x) {
-    // P1 serves pair p = (x, z) (uses g[z]), P2 serves pair p = (z, x) (uses g[z])
-    const int q = idx % d.rmax, y = (idx / d.rmax) % NO, p = idx / (d.rmax * NO);
-    const int z1 = p % NO, z2 = p / NO;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ zd pbuf[8][128];
+  // P1 serves pair p = (x, z) (uses g[z]); P2 serves pair p = (z, x) (uses g[z]);
+  // g_l[z][y] = conj(G^R(T,l)[y][z]).  Warps over rows / columns, lanes over rank.
+  for (int job = 0; job < NO2 * NO * 2; ++job) {
+    const int which = job & 1, y = (job >> 1) % NO, p = (job >> 1) / NO;
+    const int z = which == 0 ? p % NO : p / NO;
     const int rk = *Rk<NO>(d, 3, n, b, p);
-    zd a1 = zd(), a2 = zd();
-    if (q < rk) {
-      const double2* U = Up<NO>(d, 3, n, b, p) + q;
-      const double2* V = Vp<NO>(d, 3, n, b, p) + q;
-      for (int l = r0; l < rl; ++l) {  // g_l[z][y] = conj(G^R(T,l)[y][z])
-        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z1).conj() * rule_w(W, T, l);
-        a1 = cfma(g, ld(U + (long long)(l - r0) * d.rmax), a1);
+    const double2* F = which == 0 ? Up<NO>(d, 3, n, b, p) : Vp<NO>(d, 3, n, b, p);
+    const int lo = which == 0 ? r0 : c0, hi = which == 0 ? rl : c1;
+    zd part[4] = {zd(), zd(), zd(), zd()};
+    for (int l = lo + warp; l < hi; l += 8) {
+      const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+      const double2* fr = F + (long long)(l - lo) * d.rmax;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = lane + 32 * u;
+        if (q < rk) part[u] = cfma(g, ld(fr + q), part[u]);
       }
-      for (int l = c0; l < c1; ++l) {
-        const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z2).conj() * rule_w(W, T, l);
-        a2 = cfma(g, ld(V + (long long)(l - c0) * d.rmax), a2);
-      }
-      const double sv = Sp<NO>(d, 3, n, b, p)[q];
-      a1 = a1 * sv;
-      a2 = a2 * sv;
     }
-    st(Psrc<NO>(d, n, b, p, y, 0) + q, a1);
-    st(Psrc<NO>(d, n, b, p, y, 1) + q, a2);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+    __syncthreads();
+    if (tid < d.rmax) {
+      zd acc = zd();
+      for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][tid];
+      st(Psrc<NO>(d, n, b, p, y, which) + tid, tid < rk ? acc * Sp<NO>(d, 3, n, b, p)[tid] : zd());
+    }
+    __syncthreads();
   }
 }
 
@@ -1082,16 +522,6 @@ __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
     default: return cudaErrorInvalidValue;           \
   }
 
-cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
-  dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_ret_h<NO><<<g, 256, 0, s>>>(d, T)));
-  return cudaGetLastError();
-}
-cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
-  dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_les_h<NO><<<g, 256, 0, s>>>(d, T)));
-  return cudaGetLastError();
-}
 cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s) {
   if (d.cdir > 0) {
     dim3 g(d.nblk, d.n_inst);

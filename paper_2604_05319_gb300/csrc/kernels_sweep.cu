@@ -1,0 +1,742 @@
+// The two Volterra sweeps of a time step (Eq. KBER retarded row, Eq. KBEL
+// lesser column) for both storage forms (dense triangles, or HODLR with a
+// ring of uncompressed rows), organised in 32-point chunks at fixed absolute
+// positions.
+//
+// Within one chunk the unknowns couple through the near-diagonal part of the
+// discretised equation: the BDF stencil, eps, and Sigma^R entries inside the
+// chunk with their Gregory weights.  Once every coefficient of that local
+// system is final and its weights no longer depend on T, the system is frozen
+// and its inverse is computed once (k_chunk_inv) and reused at every later
+// iteration and step:
+//   retarded chunk [a, a+32): frozen when a + 32 + 2k <= T (all points see the
+//     standard Gregory weights at their end of the integral, and no row of the
+//     chunk is within k of T);
+//   lesser chunk [a, a+32): frozen when a + 32 <= T (its rows are final; the
+//     lesser weights depend on the row and column only).  Chunk 0 holds rows
+//     1..31 including the start block.
+// A chunk's solve is then F times the inverse (retarded, row vector) or the
+// inverse times F (lesser), where F holds everything outside the chunk (the
+// far field).  Only the chunks near T are solved point by point in one warp.
+#include "hodlr_util.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr int CK = 32;   // chunk length
+
+template <int NO>
+__device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which) {
+  const long long nn = (long long)(CK * NO) * (CK * NO);
+  return d.cinv + (((long long)n * d.nchunk + cc) * 2 + which) * nn;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Retarded row, Eq. KBER: unknown y(t') = G^R(T, t') (row irow), solved for
+// t' = T-1 .. 0; the start block t' >= T-k is solved together.
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, irow = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k, c = d.cdir, L = d.L;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd FB[64][NO];
+  __shared__ zd pbuf[8][128];
+  __shared__ zd Fs[CK][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* rowp = el<NO>(d.GR, d, n, T, 0);
+  auto yp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };
+  double myerr = 0.0;
+  // ---- start block t' = T-k .. T-1 (s = 1..k), and y(T) = -i ----
+  const int ns = k * NO;
+  if (warp == 0) {
+    for (int e = lane; e < ns * ns; e += 32) {
+      const int row = e / ns, col = e % ns;
+      const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
+      zd v = srx_any<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
+      if (m == j) v += zd(0, W.D[s][l] / h);
+      if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
+      sA[row * ns + col] = v;
+    }
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      zd cc = srx_any<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
+      if (irow == j) cc += zd(0, W.D[s][0] / h);
+      sB[row] = zd(0, 1) * cc;
+    }
+    __syncwarp();
+    warp_lu_solve(ns, sA, sB, 1, nullptr);
+    for (int row = lane; row < ns; row += 32) {
+      const int s = row / NO + 1, j = row % NO;
+      double2* p = yp(T - s) + j;
+      myerr = fmax(myerr, (sB[row] - ld(p)).abs2());
+      st(p, sB[row]);
+    }
+    if (lane == 0) {
+      double2* p = yp(T);
+      for (int j = 0; j < NO; ++j) {
+        zd v = (j == irow) ? zd(0, -1) : zd();
+        myerr = fmax(myerr, (ld(p + j) - v).abs2());
+        st(p + j, v);
+      }
+    }
+  }
+  __syncthreads();
+  const int top = T - k - 1;
+  for (int cc = top / CK; cc >= 0; --cc) {
+    const int a = cc * CK, b = min(a + CK, top + 1), cn = b - a;
+    const bool comp = (c > 0 && b <= c);
+    const int jl = comp ? a / L : 0, A = jl * L, E = comp ? (jl + 1) * L : 0;
+    if (comp && b == E) {
+      // Entering leaf jl from above.  (1) projections pi_B = sum_s y(s) U_B(s,:) S_B
+      // of the blocks whose columns end at E, rows summed in 4 slices.
+      for (int lv = 0; lv < d.maxl; ++lv) {
+        const int blk = d.colblk[jl * d.maxl + lv];
+        if (blk < 0 || d.b_c1[blk] != E) continue;
+        const int r0 = d.b_r0[blk], rl = min(d.b_r1[blk], c);
+        for (int p = 0; p < NO2; ++p) {
+          const int m = p / NO;
+          const int rk = *Rk<NO>(d, 2, n, blk, p);
+          const double2* U = Up<NO>(d, 2, n, blk, p);
+          zd part[4] = {zd(), zd(), zd(), zd()};
+          for (int s2 = r0 + warp; s2 < rl; s2 += 8) {  // warps over rows, lanes over rank
+            const zd yv = ld(yp(s2) + m);
+            const double2* ur = U + (long long)(s2 - r0) * d.rmax;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = lane + 32 * u;
+              if (q < rk) part[u] = cfma(yv, ld(ur + q), part[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+          __syncthreads();
+          if (tid < d.rmax) {
+            zd acc = zd();
+            for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][tid];
+            st(Pj<NO>(d, n, irow, lv, p) + tid, tid < rk ? acc * Sp<NO>(d, 2, n, blk, p)[tid] : zd());
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      // (2) for every column of the leaf: uncompressed rows s in [c, T], the
+      // blocks below the leaf (weight 1) and the near-diagonal corrections;
+      // 4 threads per column.
+      {
+        const int col = tid >> 2, sl = tid & 3;
+        zd acc[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) acc[j] = zd();
+        const int tp = A + col;
+        if (col < L) {
+          for (int s2 = c + sl; s2 <= T; s2 += 4) {
+            const double ws = rule_w(W, T - tp, T - s2);
+            const double2* yl = yp(s2);
+            const double2* sr = el<NO>(d.SR, d, n, s2, tp);
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              const zd ym = ld(yl + m) * ws;
+#pragma unroll
+              for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+            }
+          }
+          for (int lv = 0; lv < d.maxl; ++lv) {
+            const int blk = d.colblk[jl * d.maxl + lv];
+            if (blk < 0 || d.b_r0[blk] >= c) continue;
+            const int c0 = d.b_c0[blk];
+#pragma unroll
+            for (int p = 0; p < NO2; ++p) {
+              const int j = p % NO;
+              const int rk = *Rk<NO>(d, 2, n, blk, p);
+              const double2* V = Vp<NO>(d, 2, n, blk, p) + (long long)(tp - c0) * d.rmax;
+              const double2* P = Pj<NO>(d, n, irow, lv, p);
+              for (int q = sl; q < rk; q += 4) acc[j] = cfma(ld(P + q), ld(V + q).conj(), acc[j]);
+            }
+          }
+          for (int s2 = E + sl; s2 <= tp + k && s2 < c; s2 += 4) {
+            const double ws = rule_w(W, T - tp, T - s2) - 1.0;
+            const double2* bd = Bd<NO>(d, n, s2, s2 - tp);
+            const double2* yl = yp(s2);
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              const zd ym = ld(yl + m) * ws;
+#pragma unroll
+              for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(bd + m * NO + j), acc[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, 1), __shfl_xor_sync(FULL, acc[j].im, 1));
+          acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, 2), __shfl_xor_sync(FULL, acc[j].im, 2));
+        }
+        if (sl == 0 && col < L)
+#pragma unroll
+          for (int j = 0; j < NO; ++j) FB[col][j] = acc[j];
+      }
+      __syncthreads();
+    }
+    // ---- far field of the chunk: rows s >= b not covered above; 8 threads per column ----
+    {
+      const int col = tid >> 3, sl = tid & 7;
+      const int tp = a + col;
+      zd acc[NO];
+#pragma unroll
+      for (int j = 0; j < NO; ++j) acc[j] = zd();
+      if (col < cn) {
+        const int s_end = comp ? E : T + 1;   // compressed: the rest of the leaf; else every later row
+        for (int s2 = b + sl; s2 < s_end; s2 += 8) {
+          const double ws = rule_w(W, T - tp, T - s2);
+          const double2* yl = yp(s2);
+          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, s2, tp) : el<NO>(d.SR, d, n, s2, tp);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            const zd ym = ld(yl + m) * ws;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NO; ++j)
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1)
+          acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, off), __shfl_xor_sync(FULL, acc[j].im, off));
+      if (sl == 0 && col < cn) {
+        zd F[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) F[j] = (acc[j] + (comp ? FB[tp - A][j] : zd())) * h;
+        for (int jj = 1; jj <= k; ++jj) {  // BDF terms reaching above the chunk
+          const int s2 = tp + jj;
+          if (s2 < b) continue;
+          const zd cf(0, -W.a[jj] / h);
+#pragma unroll
+          for (int m = 0; m < NO; ++m) F[m] += cf * ld(yp(s2) + m);
+        }
+#pragma unroll
+        for (int j = 0; j < NO; ++j) Fs[col][j] = F[j];
+      }
+    }
+    __syncthreads();
+    if (cc < d.nfrozR) {
+      // frozen chunk: y = F C^-1 (row vector times the precomputed inverse),
+      // 8 threads per output element
+      const double2* Mi = Cinv<NO>(d, n, cc, 0);
+      constexpr int LD = CK * NO;
+      for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
+        const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, j = o % NO;
+        zd sacc = zd();
+        for (int si = sl; si < CK; si += 8)
+#pragma unroll
+          for (int m = 0; m < NO; ++m) sacc = cfma(Fs[si][m], ld(Mi + (long long)(si * NO + m) * LD + ti * NO + j), sacc);
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1)
+          sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
+        if (sl == 0) {
+          double2* p = yp(a + ti) + j;
+          myerr = fmax(myerr, (sacc - ld(p)).abs2());
+          st(p, sacc);
+        }
+      }
+    } else if (warp == 0) {
+      // chunk near T: right-looking triangular solve in one warp.  Lane L owns
+      // t'' = a + L; after point s is solved every lane with t'' < s removes
+      // y(s) C(s, t'') from its right-hand side.
+      const int L0 = lane, tq = a + L0;
+      M<NO> Dinv;
+      zd f[NO];
+      if (L0 < cn) {
+        const double ws = h * rule_w(W, T - tq, T - tq);
+        const double2* sd = comp ? Lf<NO>(d, 2, n, jl, tq, tq) : el<NO>(d.SR, d, n, tq, tq);
+        const double2* ep = epsp<NO>(d, n, tq);
+        M<NO> Mm;
+#pragma unroll
+        for (int x = 0; x < NO; ++x)
+#pragma unroll
+          for (int y2 = 0; y2 < NO; ++y2)
+            Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
+        Dinv = solve_left<NO>(Mm, M<NO>::eye(zd(1.0)));
+#pragma unroll
+        for (int j = 0; j < NO; ++j) f[j] = Fs[L0][j];
+      }
+      for (int i = cn - 1; i >= 0; --i) {
+        const int sp = a + i;
+        // coefficient C(sp, tq) for this lane (only lanes with tq < sp use it)
+        zd cf[NO2];
+        if (L0 < i) {
+          const double wl = -h * rule_w(W, T - tq, T - sp);
+          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, sp, tq) : el<NO>(d.SR, d, n, sp, tq);
+          const int dd = sp - tq;
+#pragma unroll
+          for (int q = 0; q < NO2; ++q) {
+            cf[q] = ld(sr + q) * wl;
+            if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+          }
+        }
+        zd y[NO];
+        if (L0 == i) {
+#pragma unroll
+          for (int j = 0; j < NO; ++j) {
+            y[j] = zd();
+#pragma unroll
+            for (int m = 0; m < NO; ++m) y[j] = cfma(f[m], Dinv.a[m][j], y[j]);
+          }
+          double2* p = yp(sp);
+#pragma unroll
+          for (int j = 0; j < NO; ++j) {
+            myerr = fmax(myerr, (y[j] - ld(p + j)).abs2());
+            st(p + j, y[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NO; ++j) y[j] = zd(__shfl_sync(FULL, y[j].re, i), __shfl_sync(FULL, y[j].im, i));
+        if (L0 < i) {
+#pragma unroll
+          for (int m = 0; m < NO; ++m)
+#pragma unroll
+            for (int j = 0; j < NO; ++j) f[j] -= y[m] * cf[m * NO + j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  myerr = sqrt(warp_max(myerr));
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Lesser column, Eq. KBEL: unknown x(t) = G^<(t, T) (column jc), t = 0..T.
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.y, jc = blockIdx.x;
+  if (!d.active[n]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k, c = d.cdir, L = d.L;
+  const double h = d.h;
+  const DevW& W = d.w;
+  __shared__ zd sA[20 * 20];
+  __shared__ zd sB[20];
+  __shared__ zd FB[64][NO];
+  __shared__ zd pbuf[8][128];
+  __shared__ zd Fs[CK][NO];
+  __shared__ double serr;
+  if (tid == 0) serr = 0.0;
+  double2* colp = el<NO>(d.GL, d, n, T, 0);
+  auto xp = [&](int t) { return colp + (long long)t * NO2; };  // element [m*NO + jc]
+  const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
+  double myerr = 0.0;
+  const int last = (d.rho_mode == 1) ? T - 1 : T;
+  if (warp == 0 && lane < NO) {  // x(0) = -[G^tv(T, 0+)]^dagger
+    const int m = lane;
+    zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
+    double2* p = xp(0) + m * NO + jc;
+    myerr = fmax(myerr, (v - ld(p)).abs2());
+    st(p, v);
+  }
+  __syncthreads();
+  for (int cc = 0; cc * CK <= last; ++cc) {
+    const int a = (cc == 0) ? 1 : cc * CK, b = min((cc + 1) * CK, last + 1), cn = b - a;
+    if (cn <= 0) break;
+    const bool comp = (c > 0 && b <= c);
+    const int jl = comp ? a / L : 0, A = jl * L;
+    if (comp && cc * CK == A) {
+      // Entering leaf jl.  (1) rho_B = S_B sum_l w_l conj(V_B(l,:)) x(l) for the
+      // blocks whose rows start at A (w_l = omega_l for l <= k, else 1).
+      for (int lv = 0; lv < d.maxl && jl > 0; ++lv) {
+        const int blk = d.rowblk[jl * d.maxl + lv];
+        if (blk < 0 || d.b_r0[blk] != A) continue;
+        const int c0 = d.b_c0[blk], c1 = d.b_c1[blk];
+        for (int p = 0; p < NO2; ++p) {
+          const int nn = p % NO;
+          const int rk = *Rk<NO>(d, 2, n, blk, p);
+          const double2* V = Vp<NO>(d, 2, n, blk, p);
+          zd part[4] = {zd(), zd(), zd(), zd()};
+          for (int l = c0 + warp; l < c1; l += 8) {  // warps over columns, lanes over rank
+            const double wl = (l <= k) ? W.omega[l] : 1.0;
+            const zd xv = ld(xp(l) + nn * NO + jc) * wl;
+            const double2* vr = V + (long long)(l - c0) * d.rmax;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = lane + 32 * u;
+              if (q < rk) part[u] = cfma(ld(vr + q).conj(), xv, part[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+          __syncthreads();
+          if (tid < d.rmax) {
+            zd acc = zd();
+            for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][tid];
+            st(Pj<NO>(d, n, jc, lv, p) + tid, tid < rk ? acc * Sp<NO>(d, 2, n, blk, p)[tid] : zd());
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      // (2) every row of the leaf: blocks left of it and near-diagonal corrections
+      {
+        const int row = tid >> 2, sl = tid & 3;
+        const int t = A + row;
+        zd acc[NO];
+#pragma unroll
+        for (int m = 0; m < NO; ++m) acc[m] = zd();
+        if (row < L) {
+          for (int lv = 0; lv < d.maxl; ++lv) {
+            const int blk = d.rowblk[jl * d.maxl + lv];
+            if (blk < 0) continue;
+            const int r0 = d.b_r0[blk];
+#pragma unroll
+            for (int p = 0; p < NO2; ++p) {
+              const int m = p / NO;
+              const int rk = *Rk<NO>(d, 2, n, blk, p);
+              const double2* U = Up<NO>(d, 2, n, blk, p) + (long long)(t - r0) * d.rmax;
+              const double2* P = Pj<NO>(d, n, jc, lv, p);
+              for (int q = sl; q < rk; q += 4) acc[m] = cfma(ld(U + q), ld(P + q), acc[m]);
+            }
+          }
+          for (int l = max(t - k, 0) + sl; l < A; l += 4) {
+            const double wl = rule_w(W, t, l) - 1.0;
+            const double2* bd = Bd<NO>(d, n, t, t - l);
+#pragma unroll
+            for (int y = 0; y < NO; ++y) {
+              const zd xy = ld(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+              for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(bd + m * NO + y), xy, acc[m]);
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < NO; ++m) {
+          acc[m] += zd(__shfl_xor_sync(FULL, acc[m].re, 1), __shfl_xor_sync(FULL, acc[m].im, 1));
+          acc[m] += zd(__shfl_xor_sync(FULL, acc[m].re, 2), __shfl_xor_sync(FULL, acc[m].im, 2));
+        }
+        if (sl == 0 && row < L)
+#pragma unroll
+          for (int m = 0; m < NO; ++m) FB[row][m] = acc[m];
+      }
+      __syncthreads();
+    }
+    // ---- far field F(t) = q(t) - sum_{l < a} C(t,l) x(l); 8 threads per row ----
+    {
+      const int row = tid >> 3, sl = tid & 7;
+      const int t = a + row;
+      zd acc[NO];
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[m] = zd();
+      if (row < cn) {
+        if (t <= k) {
+          if (sl == 0) {  // start rows: only l = 0 lies left of chunk 0
+            for (int y = 0; y < NO; ++y) {
+              const zd xv = ld(xp(0) + y * NO + jc);
+#pragma unroll
+              for (int m = 0; m < NO; ++m) {
+                zd cf = srx_any<NO>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
+                if (m == y) cf += zd(0, W.D[t][0] / h);
+                acc[m] -= cf * xv;
+              }
+            }
+          }
+        } else {
+          const int l0 = comp ? A : 0;
+          const double2* srow = comp ? nullptr : el<NO>(d.SR, d, n, t, 0);
+          for (int l = l0 + sl; l < a; l += 8) {
+            const double wl = h * rule_w(W, t, l);
+            const double2* sr = comp ? Lf<NO>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
+#pragma unroll
+            for (int y = 0; y < NO; ++y) {
+              const zd xy = ld(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+              for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
+            }
+          }
+          if (sl == 1) {  // BDF terms reaching left of the chunk
+            for (int jj = 1; jj <= k; ++jj) {
+              if (t - jj >= a) continue;
+              const zd cf(0, -W.a[jj] / h);
+#pragma unroll
+              for (int m = 0; m < NO; ++m) acc[m] += cf * ld(xp(t - jj) + m * NO + jc);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < NO; ++m)
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1)
+          acc[m] += zd(__shfl_xor_sync(FULL, acc[m].re, off), __shfl_xor_sync(FULL, acc[m].im, off));
+      if (sl == 0 && row < cn)
+#pragma unroll
+        for (int m = 0; m < NO; ++m)
+          Fs[row][m] = acc[m] + (comp && t > k ? FB[t - A][m] * h : zd()) + ld(qs + (long long)t * NO2 + m * NO + jc);
+    }
+    __syncthreads();
+    const bool frozen = (cc < d.nfrozL) && (b - a == ((cc == 0) ? CK - 1 : CK));
+    if (frozen) {
+      const double2* Mi = Cinv<NO>(d, n, cc, 1);
+      constexpr int LD = CK * NO;
+      for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
+        const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, m = o % NO;
+        zd sacc = zd();
+        if (ti < cn)
+          for (int li = sl; li < cn; li += 8)
+#pragma unroll
+            for (int y = 0; y < NO; ++y) sacc = cfma(ld(Mi + (long long)(ti * NO + m) * LD + li * NO + y), Fs[li][y], sacc);
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1)
+          sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
+        if (sl == 0 && ti < cn) {
+          double2* p = xp(a + ti) + m * NO + jc;
+          myerr = fmax(myerr, (sacc - ld(p)).abs2());
+          st(p, sacc);
+        }
+      }
+    } else if (warp == 0) {
+      // chunk near T: right-looking triangular solve in one warp; lane L owns
+      // row t'' = a + L.  Chunk 0 first solves its start block t = 1..k.
+      const int L0 = lane, tq = a + L0;
+      int i0 = 0;
+      zd f[NO];
+      if (L0 < cn)
+#pragma unroll
+        for (int m = 0; m < NO; ++m) f[m] = Fs[L0][m];
+      if (cc == 0) {
+        const int nsb = k * NO;
+        for (int e = lane; e < nsb * nsb; e += 32) {
+          const int row = e / nsb, col = e % nsb;
+          const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
+          zd v = srx_any<NO>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
+          if (m == y) v += zd(0, W.D[t][l] / h);
+          if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
+          sA[row * nsb + col] = v;
+        }
+        for (int row = lane; row < nsb; row += 32) sB[row] = Fs[row / NO][row % NO];
+        __syncwarp();
+        warp_lu_solve(nsb, sA, sB, 1, nullptr);
+        for (int row = lane; row < nsb; row += 32) {
+          const int t = row / NO + 1, m = row % NO;
+          if (t <= last) {
+            double2* p = xp(t) + m * NO + jc;
+            myerr = fmax(myerr, (sB[row] - ld(p)).abs2());
+            st(p, sB[row]);
+          }
+        }
+        __syncwarp();
+        if (L0 < cn && tq > k) {  // rows below the start block remove its contribution
+          for (int l = 1; l <= k; ++l) {
+            const double wl = -h * rule_w(W, tq, l);
+            const double2* sr = comp ? Lf<NO>(d, 2, n, jl, tq, l) : el<NO>(d.SR, d, n, tq, l);
+            const int dd = tq - l;
+#pragma unroll
+            for (int m = 0; m < NO; ++m)
+#pragma unroll
+              for (int y = 0; y < NO; ++y) {
+                zd cfv = ld(sr + m * NO + y) * wl;
+                if (dd <= k && m == y) cfv += zd(0, W.a[dd] / h);
+                f[m] -= cfv * sB[(l - 1) * NO + y];
+              }
+          }
+        }
+        i0 = k;  // rows a..k (a = 1) are done
+      }
+      M<NO> Dinv;
+      if (L0 < cn && L0 >= i0) {
+        const double wt = h * rule_w(W, tq, tq);
+        const double2* sd = comp ? Lf<NO>(d, 2, n, jl, tq, tq) : el<NO>(d.SR, d, n, tq, tq);
+        const double2* ep = epsp<NO>(d, n, tq);
+        M<NO> Mm;
+#pragma unroll
+        for (int x2 = 0; x2 < NO; ++x2)
+#pragma unroll
+          for (int y = 0; y < NO; ++y)
+            Mm.a[x2][y] = (x2 == y ? zd(0, W.a[0] / h) : zd()) - ld(ep + x2 * NO + y) - ld(sd + x2 * NO + y) * wt;
+        Dinv = solve_left<NO>(Mm, M<NO>::eye(zd(1.0)));
+      }
+      for (int i = i0; i < cn; ++i) {
+        const int tp = a + i;
+        zd cf[NO2];
+        if (L0 > i && L0 < cn) {
+          const double wl = -h * rule_w(W, tq, tp);
+          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, tq, tp) : el<NO>(d.SR, d, n, tq, tp);
+          const int dd = tq - tp;
+#pragma unroll
+          for (int q = 0; q < NO2; ++q) {
+            cf[q] = ld(sr + q) * wl;
+            if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+          }
+        }
+        zd x[NO];
+        if (L0 == i) {
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            x[m] = zd();
+#pragma unroll
+            for (int y = 0; y < NO; ++y) x[m] = cfma(Dinv.a[m][y], f[y], x[m]);
+          }
+#pragma unroll
+          for (int m = 0; m < NO; ++m) {
+            double2* p = xp(tp) + m * NO + jc;
+            myerr = fmax(myerr, (x[m] - ld(p)).abs2());
+            st(p, x[m]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < NO; ++m) x[m] = zd(__shfl_sync(FULL, x[m].re, i), __shfl_sync(FULL, x[m].im, i));
+        if (L0 > i && L0 < cn) {
+#pragma unroll
+          for (int m = 0; m < NO; ++m)
+#pragma unroll
+            for (int y = 0; y < NO; ++y) f[m] -= cf[m * NO + y] * x[y];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  myerr = sqrt(warp_max(myerr));
+  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
+  __syncthreads();
+  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+}
+
+// ---------------------------------------------------------------------------
+// Inverse of a frozen chunk's local system, by Gauss-Jordan with partial
+// pivoting (FP64), one CTA per instance.  Retarded (which 0): unknowns
+// y(t'), t' in [a, a+32), matrix C[(s,m),(t',j)] = (i/h) a_{s-t'} [0 <= s-t' <= k]
+// delta_mj - delta_{s t'} eps(t')_mj - h w(s-t') Sigma^R(s,t')_mj with the
+// standard Gregory end weight w(d) = omega_d (d <= k) else 1.  Lesser (which 1):
+// unknowns x(t), rows t of the chunk; rows t <= k are the start equations with
+// D and I_{0,t,.}, other rows the BDF/Gregory equation with the weights w^(t)_l.
+// ---------------------------------------------------------------------------
+template <int NO>
+__global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, double2* ws) {
+  const int n = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = d.k;
+  const double h = d.h;
+  const DevW& W = d.w;
+  const int a = (which == 1 && cc == 0) ? 1 : cc * CK;
+  const int cnt = (which == 1 && cc == 0) ? CK - 1 : CK;
+  const int nn = cnt * NO;
+  constexpr int LD = CK * NO;
+  double2* B = Cinv<NO>(d, n, cc, which);
+  double2* Am = ws + (long long)n * LD * LD;
+  __shared__ zd fcol[CK * 4];
+  __shared__ int s_piv;
+  __shared__ zd s_inv;
+  for (int e = tid; e < nn * nn; e += blockDim.x) {
+    const int r = e / nn, col = e % nn;
+    const int ri = r / NO, m = r % NO, ci = col / NO, j = col % NO;
+    zd v = zd();
+    if (which == 0) {
+      const int s = a + ri, tp = a + ci, dd = s - tp;
+      if (dd >= 0) {
+        const double wf = (dd <= k) ? W.omega[dd] : 1.0;
+        v = sr_any<NO>(d, n, s, tp, m, j) * (-h * wf);
+        if (dd <= k && m == j) v += zd(0, W.a[dd] / h);
+        if (dd == 0) v -= ld(epsp<NO>(d, n, tp) + m * NO + j);
+      }
+    } else {
+      const int t = a + ri, l = a + ci;
+      if (t <= k) {
+        if (l <= k) {
+          v = srx_any<NO>(d, n, t, l, m, j) * (-h * W.I0[t][l]);
+          if (m == j) v += zd(0, W.D[t][l] / h);
+          if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + j);
+        }
+      } else if (l <= t) {
+        v = sr_any<NO>(d, n, t, l, m, j) * (-h * rule_w(W, t, l));
+        if (t - l <= k && m == j) v += zd(0, W.a[t - l] / h);
+        if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + j);
+      }
+    }
+    st(Am + (long long)r * LD + col, v);
+    st(B + (long long)r * LD + col, (r == col) ? zd(1.0) : zd());
+  }
+  __syncthreads();
+  for (int piv = 0; piv < nn; ++piv) {
+    if (warp == 0) {
+      double best = -1.0;
+      int arg = piv;
+      for (int r = piv + lane; r < nn; r += 32) {
+        const double v = ld(Am + (long long)r * LD + piv).abs2();
+        if (v > best) { best = v; arg = r; }
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const double b2 = __shfl_xor_sync(0xffffffffu, best, off);
+        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+        if (b2 > best || (b2 == best && a2 < arg)) { best = b2; arg = a2; }
+      }
+      if (lane == 0) s_piv = arg;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != piv) {
+      for (int j = tid; j < nn; j += blockDim.x) {
+        double2 t1 = Am[(long long)piv * LD + j]; Am[(long long)piv * LD + j] = Am[(long long)p * LD + j]; Am[(long long)p * LD + j] = t1;
+        double2 t2 = B[(long long)piv * LD + j]; B[(long long)piv * LD + j] = B[(long long)p * LD + j]; B[(long long)p * LD + j] = t2;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_inv = cdiv(zd(1.0), ld(Am + (long long)piv * LD + piv));
+    __syncthreads();
+    for (int j = tid; j < nn; j += blockDim.x) {
+      st(Am + (long long)piv * LD + j, ld(Am + (long long)piv * LD + j) * s_inv);
+      st(B + (long long)piv * LD + j, ld(B + (long long)piv * LD + j) * s_inv);
+    }
+    for (int r = tid; r < nn; r += blockDim.x) fcol[r] = ld(Am + (long long)r * LD + piv);
+    __syncthreads();
+    for (int e = tid; e < nn * nn; e += blockDim.x) {
+      const int r = e / nn, j = e % nn;
+      if (r == piv) continue;
+      const zd f = fcol[r];
+      st(Am + (long long)r * LD + j, ld(Am + (long long)r * LD + j) - f * ld(Am + (long long)piv * LD + j));
+      st(B + (long long)r * LD + j, ld(B + (long long)r * LD + j) - f * ld(B + (long long)piv * LD + j));
+    }
+    __syncthreads();
+  }
+}
+
+#define HK_DISPATCH(NOV, CALL)                       \
+  switch (NOV) {                                     \
+    case 1: { constexpr int NO = 1; CALL; break; }   \
+    case 2: { constexpr int NO = 2; CALL; break; }   \
+    case 3: { constexpr int NO = 3; CALL; break; }   \
+    case 4: { constexpr int NO = 4; CALL; break; }   \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_ret2<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
+  dim3 g(d.no, d.n_inst);
+  HK_DISPATCH(d.no, (k_les2<NO><<<g, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s) {
+  for (int cc = c0; cc < c1; ++cc) {
+    HK_DISPATCH(d.no, (k_chunk_inv<NO><<<d.n_inst, 256, 0, s>>>(d, which, cc, d.cinv_ws)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace hk

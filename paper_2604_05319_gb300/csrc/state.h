@@ -43,6 +43,11 @@ struct Dev {
   double2* tsvd_ws;    // TSVD workspace, tsvd_ws_per entries per CTA
   long long tsvd_ws_per;
   int* status;         // [0] rank overflow count, [1] Jacobi non-convergence count
+  // frozen 32-point chunk inverses of the two sweeps (FP64): [n][nchunk][2][(32 no)^2]
+  double2* cinv;
+  double2* cinv_ws;    // [n][(32 no)^2] Gauss-Jordan workspace
+  int nchunk;          // ceil(nt / 32)
+  int nfrozR, nfrozL;  // chunks [0, nfroz) of each sweep have a valid inverse
   long long ntri;  // nt*(nt+1)/2
   double h, beta;
   DevW w;
@@ -79,5 +84,7 @@ cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s);
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s);
+// inverses of the frozen chunks [c0, c1) of sweep `which` (0 retarded, 1 lesser)
+cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s);
 
 }  // namespace hk
