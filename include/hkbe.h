@@ -55,7 +55,16 @@ enum {
 
 /* Storage / arithmetic of the history integrals. */
 enum {
-  HKBE_PREC_FP64 = 0      /* dense lower-triangular complex128 storage, FP64 */
+  HKBE_PREC_FP64 = 0,     /* complex128 storage of every two-time and mixed
+                             component (dense triangles or HODLR factors); FP64
+                             arithmetic throughout                               */
+  HKBE_PREC_MIXED = 1     /* complex64 storage of G, Sigma (two-time and mixed),
+                             HODLR factors, band and chunk inverses; every point
+                             solve, the TSVD core, weights, DLR matrices and
+                             accumulations stay FP64.  Expected deviation from
+                             the FP64 form: about 1e-6 relative (single-precision
+                             rounding of the stored history; a GPU design choice,
+                             the paper computes in FP64 throughout)             */
 };
 
 typedef struct {

@@ -23,6 +23,7 @@ ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "H
           -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM"}
 MODEL_NONE, MODEL_BETHE, MODEL_BATH = 0, 1, 2
 PREC_FP64 = 0
+PREC_MIXED = 1
 
 
 class HKBEError(RuntimeError):

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hkbe.h"
@@ -35,13 +36,17 @@ struct hkbe_s {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   // bootstrap snapshot for hkbe_rewind (rows 0..k of every component)
-  std::vector<double2> snap_gr, snap_gl, snap_sr, snap_sl, snap_tv, snap_stv;
+  // (raw bytes of the storage element type)
+  std::vector<char> snap_gr, snap_gl, snap_sr, snap_sl, snap_tv, snap_stv;
   // HODLR geometry (host copies) and row read-out buffers
   bool hodlr = false;
   std::vector<int> g_r0, g_r1, g_c0, g_c1, g_lvl, g_rowblk, g_colblk;
   std::vector<long long> g_uoff, g_voff, g_leafoff;
   double2 *rowbuf_r = nullptr, *rowbuf_l = nullptr;
   int* status_dev = nullptr;
+  // device arrays that make up the propagation state, zeroed by hkbe_rewind so
+  // that a rewound run starts from exactly the state that followed bootstrap
+  std::vector<std::pair<void*, size_t>> state_arrays;
 };
 
 namespace {
@@ -108,7 +113,52 @@ int dalloc(hkbe_t* h, T** p, size_t count) {
   return HKBE_OK;
 }
 
+// untyped allocation of `count` storage elements (double2 or float2)
+int dalloc_el(hkbe_t* h, void** p, size_t count) {
+  int rc = h->d.prec ? dalloc(h, reinterpret_cast<float2**>(p), count) : dalloc(h, reinterpret_cast<double2**>(p), count);
+  if (rc == HKBE_OK) h->state_arrays.push_back({*p, std::max<size_t>(count, 1) * (h->d.prec ? sizeof(float2) : sizeof(double2))});
+  return rc;
+}
+
+// mixed components: complex128 in both precision forms
+int dalloc_tv(hkbe_t* h, void** p, size_t count) {
+  int rc = dalloc(h, reinterpret_cast<double2**>(p), count);
+  if (rc == HKBE_OK) h->state_arrays.push_back({*p, std::max<size_t>(count, 1) * sizeof(double2)});
+  return rc;
+}
+
 int no2(const hkbe_t* h) { return h->p.nao * h->p.nao; }
+
+// bytes of one complex storage element
+size_t esz(const hkbe_t* h) { return h->d.prec ? sizeof(float2) : sizeof(double2); }
+char* elp(const hkbe_t* h, void* base, size_t off) { return static_cast<char*>(base) + off * esz(h); }
+
+// Copy `cnt` complex storage elements device -> host as interleaved doubles
+// (converted from float in the mixed form).  Synchronises the stream.
+cudaError_t d2h_el(hkbe_t* h, double* out, const char* src, size_t cnt) {
+  if (!h->d.prec) {
+    cudaError_t e = cudaMemcpyAsync(out, src, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(h->s);
+  }
+  std::vector<float> tmp(2 * cnt);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(float2), cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  if (e != cudaSuccess) return e;
+  for (size_t i = 0; i < 2 * cnt; ++i) out[i] = tmp[i];
+  return cudaSuccess;
+}
+// Copy `cnt` complex values (interleaved doubles) host -> device storage
+// (rounded to float in the mixed form).  Synchronises the stream.
+cudaError_t h2d_el(hkbe_t* h, char* dst, const double* in, size_t cnt) {
+  if (!h->d.prec) {
+    cudaError_t e = cudaMemcpyAsync(dst, in, cnt * sizeof(double2), cudaMemcpyHostToDevice, h->s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(h->s);
+  }
+  std::vector<float> tmp(2 * cnt);
+  for (size_t i = 0; i < 2 * cnt; ++i) tmp[i] = (float)in[i];
+  cudaError_t e = cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, h->s);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(h->s);
+}
 
 // Offset (in matrices) of element (T, 0) of instance n in a two-time array.
 size_t row_off(const hkbe_t* h, int n, int T) {
@@ -194,7 +244,8 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   if (p->n_inst < 1) return fail(nullptr, HKBE_ERR_ARG, "n_inst must be >= 1");
   if (!(p->h > 0) || !(p->beta > 0)) return fail(nullptr, HKBE_ERR_ARG, "h and beta must be > 0");
   if (p->rho_mode != 0 && p->rho_mode != 1) return fail(nullptr, HKBE_ERR_ARG, "rho_mode must be 0 or 1");
-  if (p->precision != HKBE_PREC_FP64) return fail(nullptr, HKBE_ERR_ARG, "unsupported precision");
+  if (p->precision != HKBE_PREC_FP64 && p->precision != HKBE_PREC_MIXED)
+    return fail(nullptr, HKBE_ERR_ARG, "precision must be HKBE_PREC_FP64 or HKBE_PREC_MIXED");
   if (p->max_iter < 1) return fail(nullptr, HKBE_ERR_ARG, "max_iter must be >= 1");
   if (p->svd_tol < 0) return fail(nullptr, HKBE_ERR_ARG, "svd_tol must be >= 0");
   if (p->svd_tol > 0) {
@@ -208,6 +259,7 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   Dev& d = h->d;
   d.nt = p->nt; d.k = p->k; d.no = p->nao; d.n_inst = p->n_inst; d.xi = p->xi;
   d.rho_mode = p->rho_mode; d.h = p->h; d.beta = p->beta; d.r = 0; d.model = 0;
+  d.prec = p->precision == HKBE_PREC_MIXED ? 1 : 0;
   d.ntri = (long long)p->nt * (p->nt + 1) / 2;
   hk::Weights w;
   hk::weights_build(p->k, &w);
@@ -233,15 +285,16 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
     d.tsvd_ws_per = 2LL * d.L * ncolmax + (long long)d.L * d.rmax + (long long)d.L * d.L + 2LL * ldk * ldk;
     const size_t ctas = N * 4 * d.maxl * n2;
     for (int X = 0; X < 4; ++X) {
-      if ((rc = dalloc(h, &d.hod[X].U, N * d.utot * d.rmax)) || (rc = dalloc(h, &d.hod[X].V, N * d.vtot * d.rmax)) ||
+      if ((rc = dalloc_el(h, &d.hod[X].U, N * d.utot * d.rmax)) || (rc = dalloc_el(h, &d.hod[X].V, N * d.vtot * d.rmax)) ||
           (rc = dalloc(h, &d.hod[X].S, N * d.nblk * n2 * d.rmax)) ||
-          (rc = dalloc(h, &d.hod[X].rank, N * d.nblk * n2)) || (rc = dalloc(h, &d.hod[X].leaf, N * d.leaftot * n2))) {
+          ((void)h->state_arrays.push_back({d.hod[X].S, N * d.nblk * n2 * d.rmax * sizeof(double)}), false) ||
+          (rc = dalloc(h, &d.hod[X].rank, N * d.nblk * n2)) || (rc = dalloc_el(h, &d.hod[X].leaf, N * d.leaftot * n2))) {
         g_create_error = h->err;
         hkbe_destroy(h);
         return rc;
       }
     }
-    if ((rc = dalloc(h, &d.band, N * d.nt * d.k * n2)) ||
+    if ((rc = dalloc_el(h, &d.band, N * d.nt * d.k * n2)) ||
         (rc = dalloc(h, &d.proj, N * d.no * d.maxl * n2 * d.rmax + N * d.nblk * n2 * d.no * 2 * d.rmax)) ||
         (rc = dalloc(h, &d.tsvd_ws, ctas * d.tsvd_ws_per)) || (rc = dalloc(h, &h->status_dev, 2)) ||
         (rc = dalloc(h, &h->rowbuf_r, (size_t)d.nt * n2)) || (rc = dalloc(h, &h->rowbuf_l, (size_t)d.nt * n2)) ||
@@ -256,19 +309,29 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
     }
     d.status = h->status_dev;
   }
+  if (d.prec) {
+    if ((rc = dalloc(h, &d.row64, (size_t)d.n_inst * 2 * d.nt * d.no * d.no)) ||
+        (rc = dalloc(h, &d.diag64, (size_t)d.n_inst * d.nt * d.no * d.no))) {
+      g_create_error = h->err;
+      hkbe_destroy(h);
+      return rc;
+    }
+    h->state_arrays.push_back({d.row64, (size_t)d.n_inst * 2 * d.nt * d.no * d.no * sizeof(double2)});
+    h->state_arrays.push_back({d.diag64, (size_t)d.n_inst * d.nt * d.no * d.no * sizeof(double2)});
+  }
   d.nchunk = (d.nt + 31) / 32;
   d.nfrozR = d.nfrozL = 0;
   {
     const size_t ld = 32 * (size_t)d.no;
     if ((rc = dalloc(h, &d.cinv, (size_t)d.n_inst * d.nchunk * 2 * ld * ld)) ||
-        (rc = dalloc(h, &d.cinv_ws, (size_t)d.n_inst * ld * ld))) {
+        (rc = dalloc(h, &d.cinv_ws, (size_t)d.n_inst * 2 * ld * ld))) {
       g_create_error = h->err;
       hkbe_destroy(h);
       return rc;
     }
   }
-  if ((rc = dalloc(h, &d.GR, tri)) || (rc = dalloc(h, &d.GL, tri)) || (rc = dalloc(h, &d.SR, tri)) ||
-      (rc = dalloc(h, &d.SL, tri)) ||
+  if ((rc = dalloc_el(h, &d.GR, tri)) || (rc = dalloc_el(h, &d.GL, tri)) || (rc = dalloc_el(h, &d.SR, tri)) ||
+      (rc = dalloc_el(h, &d.SL, tri)) ||
       (rc = dalloc(h, &d.eps, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
       (rc = dalloc(h, &d.mpar, (size_t)d.n_inst * hk::MP)) ||
       (rc = dalloc(h, &d.qsrc, (size_t)d.n_inst * d.nt * d.no * d.no)) ||
@@ -314,8 +377,8 @@ int hkbe_set_dlr(hkbe_t* h, int r, const double* tau, const double* omega) {
   int rc;
   if ((rc = dalloc(h, &d.tau, r)) || (rc = dalloc(h, &d.e0, r)) || (rc = dalloc(h, &d.ebeta, r)) ||
       (rc = dalloc(h, &d.rev, (size_t)r * r)) || (rc = dalloc(h, &d.q, (size_t)r * r)) ||
-      (rc = dalloc(h, &d.GTV, (size_t)d.n_inst * d.nt * r * n2)) ||
-      (rc = dalloc(h, &d.STV, (size_t)d.n_inst * d.nt * r * n2)) ||
+      (rc = dalloc_tv(h, &d.GTV, (size_t)d.n_inst * d.nt * r * n2)) ||
+      (rc = dalloc_tv(h, &d.STV, (size_t)d.n_inst * d.nt * r * n2)) ||
       (rc = dalloc(h, &d.gm, (size_t)d.n_inst * r * n2)) ||
       (rc = dalloc(h, &d.wconv, (size_t)d.n_inst * r * r * n2)) ||
       (rc = dalloc(h, &d.vvec, (size_t)d.n_inst * r * n2)))
@@ -469,10 +532,14 @@ static int hf_guess(hkbe_t* h) {
         }
       }
     const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2;
-    HK_CUDA(h, cudaMemcpyAsync(d.GR + (size_t)n * d.ntri * n2, gr.data(), sq * sizeof(double2), cudaMemcpyHostToDevice, h->s));
-    HK_CUDA(h, cudaMemcpyAsync(d.GL + (size_t)n * d.ntri * n2, gl.data(), sq * sizeof(double2), cudaMemcpyHostToDevice, h->s));
-    HK_CUDA(h, cudaMemcpyAsync(d.GTV + (size_t)n * d.nt * r * n2, gtv.data(), (size_t)(k + 1) * r * n2 * sizeof(double2),
-                               cudaMemcpyHostToDevice, h->s));
+    // rows 0..k, stored row by row (dense triangle or ring slots alike)
+    for (int t = 0; t <= k; ++t) {
+      const size_t o = (size_t)t * (t + 1) / 2 * n2 * 2, c = (size_t)(t + 1) * n2;
+      HK_CUDA(h, h2d_el(h, elp(h, d.GR, row_off(h, n, t)), gr.data() + o, c));
+      HK_CUDA(h, h2d_el(h, elp(h, d.GL, row_off(h, n, t)), gl.data() + o, c));
+    }
+    HK_CUDA(h, cudaMemcpyAsync(static_cast<double2*>(d.GTV) + (size_t)n * d.nt * r * n2, gtv.data(),
+                               (size_t)(k + 1) * r * n2 * sizeof(double2), cudaMemcpyHostToDevice, h->s));
     HK_CUDA(h, cudaStreamSynchronize(h->s));
   }
   return HKBE_OK;
@@ -553,21 +620,23 @@ int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* 
   {
     const int n2 = no2(h), k = d.k;
     const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
-    auto grab = [&](std::vector<double2>& dst, const double2* src) -> cudaError_t {
-      dst.resize(sq * d.n_inst);
+    const size_t es = esz(h);
+    auto grab = [&](std::vector<char>& dst, void* src) -> cudaError_t {
+      dst.resize(sq * d.n_inst * es);
       for (int n = 0; n < d.n_inst; ++n)
         for (int t = 0; t <= k; ++t) {
-          cudaError_t e = cudaMemcpyAsync(dst.data() + sq * n + (size_t)t * (t + 1) / 2 * n2, src + row_off(h, n, t),
-                                          (size_t)(t + 1) * n2 * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
+          cudaError_t e = cudaMemcpyAsync(dst.data() + (sq * n + (size_t)t * (t + 1) / 2 * n2) * es, elp(h, src, row_off(h, n, t)),
+                                          (size_t)(t + 1) * n2 * es, cudaMemcpyDeviceToHost, h->s);
           if (e != cudaSuccess) return e;
         }
       return cudaStreamSynchronize(h->s);
     };
-    auto grab_tv = [&](std::vector<double2>& dst, const double2* src) -> cudaError_t {
-      dst.resize(tvn * d.n_inst);
+    auto grab_tv = [&](std::vector<char>& dst, void* src) -> cudaError_t {
+      const size_t et = sizeof(double2);
+      dst.resize(tvn * d.n_inst * et);
       for (int n = 0; n < d.n_inst; ++n) {
-        cudaError_t e = cudaMemcpyAsync(dst.data() + tvn * n, src + (size_t)n * d.nt * d.r * n2,
-                                        tvn * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
+        cudaError_t e = cudaMemcpyAsync(dst.data() + tvn * n * et, static_cast<char*>(src) + (size_t)n * d.nt * d.r * n2 * et,
+                                        tvn * et, cudaMemcpyDeviceToHost, h->s);
         if (e != cudaSuccess) return e;
       }
       return cudaStreamSynchronize(h->s);
@@ -579,6 +648,7 @@ int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* 
     HK_CUDA(h, grab_tv(h->snap_tv, d.GTV));
     HK_CUDA(h, grab_tv(h->snap_stv, d.STV));
   }
+  HK_CUDA(h, hk::launch_diag_seed(d, h->s));
   h->cur = d.k;
   if (failed) return fail(h, HKBE_ERR_NOCONV, "bootstrap did not converge");
   return HKBE_OK;
@@ -668,14 +738,14 @@ int hkbe_current_step(const hkbe_t* h, int32_t* T) {
 // (either may be NULL); compressed rows are reconstructed on the device.
 static int fetch_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
   const size_t cnt = (size_t)(T + 1) * no2(h);
-  const hk::Dev& d = h->d;
+  hk::Dev& d = h->d;
   if (h->hodlr && T < d.cdir) {
     HK_CUDA(h, hk::launch_row_out(d, inst, T, gr ? h->rowbuf_r : nullptr, gl ? h->rowbuf_l : nullptr, h->s));
     if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, h->rowbuf_r, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
     if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, h->rowbuf_l, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
   } else {
-    if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, d.GR + row_off(h, inst, T), cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
-    if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, d.GL + row_off(h, inst, T), cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+    if (gr) HK_CUDA(h, d2h_el(h, gr, elp(h, d.GR, row_off(h, inst, T)), cnt));
+    if (gl) HK_CUDA(h, d2h_el(h, gl, elp(h, d.GL, row_off(h, inst, T)), cnt));
   }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
@@ -720,8 +790,8 @@ int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out) {
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
   if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
   const size_t cnt = (size_t)h->d.r * no2(h);
-  HK_CUDA(h, cudaMemcpyAsync(out, h->d.GTV + ((size_t)inst * h->d.nt + t) * cnt, cnt * sizeof(double2),
-                             cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(out, static_cast<double2*>(h->d.GTV) + ((size_t)inst * h->d.nt + t) * cnt,
+                             cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
 }
@@ -789,34 +859,39 @@ int hkbe_rewind(hkbe_t* h) {
   Dev& d = h->d;
   const int n2 = no2(h), k = d.k;
   const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * d.r * n2;
-  auto put = [&](const std::vector<double2>& src, double2* dst) -> cudaError_t {
+  const size_t es = esz(h);
+  auto put = [&](const std::vector<char>& src, void* dst) -> cudaError_t {
     for (int n = 0; n < d.n_inst; ++n)
       for (int t = 0; t <= k; ++t) {
-        cudaError_t e = cudaMemcpyAsync(dst + row_off(h, n, t), src.data() + sq * n + (size_t)t * (t + 1) / 2 * n2,
-                                        (size_t)(t + 1) * n2 * sizeof(double2), cudaMemcpyHostToDevice, h->s);
+        cudaError_t e = cudaMemcpyAsync(elp(h, dst, row_off(h, n, t)), src.data() + (sq * n + (size_t)t * (t + 1) / 2 * n2) * es,
+                                        (size_t)(t + 1) * n2 * es, cudaMemcpyHostToDevice, h->s);
         if (e != cudaSuccess) return e;
       }
     return cudaSuccess;
   };
-  auto put_tv = [&](const std::vector<double2>& src, double2* dst) -> cudaError_t {
+  auto put_tv = [&](const std::vector<char>& src, void* dst) -> cudaError_t {
+    const size_t et = sizeof(double2);
     for (int n = 0; n < d.n_inst; ++n) {
-      cudaError_t e = cudaMemcpyAsync(dst + (size_t)n * d.nt * d.r * n2, src.data() + tvn * n, tvn * sizeof(double2),
-                                      cudaMemcpyHostToDevice, h->s);
+      cudaError_t e = cudaMemcpyAsync(static_cast<char*>(dst) + (size_t)n * d.nt * d.r * n2 * et, src.data() + tvn * n * et,
+                                      tvn * et, cudaMemcpyHostToDevice, h->s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
+  for (auto& a : h->state_arrays) HK_CUDA(h, cudaMemsetAsync(a.first, 0, a.second, h->s));
   HK_CUDA(h, put(h->snap_gr, d.GR));
   HK_CUDA(h, put(h->snap_gl, d.GL));
   HK_CUDA(h, put(h->snap_sr, d.SR));
   HK_CUDA(h, put(h->snap_sl, d.SL));
   HK_CUDA(h, put_tv(h->snap_tv, d.GTV));
   HK_CUDA(h, put_tv(h->snap_stv, d.STV));
+  HK_CUDA(h, hk::launch_diag_seed(d, h->s));
   d.nfrozR = d.nfrozL = 0;
   if (h->hodlr) {
     d.cdir = 0;
     for (int X = 0; X < 4; ++X)
       HK_CUDA(h, cudaMemsetAsync(d.hod[X].rank, 0, (size_t)d.n_inst * d.nblk * n2 * sizeof(int), h->s));
+    HK_CUDA(h, cudaMemsetAsync(h->status_dev, 0, 2 * sizeof(int), h->s));
   }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->cur = k;

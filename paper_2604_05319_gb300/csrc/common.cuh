@@ -38,6 +38,10 @@ template <typename R> HD cx<R> cfma(const cx<R>& a, const cx<R>& b, const cx<R>&
 
 HD zd ld(const double2* p) { double2 v = *p; return zd(v.x, v.y); }
 HD void st(double2* p, const zd& z) { *p = make_double2(z.re, z.im); }
+// single-precision storage of the mixed-precision form: loads widen to
+// double, stores round to nearest float
+HD zd ld(const float2* p) { float2 v = *p; return zd((double)v.x, (double)v.y); }
+HD void st(float2* p, const zd& z) { *p = make_float2((float)z.re, (float)z.im); }
 
 HD zd cdiv(const zd& a, const zd& b) {
   double d = b.re * b.re + b.im * b.im;
@@ -55,7 +59,7 @@ struct M {
   HD const zd& operator()(int i, int j) const { return a[i][j]; }
 };
 
-template <int N> HD M<N> load(const double2* p) {
+template <int N, typename P> HD M<N> load(const P* p) {
   M<N> m;
 #pragma unroll
   for (int i = 0; i < N; ++i)
@@ -63,7 +67,7 @@ template <int N> HD M<N> load(const double2* p) {
     for (int j = 0; j < N; ++j) m.a[i][j] = ld(p + i * N + j);
   return m;
 }
-template <int N> HD void store(double2* p, const M<N>& m) {
+template <int N, typename P> HD void store(P* p, const M<N>& m) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll

@@ -12,14 +12,18 @@ __device__ __forceinline__ long long tri(int T) { return (long long)T * (T + 1) 
 
 // Row T of a two-time component: the dense lower triangle, or (compressed
 // storage) the ring of uncompressed rows, slot T mod ring.
-template <int NO>
-__device__ __forceinline__ double2* el(double2* base, const Dev& d, int n, int T, int t) {
-  if (d.ring) return base + (((long long)n * d.ring + (T % d.ring)) * d.nt + t) * (NO * NO);
-  return base + ((long long)n * d.ntri + tri(T) + t) * (NO * NO);
+// S is the storage element type (double2 or float2).
+template <int NO, typename S>
+__device__ __forceinline__ S* el(void* base, const Dev& d, int n, int T, int t) {
+  S* b = static_cast<S*>(base);
+  if (d.ring) return b + (((long long)n * d.ring + (T % d.ring)) * d.nt + t) * (NO * NO);
+  return b + ((long long)n * d.ntri + tri(T) + t) * (NO * NO);
 }
+// Mixed components G^tv, Sigma^tv: complex128 in both precision forms (their
+// DLR convolution is ill-conditioned; they are r/T times smaller than a row set).
 template <int NO>
-__device__ __forceinline__ double2* tv(double2* base, const Dev& d, int n, int T, int i) {
-  return base + (((long long)n * d.nt + T) * d.r + i) * (NO * NO);
+__device__ __forceinline__ double2* tv(void* base, const Dev& d, int n, int T, int i) {
+  return static_cast<double2*>(base) + (((long long)n * d.nt + T) * d.r + i) * (NO * NO);
 }
 template <int NO>
 __device__ __forceinline__ double2* epsp(const Dev& d, int n, int t) {  // eps(t), t >= -1
@@ -59,16 +63,16 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // Sigma^R(a, b) continued above the diagonal: -[Sigma^R(b, a)]^dagger for a < b.
-template <int NO>
+template <int NO, typename S>
 __device__ __forceinline__ zd srx(const Dev& d, int n, int a, int b, int x, int y) {
-  if (a >= b) return ld(el<NO>(d.SR, d, n, a, b) + x * NO + y);
-  return -ld(el<NO>(d.SR, d, n, b, a) + y * NO + x).conj();
+  if (a >= b) return ld(el<NO, S>(d.SR, d, n, a, b) + x * NO + y);
+  return -ld(el<NO, S>(d.SR, d, n, b, a) + y * NO + x).conj();
 }
 // Sigma^<(t, l) anywhere (Eq. GLantiHerm)
-template <int NO>
+template <int NO, typename S>
 __device__ __forceinline__ zd sless(const Dev& d, int n, int t, int l, int x, int y) {
-  if (t <= l) return ld(el<NO>(d.SL, d, n, l, t) + x * NO + y);
-  return -ld(el<NO>(d.SL, d, n, t, l) + y * NO + x).conj();
+  if (t <= l) return ld(el<NO, S>(d.SL, d, n, l, t) + x * NO + y);
+  return -ld(el<NO, S>(d.SL, d, n, t, l) + y * NO + x).conj();
 }
 
 // ---------------------------------------------------------------------------

@@ -55,7 +55,7 @@ __device__ void bath_sigma(const double* mp, zd g0, double eb_dt_sign, int which
   (void)g0; (void)eb_dt_sign;
 }
 
-template <int NO>
+template <int NO, typename S>
 __global__ void k_sigma(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y;
@@ -64,33 +64,30 @@ __global__ void k_sigma(Dev d, int T) {
   const int total = 2 * (T + 1) + d.r;
   if (idx >= total) return;
   const double* mp = d.mpar + (long long)n * MP;
-  double2 *src, *dst;
-  int which;
-  double tph = 0.0, tauv = 0.0;
+  // src / dst are S* for the two-time rows, double2* for the mixed row
+  auto apply = [&](const auto* src, auto* dst, int which, double tph, double tauv) {
+    if (d.model == 1) {  // Bethe: Sigma = v^2 G
+      const double v2 = mp[0] * mp[0];
+#pragma unroll
+      for (int e = 0; e < NO2; ++e) st(dst + e, ld(src + e) * v2);
+    } else if (d.model == 2) {
+      zd out[NO2];
+      bath_sigma<NO>(mp, zd(), 0.0, which, d, tph, tauv, out);
+#pragma unroll
+      for (int e = 0; e < NO2; ++e) st(dst + e, out[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < NO2; ++e) st(dst + e, zd());
+    }
+  };
   if (idx <= T) {
-    src = el<NO>(d.GR, d, n, T, idx); dst = el<NO>(d.SR, d, n, T, idx);
-    which = 0; tph = (T - idx) * d.h;
+    apply(el<NO, S>(d.GR, d, n, T, idx), el<NO, S>(d.SR, d, n, T, idx), 0, (T - idx) * d.h, 0.0);
   } else if (idx <= 2 * T + 1) {
     const int t = idx - (T + 1);
-    src = el<NO>(d.GL, d, n, T, t); dst = el<NO>(d.SL, d, n, T, t);
-    which = 1; tph = (t - T) * d.h;
+    apply(el<NO, S>(d.GL, d, n, T, t), el<NO, S>(d.SL, d, n, T, t), 1, (t - T) * d.h, 0.0);
   } else {
     const int i = idx - 2 * (T + 1);
-    src = tv<NO>(d.GTV, d, n, T, i); dst = tv<NO>(d.STV, d, n, T, i);
-    which = 2; tph = T * d.h; tauv = d.tau[i];
-  }
-  if (d.model == 1) {  // Bethe: Sigma = v^2 G
-    const double v2 = mp[0] * mp[0];
-#pragma unroll
-    for (int e = 0; e < NO2; ++e) st(dst + e, ld(src + e) * v2);
-  } else if (d.model == 2) {
-    zd out[NO2];
-    bath_sigma<NO>(mp, zd(), 0.0, which, d, tph, tauv, out);
-#pragma unroll
-    for (int e = 0; e < NO2; ++e) st(dst + e, out[e]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < NO2; ++e) st(dst + e, zd());
+    apply(tv<NO>(d.GTV, d, n, T, i), tv<NO>(d.STV, d, n, T, i), 2, T * d.h, d.tau[i]);
   }
 }
 
@@ -98,7 +95,7 @@ __global__ void k_sigma(Dev d, int T) {
 // Extrapolated initial guess for step T (Sec. 3.4): degree-k polynomial along
 // the diagonal through the previous k+1 points, e_l = (-1)^l C(k+1, l+1).
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void k_extrap(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y;
@@ -115,40 +112,42 @@ __global__ void k_extrap(Dev d, int T) {
   }
   zd acc[NO2];
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
-  double2* dst;
+  S* dst = nullptr;
   if (idx <= T) {
     const int tp = idx;
-    dst = el<NO>(d.GR, d, n, T, tp);
+    dst = el<NO, S>(d.GR, d, n, T, tp);
     if (tp == T) {
       for (int x = 0; x < NO; ++x) acc[x * NO + x] = zd(0, -1);
     } else if (tp >= k + 1 || tp == 0) {
       for (int l = 0; l <= k; ++l) {
-        const double2* s = (tp == 0) ? el<NO>(d.GR, d, n, T - 1 - l, 0) : el<NO>(d.GR, d, n, T - 1 - l, tp - 1 - l);
+        const S* s = (tp == 0) ? el<NO, S>(d.GR, d, n, T - 1 - l, 0) : el<NO, S>(d.GR, d, n, T - 1 - l, tp - 1 - l);
         for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
       }
     } else {
-      const double2* s = el<NO>(d.GR, d, n, T - 1, tp - 1);
+      const S* s = el<NO, S>(d.GR, d, n, T - 1, tp - 1);
       for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
     }
   } else if (idx <= 2 * T + 1) {
     const int t = idx - (T + 1);
-    dst = el<NO>(d.GL, d, n, T, t);
+    dst = el<NO, S>(d.GL, d, n, T, t);
     if (t >= k + 1 || t == 0) {
       for (int l = 0; l <= k; ++l) {
-        const double2* s = (t == 0) ? el<NO>(d.GL, d, n, T - 1 - l, 0) : el<NO>(d.GL, d, n, T - 1 - l, t - 1 - l);
+        const S* s = (t == 0) ? el<NO, S>(d.GL, d, n, T - 1 - l, 0) : el<NO, S>(d.GL, d, n, T - 1 - l, t - 1 - l);
         for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
       }
     } else {
-      const double2* s = el<NO>(d.GL, d, n, T - 1, t - 1);
+      const S* s = el<NO, S>(d.GL, d, n, T - 1, t - 1);
       for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
     }
   } else {
     const int i = idx - 2 * (T + 1);
-    dst = tv<NO>(d.GTV, d, n, T, i);
     for (int l = 0; l <= k; ++l) {
       const double2* s = tv<NO>(d.GTV, d, n, T - 1 - l, i);
       for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
     }
+    double2* dtv = tv<NO>(d.GTV, d, n, T, i);
+    for (int q = 0; q < NO2; ++q) st(dtv + q, acc[q]);
+    return;
   }
   for (int q = 0; q < NO2; ++q) st(dst + q, acc[q]);
 }
@@ -159,7 +158,7 @@ __global__ void k_extrap(Dev d, int T) {
 constexpr int CH = 32;     // chunk of the sequential sweeps
 constexpr int NWARP = 8;   // warps per sweep CTA
 
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y, irow = blockIdx.x;
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
   __shared__ zd ych[CH][NO];
   __shared__ double serr;
   if (tid == 0) serr = 0.0;
-  double2* rowp = el<NO>(d.GR, d, n, T, 0);  // G^R(T, t') at rowp + t' NO2
+  S* rowp = el<NO, S>(d.GR, d, n, T, 0);  // G^R(T, t') at rowp + t' NO2
   auto yptr = [&](int s) { return rowp + (long long)(T - s) * NO2 + irow * NO; };
   double myerr = 0.0;
   // ---- start block s = 1..k ----
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
     for (int e = lane; e < ns * ns; e += 32) {
       const int row = e / ns, col = e % ns;       // row (s, j), col (l, m)
       const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
-      zd v = srx<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
+      zd v = srx<NO, S>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
       if (m == j) v += zd(0, W.D[s][l] / h);
       if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
       sA[row * ns + col] = v;
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
     for (int row = lane; row < ns; row += 32) {
       const int s = row / NO + 1, j = row % NO;
       // b_s[j] = -sum_m y0[m] C[0,s][m][j], y0 = -i e_irow  ->  i C[0,s][irow][j]
-      zd c = srx<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
+      zd c = srx<NO, S>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
       if (irow == j) c += zd(0, W.D[s][0] / h);
       sB[row] = zd(0, 1) * c;
     }
@@ -199,13 +198,13 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
     warp_lu_solve(ns, sA, sB, 1, nullptr);
     for (int row = lane; row < ns; row += 32) {
       const int s = row / NO + 1, j = row % NO;
-      double2* p = yptr(s) + j;
+      S* p = yptr(s) + j;
       zd old = ld(p);
       st(p, sB[row]);
       myerr = fmax(myerr, sqrt((sB[row] - old).abs2()));
     }
     if (lane == 0) {
-      double2* p = yptr(0);
+      S* p = yptr(0);
       for (int j = 0; j < NO; ++j) {
         zd v = (j == irow) ? zd(0, -1) : zd();
         myerr = fmax(myerr, sqrt((ld(p + j) - v).abs2()));
@@ -225,8 +224,8 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
       if (lane < cn) {
         for (int l = warp; l < s0; l += NWARP) {
           const double wl = rule_w(W, s, l);
-          const double2* yl = yptr(l);
-          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+          const S* yl = yptr(l);
+          const S* sr = el<NO, S>(d.SR, d, n, T - l, T - s);
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
             const zd ym = ld(yl + m) * wl;
@@ -255,7 +254,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
         if (lane < sl) {  // near field, l in [s0, s)
           const int l = s0 + lane;
           const double wl = h * rule_w(W, s, l);
-          const double2* sr = el<NO>(d.SR, d, n, T - l, T - s);
+          const S* sr = el<NO, S>(d.SR, d, n, T - l, T - s);
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
             const zd ym = ych[lane][m] * wl;
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
 #pragma unroll
           for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
           const double ws = h * rule_w(W, s, s);
-          const double2* sd = el<NO>(d.SR, d, n, T - s, T - s);
+          const S* sd = el<NO, S>(d.SR, d, n, T - s, T - s);
           const double2* ep = epsp<NO>(d, n, T - s);
           M<NO> Mm;
 #pragma unroll
@@ -287,7 +286,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
             for (int y2 = 0; y2 < NO; ++y2)
               Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
           solve_row<NO>(Mm, rhs, y);
-          double2* p = yptr(s);
+          S* p = yptr(s);
 #pragma unroll
           for (int j = 0; j < NO; ++j) {
             myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
@@ -309,7 +308,7 @@ __global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
 // ---------------------------------------------------------------------------
 // Mixed component at step T, Eq. KBET (one warp per (instance, node)).
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void k_mixed(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -324,21 +323,21 @@ __global__ void k_mixed(Dev d, int T) {
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
   for (int l = lane; l < T; l += 32) {  // h sum_l w_l Sigma^R(T,l) G^tv(l, tau_i)
     const double wl = h * rule_w(W, T, l);
-    M<NO> S = load<NO>(el<NO>(d.SR, d, n, T, l));
+    M<NO> Sm = load<NO>(el<NO, S>(d.SR, d, n, T, l));
     M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, l, i));
 #pragma unroll
     for (int x = 0; x < NO; ++x)
 #pragma unroll
       for (int z = 0; z < NO; ++z) {
-        zd sx = S.a[x][z] * wl;
+        zd sx = Sm.a[x][z] * wl;
 #pragma unroll
         for (int y = 0; y < NO; ++y) acc[x * NO + y] = cfma(sx, G.a[z][y], acc[x * NO + y]);
       }
   }
   for (int a = lane; a < d.r; a += 32) {  // sum_a Sigma^tv(T, tau_a) W[a][i]
-    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, T, a));
+    M<NO> Sm = load<NO>(tv<NO>(d.STV, d, n, T, a));
     M<NO> C = load<NO>(d.wconv + (((long long)n * d.r + a) * d.r + i) * NO2);
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, C, zd(1.0));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, C, zd(1.0));
   }
   if (lane >= 1 && lane <= k) {
     M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, T - lane, i));
@@ -350,7 +349,7 @@ __global__ void k_mixed(Dev d, int T) {
   if (lane == 0) {
     const double wt = h * rule_w(W, T, T);
     M<NO> Mm, R;
-    const double2* sd = el<NO>(d.SR, d, n, T, T);
+    const S* sd = el<NO, S>(d.SR, d, n, T, T);
     const double2* ep = epsp<NO>(d, n, T);
 #pragma unroll
     for (int x = 0; x < NO; ++x)
@@ -369,7 +368,7 @@ __global__ void k_mixed(Dev d, int T) {
 
 // v_a = sum_b Q_ab G^vt(tau_b, T), G^vt(tau_b, T) = -xi [G^tv(T, beta - tau_b)]^dagger,
 // x_0 = -[G^tv(T, 0+)]^dagger.  One CTA per instance, thread per node.
-template <int NO>
+template <int NO, typename S>
 __global__ void k_vt(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.x;
@@ -414,7 +413,7 @@ __global__ void k_vt(Dev d, int T) {
 }
 
 // Lesser source q(t) = h sum_l w^(T)_l Sigma^<(t,l) G^A(l,T) - i sum_a Sigma^tv(t,tau_a) v_a
-template <int NO>
+template <int NO, typename S>
 __global__ void k_src(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -427,18 +426,18 @@ __global__ void k_src(Dev d, int T) {
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
   for (int l = lane; l <= T; l += 32) {
     const double wl = h * rule_w(d.w, T, l);
-    M<NO> S;
+    M<NO> Sm;
 #pragma unroll
     for (int x = 0; x < NO; ++x)
 #pragma unroll
-      for (int y = 0; y < NO; ++y) S.a[x][y] = sless<NO>(d, n, t, l, x, y);
-    M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+      for (int y = 0; y < NO; ++y) Sm.a[x][y] = sless<NO, S>(d, n, t, l, x, y);
+    M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(wl));
   }
   for (int a = lane; a < d.r; a += 32) {
-    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, t, a));
+    M<NO> Sm = load<NO>(tv<NO>(d.STV, d, n, t, a));
     M<NO> V = load<NO>(d.vvec + ((long long)n * d.r + a) * NO2);
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, V, zd(0, -1));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, V, zd(0, -1));
   }
   warp_sum<NO2>(acc);
   if (lane == 0) {
@@ -451,7 +450,7 @@ __global__ void k_src(Dev d, int T) {
 // ---------------------------------------------------------------------------
 // Lesser column, Eq. KBEL: x_t = G^<(t, T), left-multiplying VIDE in t.
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y, jc = blockIdx.x;
@@ -466,7 +465,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
   __shared__ zd xch[CH][NO];
   __shared__ double serr;
   if (tid == 0) serr = 0.0;
-  double2* colp = el<NO>(d.GL, d, n, T, 0);  // G^<(t, T) at colp + t NO2
+  S* colp = el<NO, S>(d.GL, d, n, T, 0);  // G^<(t, T) at colp + t NO2
   auto xptr = [&](int t) { return colp + (long long)t * NO2; };   // element [m][jc] at + m*NO + jc
   const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
   double myerr = 0.0;
@@ -476,7 +475,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
     if (lane < NO) {
       const int m = lane;
       zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
-      double2* p = xptr(0) + m * NO + jc;
+      S* p = xptr(0) + m * NO + jc;
       myerr = fmax(myerr, sqrt((v - ld(p)).abs2()));
       st(p, v);
     }
@@ -485,7 +484,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
     for (int e = lane; e < ns * ns; e += 32) {
       const int row = e / ns, col = e % ns;       // row (t, m), col (l, y)
       const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
-      zd v = srx<NO>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
+      zd v = srx<NO, S>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
       if (m == y) v += zd(0, W.D[t][l] / h);
       if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
       sA[row * ns + col] = v;
@@ -494,7 +493,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
       const int t = row / NO + 1, m = row % NO;
       zd b = ld(qs + t * NO2 + m * NO + jc);
       for (int y = 0; y < NO; ++y) {
-        zd c = srx<NO>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
+        zd c = srx<NO, S>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
         if (m == y) c += zd(0, W.D[t][0] / h);
         if (t == 0) c -= ld(epsp<NO>(d, n, t) + m * NO + y);
         b -= c * ld(xptr(0) + y * NO + jc);
@@ -506,7 +505,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
     for (int row = lane; row < ns; row += 32) {
       const int t = row / NO + 1, m = row % NO;
       if (t > last) continue;
-      double2* p = xptr(t) + m * NO + jc;
+      S* p = xptr(t) + m * NO + jc;
       myerr = fmax(myerr, sqrt((sB[row] - ld(p)).abs2()));
       st(p, sB[row]);
     }
@@ -520,11 +519,11 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
       zd acc[NO];
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[m] = zd();
-      const double2* srow = el<NO>(d.SR, d, n, t, 0);
+      const S* srow = el<NO, S>(d.SR, d, n, t, 0);
       for (int l = lane; l < t0; l += 32) {
         const double wl = rule_w(W, t, l);
-        const double2* sr = srow + (long long)l * NO2;
-        const double2* xl = xptr(l);
+        const S* sr = srow + (long long)l * NO2;
+        const S* xl = xptr(l);
 #pragma unroll
         for (int y = 0; y < NO; ++y) {
           const zd xy = ld(xl + y * NO + jc) * wl;
@@ -547,7 +546,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
         if (lane < tl) {
           const int l = t0 + lane;
           const double wl = h * rule_w(W, t, l);
-          const double2* sr = el<NO>(d.SR, d, n, t, l);
+          const S* sr = el<NO, S>(d.SR, d, n, t, l);
 #pragma unroll
           for (int y = 0; y < NO; ++y) {
             const zd xy = xch[lane][y] * wl;
@@ -570,7 +569,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
 #pragma unroll
           for (int m = 0; m < NO; ++m) rhs[m] = part[m] + farsh[tl][m] + ld(qs + (long long)t * NO2 + m * NO + jc);
           const double wt = h * rule_w(W, t, t);
-          const double2* sd = el<NO>(d.SR, d, n, t, t);
+          const S* sd = el<NO, S>(d.SR, d, n, t, t);
           const double2* ep = epsp<NO>(d, n, t);
           M<NO> Mm;
 #pragma unroll
@@ -581,7 +580,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
           solve_col<NO>(Mm, rhs, x);
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
-            double2* p = xptr(t) + m * NO + jc;
+            S* p = xptr(t) + m * NO + jc;
             myerr = fmax(myerr, sqrt((x[m] - ld(p)).abs2()));
             st(p, x[m]);
             xch[tl][m] = x[m];
@@ -603,7 +602,7 @@ __global__ void __launch_bounds__(256) k_les(Dev d, int T) {
 //   -(1/h) sum_{j>=1} a_j rho(T-j) + xi (r0 + r0^dag),
 // A = eps(T) + h w_T Sigma^R(T,T), r0 = h sum_{l<T} w_l Sigma^R(T,l) x_l + q(T).
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void k_rho(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.x;
@@ -615,9 +614,9 @@ __global__ void k_rho(Dev d, int T) {
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
   for (int l = threadIdx.x; l < T; l += blockDim.x) {
     const double wl = h * rule_w(d.w, T, l);
-    M<NO> S = load<NO>(el<NO>(d.SR, d, n, T, l));
-    M<NO> X = load<NO>(el<NO>(d.GL, d, n, T, l));
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, X, zd(wl));
+    M<NO> Sm = load<NO>(el<NO, S>(d.SR, d, n, T, l));
+    M<NO> X = load<NO>(el<NO, S>(d.GL, d, n, T, l));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, X, zd(wl));
   }
   warp_sum<NO2>(acc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -633,15 +632,18 @@ __global__ void k_rho(Dev d, int T) {
   const double xi = d.xi;
   const double wt = h * rule_w(d.w, T, T);
   M<NO> A, rhs;
-  const double2* sd = el<NO>(d.SR, d, n, T, T);
+  const S* sd = el<NO, S>(d.SR, d, n, T, T);
   const double2* ep = epsp<NO>(d, n, T);
   for (int x = 0; x < NO; ++x)
     for (int y = 0; y < NO; ++y) {
       A.a[x][y] = ld(ep + x * NO + y) + ld(sd + x * NO + y) * wt;
       rhs.a[x][y] = (r0[x * NO + y] + r0[y * NO + x].conj()) * xi;
     }
+  constexpr bool f64 = sizeof(S) == sizeof(double2);  // else: FP64 diagonal history in diag64
   for (int j = 1; j <= d.k; ++j) {
-    M<NO> rho = scale<NO>(load<NO>(el<NO>(d.GL, d, n, T - j, T - j)), zd(0, xi));
+    const M<NO> gd = f64 ? load<NO>(el<NO, S>(d.GL, d, n, T - j, T - j))
+                         : load<NO>(d.diag64 + ((long long)n * d.nt + T - j) * NO2);
+    M<NO> rho = scale<NO>(gd, zd(0, xi));
     rhs = rhs - scale<NO>(rho, zd(d.w.a[j] / h));
   }
   // L vec(rho) = vec(rhs), vec row-major, L[(x,y),(u,v)]
@@ -677,20 +679,31 @@ __global__ void k_rho(Dev d, int T) {
     for (int j = c + 1; j < NO2; ++j) s -= L[c * NO2 + j] * b[j];
     b[c] = cdiv(s, L[c * NO2 + c]);
   }
-  double2* p = el<NO>(d.GL, d, n, T, T);
+  S* p = el<NO, S>(d.GL, d, n, T, T);
   double e = 0.0;
   for (int q = 0; q < NO2; ++q) {
     zd x = b[q] * zd(0, -xi);  // G^<(T,T) = -i xi rho
     e = fmax(e, sqrt((x - ld(p + q)).abs2()));
     st(p + q, x);
+    if (!f64) st(d.diag64 + ((long long)n * d.nt + T) * NO2 + q, x);
   }
   atomic_max_nonneg(d.err + n, e);
+}
+
+template <int NO, typename S>
+__global__ void k_diag_seed(Dev d) {
+  constexpr int NO2 = NO * NO;
+  const int n = blockIdx.x;
+  for (int e = threadIdx.x; e < (d.k + 1) * NO2; e += blockDim.x) {
+    const int t = e / NO2, q = e % NO2;
+    st(d.diag64 + ((long long)n * d.nt + t) * NO2 + q, ld(el<NO, S>(d.GL, d, n, t, t) + q));
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Bootstrap square t <= k (Sec. 3.3, polynomial weights of Appendix A).
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_boot_mixed(Dev d) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.x;
@@ -719,7 +732,7 @@ __global__ void __launch_bounds__(256) k_boot_mixed(Dev d) {
     for (int e = lane; e < ns * ns; e += 32) {
       const int row = e / ns, col = e % ns;
       const int m = row / NO + 1, x = row % NO, l = col / NO + 1, y = col % NO;
-      zd v = srx<NO>(d, n, m, l, x, y) * (-h * W.I0[m][l]);
+      zd v = srx<NO, S>(d, n, m, l, x, y) * (-h * W.I0[m][l]);
       if (x == y) v += zd(0, W.D[m][l] / h);
       if (l == m) v -= ld(epsp<NO>(d, n, m) + x * NO + y);
       sA[row * ns + col] = v;
@@ -736,12 +749,12 @@ __global__ void __launch_bounds__(256) k_boot_mixed(Dev d) {
       for (int x = 0; x < NO; ++x) {
         zd s = zd();
         for (int a = 0; a < r; ++a) {  // C(m, tau_i) = sum_a Sigma^tv(m, a) W[a][i]
-          const double2* S = tv<NO>(d.STV, d, n, m, a);
+          const double2* Sa = tv<NO>(d.STV, d, n, m, a);
           const double2* C = d.wconv + (((long long)n * r + a) * r + i) * NO2;
-          for (int z = 0; z < NO; ++z) s += ld(S + x * NO + z) * ld(C + z * NO + y);
+          for (int z = 0; z < NO; ++z) s += ld(Sa + x * NO + z) * ld(C + z * NO + y);
         }
         for (int z = 0; z < NO; ++z) {
-          zd c0 = srx<NO>(d, n, m, 0, x, z) * (-h * W.I0[m][0]);
+          zd c0 = srx<NO, S>(d, n, m, 0, x, z) * (-h * W.I0[m][0]);
           if (x == z) c0 += zd(0, W.D[m][0] / h);
           s -= c0 * ld(tv<NO>(d.GTV, d, n, 0, i) + z * NO + y);
         }
@@ -759,7 +772,7 @@ __global__ void __launch_bounds__(256) k_boot_mixed(Dev d) {
   }
 }
 
-template <int NO>
+template <int NO, typename S>
 __global__ void k_boot_ret(Dev d) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.x;
@@ -770,7 +783,7 @@ __global__ void k_boot_ret(Dev d) {
   __shared__ zd sA[20 * 20];
   __shared__ zd sB[20 * 4];
   for (int m = 0; m <= k; ++m)
-    if (lane < NO2) st(el<NO>(d.GR, d, n, m, m) + lane, (lane / NO == lane % NO) ? zd(0, -1) : zd());
+    if (lane < NO2) st(el<NO, S>(d.GR, d, n, m, m) + lane, (lane / NO == lane % NO) ? zd(0, -1) : zd());
   __syncwarp();
   double e = 0.0;
   for (int c = 0; c < k; ++c) {  // column n' = c
@@ -778,7 +791,7 @@ __global__ void k_boot_ret(Dev d) {
     for (int idx = lane; idx < nu * nu; idx += 32) {
       const int row = idx / nu, col = idx % nu;
       const int m = row / NO + c + 1, x = row % NO, l = col / NO + c + 1, y = col % NO;
-      zd v = srx<NO>(d, n, m, l, x, y) * (-h * (W.I0[m][l] - W.I0[c][l]));
+      zd v = srx<NO, S>(d, n, m, l, x, y) * (-h * (W.I0[m][l] - W.I0[c][l]));
       if (x == y) v += zd(0, W.D[m][l] / h);
       if (l == m) v -= ld(epsp<NO>(d, n, m) + x * NO + y);
       sA[row * nu + col] = v;
@@ -789,11 +802,11 @@ __global__ void k_boot_ret(Dev d) {
       zd s = zd();
       for (int l = 0; l <= c; ++l)
         for (int z = 0; z < NO; ++z) {
-          zd blk = srx<NO>(d, n, m, l, x, z) * (-h * (W.I0[m][l] - W.I0[c][l]));
+          zd blk = srx<NO, S>(d, n, m, l, x, z) * (-h * (W.I0[m][l] - W.I0[c][l]));
           if (x == z) blk += zd(0, W.D[m][l] / h);
           // gx(l) = G^R(l, c) for l >= c, -[G^R(c, l)]^dagger for l < c
-          zd g = (l >= c) ? ld(el<NO>(d.GR, d, n, l, c) + z * NO + y)
-                          : -ld(el<NO>(d.GR, d, n, c, l) + y * NO + z).conj();
+          zd g = (l >= c) ? ld(el<NO, S>(d.GR, d, n, l, c) + z * NO + y)
+                          : -ld(el<NO, S>(d.GR, d, n, c, l) + y * NO + z).conj();
           s -= blk * g;
         }
       sB[row * NO + y] = s;
@@ -803,7 +816,7 @@ __global__ void k_boot_ret(Dev d) {
     for (int idx = lane; idx < nu * NO; idx += 32) {
       const int row = idx / NO, y = idx % NO;
       const int m = row / NO + c + 1, x = row % NO;
-      double2* p = el<NO>(d.GR, d, n, m, c) + x * NO + y;
+      S* p = el<NO, S>(d.GR, d, n, m, c) + x * NO + y;
       e = fmax(e, sqrt((sB[row * NO + y] - ld(p)).abs2()));
       st(p, sB[row * NO + y]);
     }
@@ -813,7 +826,7 @@ __global__ void k_boot_ret(Dev d) {
   if (lane == 0) atomic_max_nonneg(d.err + n, e);
 }
 
-template <int NO>
+template <int NO, typename S>
 __global__ void k_boot_les(Dev d) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.x;
@@ -833,7 +846,7 @@ __global__ void k_boot_les(Dev d) {
       zd s = zd();
       for (int c = 0; c < r; ++c) s += ld(tv<NO>(d.GTV, d, n, m, c) + y * NO + x) * d.e0[c];
       x0s[lane] = -s.conj();
-      double2* p = el<NO>(d.GL, d, n, m, 0) + lane;
+      S* p = el<NO, S>(d.GL, d, n, m, 0) + lane;
       e = fmax(e, sqrt((x0s[lane] - ld(p)).abs2()));
       st(p, x0s[lane]);
     }
@@ -855,7 +868,7 @@ __global__ void k_boot_les(Dev d) {
     for (int idx = lane; idx < nu * nu; idx += 32) {
       const int row = idx / nu, col = idx % nu;
       const int t = row / NO + 1, x = row % NO, l = col / NO + 1, y = col % NO;
-      zd v = srx<NO>(d, n, t, l, x, y) * (-h * W.I0[t][l]);
+      zd v = srx<NO, S>(d, n, t, l, x, y) * (-h * W.I0[t][l]);
       if (x == y) v += zd(0, W.D[t][l] / h);
       if (l == t) v -= ld(epsp<NO>(d, n, t) + x * NO + y);
       sA[row * nu + col] = v;
@@ -868,16 +881,16 @@ __global__ void k_boot_les(Dev d) {
       for (int l = 0; l <= k; ++l) {
         const double wl = h * W.I0[m][l];
         for (int z = 0; z < NO; ++z) {
-          zd ga = (l <= m) ? ld(el<NO>(d.GR, d, n, m, l) + y * NO + z).conj()
-                           : -ld(el<NO>(d.GR, d, n, l, m) + z * NO + y);
-          s += sless<NO>(d, n, t, l, x, z) * ga * wl;
+          zd ga = (l <= m) ? ld(el<NO, S>(d.GR, d, n, m, l) + y * NO + z).conj()
+                           : -ld(el<NO, S>(d.GR, d, n, l, m) + z * NO + y);
+          s += sless<NO, S>(d, n, t, l, x, z) * ga * wl;
         }
       }
       for (int a = 0; a < r; ++a)
         for (int z = 0; z < NO; ++z)
           s += ld(tv<NO>(d.STV, d, n, t, a) + x * NO + z) * ld(vv + a * NO2 + z * NO + y) * zd(0, -1);
       for (int z = 0; z < NO; ++z) {  // known point l = 0
-        zd blk = srx<NO>(d, n, t, 0, x, z) * (-h * W.I0[t][0]);
+        zd blk = srx<NO, S>(d, n, t, 0, x, z) * (-h * W.I0[t][0]);
         if (x == z) blk += zd(0, W.D[t][0] / h);
         s -= blk * x0s[z * NO + y];
       }
@@ -889,7 +902,7 @@ __global__ void k_boot_les(Dev d) {
       const int row = idx / NO, y = idx % NO;
       const int t = row / NO + 1, x = row % NO;
       if (t > m) continue;
-      double2* p = el<NO>(d.GL, d, n, m, t) + x * NO + y;
+      S* p = el<NO, S>(d.GL, d, n, m, t) + x * NO + y;
       e = fmax(e, sqrt((sB[row * NO + y] - ld(p)).abs2()));
       st(p, sB[row * NO + y]);
     }
@@ -912,51 +925,60 @@ __global__ void k_set_active(Dev d, double tol, int iter, int min_iter, int* any
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-#define HK_DISPATCH(NOV, CALL)            \
-  switch (NOV) {                          \
-    case 1: { constexpr int NO = 1; CALL; break; } \
-    case 2: { constexpr int NO = 2; CALL; break; } \
-    case 3: { constexpr int NO = 3; CALL; break; } \
-    case 4: { constexpr int NO = 4; CALL; break; } \
-    default: return cudaErrorInvalidValue; \
+#define HK_DISPATCH(NOV, CALL)                                                  \
+  switch ((NOV) * 2 + d.prec) {                                                 \
+    case 2: { constexpr int NO = 1; using S = double2; CALL; break; }           \
+    case 3: { constexpr int NO = 1; using S = float2; CALL; break; }            \
+    case 4: { constexpr int NO = 2; using S = double2; CALL; break; }           \
+    case 5: { constexpr int NO = 2; using S = float2; CALL; break; }            \
+    case 6: { constexpr int NO = 3; using S = double2; CALL; break; }           \
+    case 7: { constexpr int NO = 3; using S = float2; CALL; break; }            \
+    case 8: { constexpr int NO = 4; using S = double2; CALL; break; }           \
+    case 9: { constexpr int NO = 4; using S = float2; CALL; break; }            \
+    default: return cudaErrorInvalidValue;                                      \
   }
 
 cudaError_t launch_extrapolate(const Dev& d, int T, cudaStream_t s) {
   dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
-  HK_DISPATCH(d.no, (k_extrap<NO><<<g, 128, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_extrap<NO, S><<<g, 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_sigma(const Dev& d, int T, cudaStream_t s) {
   dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
-  HK_DISPATCH(d.no, (k_sigma<NO><<<g, 128, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_sigma<NO, S><<<g, 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_ret(const Dev& d, int T, cudaStream_t s) {
   dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_ret<NO><<<g, 256, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_ret<NO, S><<<g, 256, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_mixed(const Dev& d, int T, cudaStream_t s) {
   const long long warps = (long long)d.n_inst * d.r;
-  HK_DISPATCH(d.no, (k_mixed<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_mixed<NO, S><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_vt(const Dev& d, int T, cudaStream_t s) {
-  HK_DISPATCH(d.no, (k_vt<NO><<<d.n_inst, 128, d.r * NO * NO * sizeof(zd), s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_vt<NO, S><<<d.n_inst, 128, d.r * NO * NO * sizeof(zd), s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_src(const Dev& d, int T, cudaStream_t s) {
   const long long warps = (long long)d.n_inst * (T + 1);
-  HK_DISPATCH(d.no, (k_src<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_src<NO, S><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_les(const Dev& d, int T, cudaStream_t s) {
   dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_les<NO><<<g, 256, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_les<NO, S><<<g, 256, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_rho(const Dev& d, int T, cudaStream_t s) {
-  HK_DISPATCH(d.no, (k_rho<NO><<<d.n_inst, 256, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_rho<NO, S><<<d.n_inst, 256, 0, s>>>(d, T)));
+  return cudaGetLastError();
+}
+cudaError_t launch_diag_seed(const Dev& d, cudaStream_t s) {
+  if (!d.diag64) return cudaSuccess;
+  HK_DISPATCH(d.no, (k_diag_seed<NO, S><<<d.n_inst, 128, 0, s>>>(d)));
   return cudaGetLastError();
 }
 cudaError_t launch_boot(const Dev& d, cudaStream_t s) {
@@ -964,9 +986,9 @@ cudaError_t launch_boot(const Dev& d, cudaStream_t s) {
     cudaError_t e = launch_sigma(d, t, s);
     if (e != cudaSuccess) return e;
   }
-  HK_DISPATCH(d.no, (k_boot_mixed<NO><<<d.n_inst, 256, 0, s>>>(d)));
-  HK_DISPATCH(d.no, (k_boot_ret<NO><<<d.n_inst, 32, 0, s>>>(d)));
-  HK_DISPATCH(d.no, (k_boot_les<NO><<<d.n_inst, 32, 0, s>>>(d)));
+  HK_DISPATCH(d.no, (k_boot_mixed<NO, S><<<d.n_inst, 256, 0, s>>>(d)));
+  HK_DISPATCH(d.no, (k_boot_ret<NO, S><<<d.n_inst, 32, 0, s>>>(d)));
+  HK_DISPATCH(d.no, (k_boot_les<NO, S><<<d.n_inst, 32, 0, s>>>(d)));
   return cudaGetLastError();
 }
 cudaError_t launch_set_active(const Dev& d, double tol, int iter, int min_iter, int* any, cudaStream_t s) {

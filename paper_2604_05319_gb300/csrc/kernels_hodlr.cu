@@ -40,7 +40,7 @@ __device__ __forceinline__ double2* Psrc(const Dev& d, int n, int b, int p, int 
          (((((long long)n * d.nblk + b) * (NO * NO) + p) * NO + y) * 2 + which) * d.rmax;
 }
 
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int b = blockIdx.x, n = blockIdx.y;
@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
     const int which = job & 1, y = (job >> 1) % NO, p = (job >> 1) / NO;
     const int z = which == 0 ? p % NO : p / NO;
     const int rk = *Rk<NO>(d, 3, n, b, p);
-    const double2* F = which == 0 ? Up<NO>(d, 3, n, b, p) : Vp<NO>(d, 3, n, b, p);
+    const S* F = which == 0 ? Up<NO, S>(d, 3, n, b, p) : Vp<NO, S>(d, 3, n, b, p);
     const int lo = which == 0 ? r0 : c0, hi = which == 0 ? rl : c1;
     zd part[4] = {zd(), zd(), zd(), zd()};
     for (int l = lo + warp; l < hi; l += 8) {
-      const zd g = ld(el<NO>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
-      const double2* fr = F + (long long)(l - lo) * d.rmax;
+      const zd g = ld(el<NO, S>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
+      const S* fr = F + (long long)(l - lo) * d.rmax;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = lane + 32 * u;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   }
 }
 
-template <int NO>
+template <int NO, typename S>
 __global__ void k_src_h(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -98,16 +98,16 @@ __global__ void k_src_h(Dev d, int T) {
   // part 1, l >= t: S[l][t]
   for (int l = max(t, c) + lane; l <= T; l += 32) {  // uncompressed rows
     const double wl = rule_w(W, T, l);
-    M<NO> S = load<NO>(el<NO>(d.SL, d, n, l, t));
-    M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+    M<NO> Sm = load<NO>(el<NO, S>(d.SL, d, n, l, t));
+    M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(wl));
   }
   if (t < c) {
     for (int l = t + lane; l < min(E, c); l += 32) {  // same leaf
       const double wl = rule_w(W, T, l);
-      M<NO> S = load<NO>(Lf<NO>(d, 3, n, jt, l, t));
-      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(wl));
+      M<NO> Sm = load<NO>(Lf<NO, S>(d, 3, n, jt, l, t));
+      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(wl));
     }
   }
   for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their columns
@@ -118,7 +118,7 @@ __global__ void k_src_h(Dev d, int T) {
     for (int p = 0; p < NO2; ++p) {
       const int x = p / NO;
       const int rk = *Rk<NO>(d, 3, n, b, p);
-      const double2* V = Vp<NO>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
+      const S* V = Vp<NO, S>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
         const double2* P = Psrc<NO>(d, n, b, p, y, 0);
@@ -130,16 +130,16 @@ __global__ void k_src_h(Dev d, int T) {
   if (t >= c) {
     for (int l = lane; l < t; l += 32) {
       const double wl = rule_w(W, T, l);
-      M<NO> S = dag<NO>(load<NO>(el<NO>(d.SL, d, n, t, l)));
-      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(-wl));
+      M<NO> Sm = dag<NO>(load<NO>(el<NO, S>(d.SL, d, n, t, l)));
+      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(-wl));
     }
   } else {
     for (int l = A + lane; l < t; l += 32) {
       const double wl = rule_w(W, T, l);
-      M<NO> S = dag<NO>(load<NO>(Lf<NO>(d, 3, n, jt, t, l)));
-      M<NO> GA = dag<NO>(load<NO>(el<NO>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, GA, zd(-wl));
+      M<NO> Sm = dag<NO>(load<NO>(Lf<NO, S>(d, 3, n, jt, t, l)));
+      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
+      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(-wl));
     }
     for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their rows
       const int b = d.rowblk[jt * d.maxl + lv];
@@ -149,7 +149,7 @@ __global__ void k_src_h(Dev d, int T) {
       for (int p = 0; p < NO2; ++p) {  // p = (z, x): conj(U^{zx}(t,:)) . P2^{(zx), y} -> q_xy
         const int x = p % NO;
         const int rk = *Rk<NO>(d, 3, n, b, p);
-        const double2* U = Up<NO>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
+        const S* U = Up<NO, S>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
 #pragma unroll
         for (int y = 0; y < NO; ++y) {
           const double2* P = Psrc<NO>(d, n, b, p, y, 1);
@@ -163,9 +163,9 @@ __global__ void k_src_h(Dev d, int T) {
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = acc[q] * h;
   for (int a = lane; a < d.r; a += 32) {
-    M<NO> S = load<NO>(tv<NO>(d.STV, d, n, t, a));
+    M<NO> Sm = load<NO>(tv<NO>(d.STV, d, n, t, a));
     M<NO> V = load<NO>(d.vvec + ((long long)n * d.r + a) * NO2);
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), S, V, zd(0, -1));
+    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, V, zd(0, -1));
   }
   warp_sum<NO2>(acc);
   if (lane == 0) {
@@ -178,7 +178,7 @@ __global__ void k_src_h(Dev d, int T) {
 // ---------------------------------------------------------------------------
 // update_blocks: compress the rows [A, A+nb) of every component
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void k_comp_copy(Dev d, int A, int nb) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y;
@@ -195,21 +195,21 @@ __global__ void k_comp_copy(Dev d, int A, int nb) {
       while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
       const int l = (int)(e - (long long)i * (i + 1) / 2);
       const int t = A + i, col = A + l;
-      const double2* src = el<NO>(ringX(d, X), d, n, t, col);
-      double2* dst = Lf<NO>(d, X, n, j, t, col);
+      const S* src = el<NO, S>(ringX(d, X), d, n, t, col);
+      S* dst = Lf<NO, S>(d, X, n, j, t, col);
 #pragma unroll
       for (int q = 0; q < NO2; ++q) dst[q] = src[q];
     } else {
       const long long e = idx - 4 * ntr;
       const int t = A + (int)(e / d.k), dd = (int)(e % d.k) + 1;
-      double2* dst = Bd<NO>(d, n, t, dd);
+      S* dst = Bd<NO, S>(d, n, t, dd);
       if (t - dd >= 0) {
-        const double2* src = el<NO>(d.SR, d, n, t, t - dd);
+        const S* src = el<NO, S>(d.SR, d, n, t, t - dd);
 #pragma unroll
         for (int q = 0; q < NO2; ++q) dst[q] = src[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < NO2; ++q) dst[q] = make_double2(0, 0);
+        for (int q = 0; q < NO2; ++q) st(dst + q, zd());
       }
     }
   }
@@ -218,7 +218,9 @@ __global__ void k_comp_copy(Dev d, int A, int nb) {
 // One CTA per (component X, level slot, pair p) x instance.  Workspace per
 // CTA (complex doubles): E [nb][ncol], Q [nb][ncol], P [nb][rmax], C [nb][nb],
 // K [(rmax+nb)][(rmax+nb)] column-major, Vh [(rmax+nb)][(rmax+nb)] column-major.
-template <int NO>
+constexpr double kF32Unit = 5.9604644775390625e-8;  // 2^-24, complex64 unit roundoff
+
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y;
@@ -241,19 +243,28 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   double2* Km = Cm + (long long)d.L * d.L;            // [ld_k cols][ld_k rows]
   double2* Vh = Km + (long long)ld_k * ld_k;          // [ld_k cols][ld_k rows]
   __shared__ int s_ke, s_rnew;
+  __shared__ double s_wpart[32];
   __shared__ double s_sig[256];
   __shared__ int s_ord[256];
   int* rkp = Rk<NO>(d, X, n, b, p);
   const int r = *rkp;
-  double2* U = Up<NO>(d, X, n, b, p);
-  double2* V = Vp<NO>(d, X, n, b, p);
-  double* S = Sp<NO>(d, X, n, b, p);
-  const double2* ring = ringX(d, X);
-  // E <- new rows
+  S* U = Up<NO, S>(d, X, n, b, p);
+  S* V = Vp<NO, S>(d, X, n, b, p);
+  double* Sv = Sp<NO>(d, X, n, b, p);
+  void* ring = ringX(d, X);
+  // E <- new rows (and max |E| for the complex64 rounding floor below)
+  double emax = 0.0;
   for (long long e = tid; e < (long long)nb * ncol; e += blockDim.x) {
     const int i = (int)(e / ncol), l = (int)(e % ncol);
-    Em[(long long)i * ncol + l] = el<NO>(const_cast<double2*>(ring), d, n, A + i, c0 + l)[p];
+    const zd v = ld(el<NO, S>(ring, d, n, A + i, c0 + l) + p);
+    emax = fmax(emax, v.abs2());
+    st(Em + (long long)i * ncol + l, v);
   }
+  emax = warp_max(emax);
+  if (lane == 0) s_wpart[warp] = emax;
+  __syncthreads();
+  for (int w2 = 0; w2 < nw; ++w2) emax = fmax(emax, s_wpart[w2]);
+  emax = sqrt(emax);
   __syncthreads();
   // P = E V, E -= P V^dagger, twice (the second pass restores orthogonality
   // to V lost to rounding).  The per-pass coefficients are staged in Q's
@@ -283,7 +294,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   // Two-pass Gram-Schmidt on the rows of E: E = C Q, rows of Q orthonormal.
   const double delta = 0.25 * d.svd_tol;
   __shared__ zd s_coef[64];
-  __shared__ double s_nrm;
+
   for (int i = 0; i < nb; ++i) {
     double2* v = Em + (long long)i * ncol;
     for (int pass = 0; pass < 2; ++pass) {
@@ -310,11 +321,11 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
     for (int l = tid; l < ncol; l += blockDim.x) part += ld(v + l).abs2();
 #pragma unroll
     for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if (tid == 0) s_nrm = 0.0;
+    if (lane == 0) s_wpart[warp] = part;
     __syncthreads();
-    if (lane == 0) atomicAdd(&s_nrm, part);
-    __syncthreads();
-    const double nrm = sqrt(s_nrm);
+    double nsq = 0.0;  // fixed summation order: reproducible bit for bit
+    for (int w2 = 0; w2 < nw; ++w2) nsq += s_wpart[w2];
+    const double nrm = sqrt(nsq);
     const int ke = s_ke;
     if (nrm > delta) {
       for (int l = tid; l < ncol; l += blockDim.x) st(Qm + (long long)ke * ncol + l, ld(v + l) * (1.0 / nrm));
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   for (int e = tid; e < nk * m; e += blockDim.x) {
     const int col = e / m, row = e % m;
     zd v = zd();
-    if (row < r) v = (col == row) ? zd(S[row]) : zd();
+    if (row < r) v = (col == row) ? zd(Sv[row]) : zd();
     else if (col < r) v = ld(Pm + (long long)(row - r) * rmax + col);
     else v = ld(Cm + (long long)(row - r) * d.L + (col - r));
     st(Km + (long long)col * ld_k + row, v);
@@ -416,8 +427,16 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
         if (s_sig[s_ord[q]] > s_sig[s_ord[best]]) best = q;
       int t2 = s_ord[i]; s_ord[i] = s_ord[best]; s_ord[best] = t2;
     }
+    // Truncation threshold: eps_SVD, raised in the complex64 storage form to
+    // the rounding floor of the appended rows.  Their rounding is a matrix of
+    // independent entries below 2^-24 max|E|, whose largest singular value
+    // stays below 2^-24 max|E| (sqrt(nb) + sqrt(ncol)); directions under that
+    // level are storage noise, and keeping them would let the rank grow by the
+    // leaf size at every append.
+    double tol = d.svd_tol;
+    if (sizeof(S) == sizeof(float2)) tol = fmax(tol, kF32Unit * emax * (sqrt((double)nb) + sqrt((double)ncol)));
     int rn = 0;
-    while (rn < nk && s_sig[s_ord[rn]] > d.svd_tol) ++rn;
+    while (rn < nk && s_sig[s_ord[rn]] > tol) ++rn;
     if (rn > rmax) { atomicAdd(d.status, 1); rn = rmax; }
     s_rnew = rn;
   }
@@ -426,7 +445,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   // U' = [[U, 0], [0, I]] Uhat : old rows r0..A-1, new rows A..A+nb-1
   const int nold = A - r0;
   for (int row = warp; row < nold + nb; row += nw) {
-    double2* urow = U + (long long)row * rmax;
+    S* urow = U + (long long)row * rmax;
     // compute U'[row][j] for j = lane, lane+32, ...
     zd res[4];
     for (int t2 = 0; t2 < 4; ++t2) res[t2] = zd();
@@ -452,7 +471,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   }
   // V' = [V, Q^H] Vhat
   for (int l = warp; l < ncol; l += nw) {
-    double2* vrow = V + (long long)l * rmax;
+    S* vrow = V + (long long)l * rmax;
     zd res[4];
     for (int t2 = 0; t2 < 4; ++t2) {
       res[t2] = zd();
@@ -473,13 +492,13 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
     __syncwarp();
   }
   __syncthreads();
-  for (int q = tid; q < rmax; q += blockDim.x) S[q] = (q < rn) ? s_sig[s_ord[q]] : 0.0;
+  for (int q = tid; q < rmax; q += blockDim.x) Sv[q] = (q < rn) ? s_sig[s_ord[q]] : 0.0;
   if (tid == 0) *rkp = rn;
 }
 
 // Reconstruct row T of G^R and G^< (any T <= current) into out_r, out_l
 // ([T+1][no2] each), from the ring, the leaves or the blocks.
-template <int NO>
+template <int NO, typename S>
 __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
   constexpr int NO2 = NO * NO;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,21 +509,21 @@ __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
     for (int p = 0; p < NO2; ++p) {
       zd v;
       if (T >= d.cdir) {
-        v = ld(el<NO>(ringX(d, X), d, n, T, t) + p);
+        v = ld(el<NO, S>(ringX(d, X), d, n, T, t) + p);
       } else {
         const int jT = T / d.L, jt = t / d.L;
         if (jT == jt) {
-          v = ld(Lf<NO>(d, X, n, jT, T, t) + p);
+          v = ld(Lf<NO, S>(d, X, n, jT, T, t) + p);
         } else {
           v = zd();
           for (int lv = 0; lv < d.maxl; ++lv) {
             const int b = d.rowblk[jT * d.maxl + lv];
             if (b < 0 || t < d.b_c0[b] || t >= d.b_c1[b]) continue;
             const int rk = *Rk<NO>(d, X, n, b, p);
-            const double2* U = Up<NO>(d, X, n, b, p) + (long long)(T - d.b_r0[b]) * d.rmax;
-            const double2* V = Vp<NO>(d, X, n, b, p) + (long long)(t - d.b_c0[b]) * d.rmax;
-            const double* S = Sp<NO>(d, X, n, b, p);
-            for (int q = 0; q < rk; ++q) v += ld(U + q) * ld(V + q).conj() * S[q];
+            const S* U = Up<NO, S>(d, X, n, b, p) + (long long)(T - d.b_r0[b]) * d.rmax;
+            const S* V = Vp<NO, S>(d, X, n, b, p) + (long long)(t - d.b_c0[b]) * d.rmax;
+            const double* Sv = Sp<NO>(d, X, n, b, p);
+            for (int q = 0; q < rk; ++q) v += ld(U + q) * ld(V + q).conj() * Sv[q];
           }
         }
       }
@@ -513,35 +532,39 @@ __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
   }
 }
 
-#define HK_DISPATCH(NOV, CALL)                       \
-  switch (NOV) {                                     \
-    case 1: { constexpr int NO = 1; CALL; break; }   \
-    case 2: { constexpr int NO = 2; CALL; break; }   \
-    case 3: { constexpr int NO = 3; CALL; break; }   \
-    case 4: { constexpr int NO = 4; CALL; break; }   \
-    default: return cudaErrorInvalidValue;           \
+#define HK_DISPATCH(NOV, CALL)                                                  \
+  switch ((NOV) * 2 + d.prec) {                                                 \
+    case 2: { constexpr int NO = 1; using S = double2; CALL; break; }           \
+    case 3: { constexpr int NO = 1; using S = float2; CALL; break; }            \
+    case 4: { constexpr int NO = 2; using S = double2; CALL; break; }           \
+    case 5: { constexpr int NO = 2; using S = float2; CALL; break; }            \
+    case 6: { constexpr int NO = 3; using S = double2; CALL; break; }           \
+    case 7: { constexpr int NO = 3; using S = float2; CALL; break; }            \
+    case 8: { constexpr int NO = 4; using S = double2; CALL; break; }           \
+    case 9: { constexpr int NO = 4; using S = float2; CALL; break; }            \
+    default: return cudaErrorInvalidValue;                                      \
   }
 
 cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s) {
   if (d.cdir > 0) {
     dim3 g(d.nblk, d.n_inst);
-    HK_DISPATCH(d.no, (k_src_proj<NO><<<g, 256, 0, s>>>(d, T)));
+    HK_DISPATCH(d.no, (k_src_proj<NO, S><<<g, 256, 0, s>>>(d, T)));
   }
   const long long warps = (long long)d.n_inst * (T + 1);
-  HK_DISPATCH(d.no, (k_src_h<NO><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_src_h<NO, S><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s) {
   {
     dim3 g(64, d.n_inst);
-    HK_DISPATCH(d.no, (k_comp_copy<NO><<<g, 256, 0, s>>>(d, A, nb)));
+    HK_DISPATCH(d.no, (k_comp_copy<NO, S><<<g, 256, 0, s>>>(d, A, nb)));
   }
   dim3 g(4 * d.maxl * d.no * d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_tsvd<NO><<<g, 256, 0, s>>>(d, A, nb)));
+  HK_DISPATCH(d.no, (k_tsvd<NO, S><<<g, 256, 0, s>>>(d, A, nb)));
   return cudaGetLastError();
 }
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s) {
-  HK_DISPATCH(d.no, (k_row_out<NO><<<(T + 128) / 128, 128, 0, s>>>(d, n, T, out_r, out_l)));
+  HK_DISPATCH(d.no, (k_row_out<NO, S><<<(T + 128) / 128, 128, 0, s>>>(d, n, T, out_r, out_l)));
   return cudaGetLastError();
 }
 

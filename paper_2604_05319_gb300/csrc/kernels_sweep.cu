@@ -25,7 +25,27 @@ namespace hk {
 namespace {
 
 constexpr int CK = 32;   // chunk length
+using Y = double2;       // element type of the row / column being solved
 
+// Where a sweep keeps the row it solves: in place (FP64 storage) or in the
+// FP64 buffer row64[n][which] (complex64 storage).
+template <int NO, typename S>
+struct Row64 {
+  static constexpr bool separate = true;
+  __device__ static Y* get(const Dev& d, int n, int which, S*) {
+    return d.row64 + ((long long)n * 2 + which) * d.nt * (NO * NO);
+  }
+};
+template <int NO>
+struct Row64<NO, double2> {
+  static constexpr bool separate = false;
+  __device__ static Y* get(const Dev&, int, int, double2* p) { return p; }
+};
+
+// Inverse of frozen chunk cc of sweep `which`: complex128 in both storage
+// forms (it solves the implicit part of the Volterra equation; a complex64
+// inverse would put a relative error of order 2^-24 times the BDF amplitude
+// a_j / h into every chunk and accumulate along the sweep).
 template <int NO>
 __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which) {
   const long long nn = (long long)(CK * NO) * (CK * NO);
@@ -38,7 +58,7 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
 // Retarded row, Eq. KBER: unknown y(t') = G^R(T, t') (row irow), solved for
 // t' = T-1 .. 0; the start block t' >= T-k is solved together.
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y, irow = blockIdx.x;
@@ -54,8 +74,15 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
   if (tid == 0) serr = 0.0;
-  double2* rowp = el<NO>(d.GR, d, n, T, 0);
-  auto yp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };
+  // The row being solved lives in FP64 during the sweep (in the complex64
+  // storage form a separate buffer, copied out rounded at the end), so the
+  // point-to-point recursion of the sweep does not accumulate storage rounding.
+  // yp: the row as the sweep reads and writes it; sp: its storage (previous
+  // iterate, for the convergence measure).
+  S* rowp = el<NO, S>(d.GR, d, n, T, 0);
+  Y* rowy = Row64<NO, S>::get(d, n, 0, rowp);
+  auto yp = [&](int tp) { return rowy + (long long)tp * NO2 + irow * NO; };
+  auto sp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };
   double myerr = 0.0;
   // ---- start block t' = T-k .. T-1 (s = 1..k), and y(T) = -i ----
   const int ns = k * NO;
@@ -63,14 +90,14 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
     for (int e = lane; e < ns * ns; e += 32) {
       const int row = e / ns, col = e % ns;
       const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
-      zd v = srx_any<NO>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
+      zd v = srx_any<NO, S>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
       if (m == j) v += zd(0, W.D[s][l] / h);
       if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
       sA[row * ns + col] = v;
     }
     for (int row = lane; row < ns; row += 32) {
       const int s = row / NO + 1, j = row % NO;
-      zd cc = srx_any<NO>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
+      zd cc = srx_any<NO, S>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
       if (irow == j) cc += zd(0, W.D[s][0] / h);
       sB[row] = zd(0, 1) * cc;
     }
@@ -78,16 +105,14 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
     warp_lu_solve(ns, sA, sB, 1, nullptr);
     for (int row = lane; row < ns; row += 32) {
       const int s = row / NO + 1, j = row % NO;
-      double2* p = yp(T - s) + j;
-      myerr = fmax(myerr, (sB[row] - ld(p)).abs2());
-      st(p, sB[row]);
+      myerr = fmax(myerr, (sB[row] - ld(sp(T - s) + j)).abs2());
+      st(yp(T - s) + j, sB[row]);
     }
     if (lane == 0) {
-      double2* p = yp(T);
       for (int j = 0; j < NO; ++j) {
         zd v = (j == irow) ? zd(0, -1) : zd();
-        myerr = fmax(myerr, (ld(p + j) - v).abs2());
-        st(p + j, v);
+        myerr = fmax(myerr, (ld(sp(T) + j) - v).abs2());
+        st(yp(T) + j, v);
       }
     }
   }
@@ -107,11 +132,11 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         for (int p = 0; p < NO2; ++p) {
           const int m = p / NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
-          const double2* U = Up<NO>(d, 2, n, blk, p);
+          const S* U = Up<NO, S>(d, 2, n, blk, p);
           zd part[4] = {zd(), zd(), zd(), zd()};
           for (int s2 = r0 + warp; s2 < rl; s2 += 8) {  // warps over rows, lanes over rank
             const zd yv = ld(yp(s2) + m);
-            const double2* ur = U + (long long)(s2 - r0) * d.rmax;
+            const S* ur = U + (long long)(s2 - r0) * d.rmax;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int q = lane + 32 * u;
@@ -142,8 +167,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         if (col < L) {
           for (int s2 = c + sl; s2 <= T; s2 += 4) {
             const double ws = rule_w(W, T - tp, T - s2);
-            const double2* yl = yp(s2);
-            const double2* sr = el<NO>(d.SR, d, n, s2, tp);
+            const Y* yl = yp(s2);
+            const S* sr = el<NO, S>(d.SR, d, n, s2, tp);
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               const zd ym = ld(yl + m) * ws;
@@ -159,15 +184,15 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
             for (int p = 0; p < NO2; ++p) {
               const int j = p % NO;
               const int rk = *Rk<NO>(d, 2, n, blk, p);
-              const double2* V = Vp<NO>(d, 2, n, blk, p) + (long long)(tp - c0) * d.rmax;
+              const S* V = Vp<NO, S>(d, 2, n, blk, p) + (long long)(tp - c0) * d.rmax;
               const double2* P = Pj<NO>(d, n, irow, lv, p);
               for (int q = sl; q < rk; q += 4) acc[j] = cfma(ld(P + q), ld(V + q).conj(), acc[j]);
             }
           }
           for (int s2 = E + sl; s2 <= tp + k && s2 < c; s2 += 4) {
             const double ws = rule_w(W, T - tp, T - s2) - 1.0;
-            const double2* bd = Bd<NO>(d, n, s2, s2 - tp);
-            const double2* yl = yp(s2);
+            const S* bd = Bd<NO, S>(d, n, s2, s2 - tp);
+            const Y* yl = yp(s2);
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               const zd ym = ld(yl + m) * ws;
@@ -198,8 +223,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         const int s_end = comp ? E : T + 1;   // compressed: the rest of the leaf; else every later row
         for (int s2 = b + sl; s2 < s_end; s2 += 8) {
           const double ws = rule_w(W, T - tp, T - s2);
-          const double2* yl = yp(s2);
-          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, s2, tp) : el<NO>(d.SR, d, n, s2, tp);
+          const Y* yl = yp(s2);
+          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, s2, tp) : el<NO, S>(d.SR, d, n, s2, tp);
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
             const zd ym = ld(yl + m) * ws;
@@ -244,9 +269,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         for (int off = 1; off < 8; off <<= 1)
           sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
         if (sl == 0) {
-          double2* p = yp(a + ti) + j;
-          myerr = fmax(myerr, (sacc - ld(p)).abs2());
-          st(p, sacc);
+          myerr = fmax(myerr, (sacc - ld(sp(a + ti) + j)).abs2());
+          st(yp(a + ti) + j, sacc);
         }
       }
     } else if (warp == 0) {
@@ -258,7 +282,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
       zd f[NO];
       if (L0 < cn) {
         const double ws = h * rule_w(W, T - tq, T - tq);
-        const double2* sd = comp ? Lf<NO>(d, 2, n, jl, tq, tq) : el<NO>(d.SR, d, n, tq, tq);
+        const S* sd = comp ? Lf<NO, S>(d, 2, n, jl, tq, tq) : el<NO, S>(d.SR, d, n, tq, tq);
         const double2* ep = epsp<NO>(d, n, tq);
         M<NO> Mm;
 #pragma unroll
@@ -271,13 +295,13 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         for (int j = 0; j < NO; ++j) f[j] = Fs[L0][j];
       }
       for (int i = cn - 1; i >= 0; --i) {
-        const int sp = a + i;
-        // coefficient C(sp, tq) for this lane (only lanes with tq < sp use it)
+        const int spt = a + i;
+        // coefficient C(spt, tq) for this lane (only lanes with tq < spt use it)
         zd cf[NO2];
         if (L0 < i) {
-          const double wl = -h * rule_w(W, T - tq, T - sp);
-          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, sp, tq) : el<NO>(d.SR, d, n, sp, tq);
-          const int dd = sp - tq;
+          const double wl = -h * rule_w(W, T - tq, T - spt);
+          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, spt, tq) : el<NO, S>(d.SR, d, n, spt, tq);
+          const int dd = spt - tq;
 #pragma unroll
           for (int q = 0; q < NO2; ++q) {
             cf[q] = ld(sr + q) * wl;
@@ -292,11 +316,10 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
 #pragma unroll
             for (int m = 0; m < NO; ++m) y[j] = cfma(f[m], Dinv.a[m][j], y[j]);
           }
-          double2* p = yp(sp);
 #pragma unroll
           for (int j = 0; j < NO; ++j) {
-            myerr = fmax(myerr, (y[j] - ld(p + j)).abs2());
-            st(p + j, y[j]);
+            myerr = fmax(myerr, (y[j] - ld(sp(spt) + j)).abs2());
+            st(yp(spt) + j, y[j]);
           }
         }
 #pragma unroll
@@ -311,6 +334,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
     }
     __syncthreads();
   }
+  if (Row64<NO, S>::separate)  // copy the FP64 row out to its storage, rounded
+    for (int e = tid; e < (T + 1) * NO; e += blockDim.x) st(sp(e / NO) + e % NO, ld(yp(e / NO) + e % NO));
   myerr = sqrt(warp_max(myerr));
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
@@ -320,7 +345,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
 // ---------------------------------------------------------------------------
 // Lesser column, Eq. KBEL: unknown x(t) = G^<(t, T) (column jc), t = 0..T.
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y, jc = blockIdx.x;
@@ -336,17 +361,19 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
   if (tid == 0) serr = 0.0;
-  double2* colp = el<NO>(d.GL, d, n, T, 0);
-  auto xp = [&](int t) { return colp + (long long)t * NO2; };  // element [m*NO + jc]
+  // FP64 column during the sweep (see k_ret2); xp: as solved, sp: storage
+  S* colp = el<NO, S>(d.GL, d, n, T, 0);
+  Y* coly = Row64<NO, S>::get(d, n, 1, colp);
+  auto xp = [&](int t) { return coly + (long long)t * NO2; };  // element [m*NO + jc]
+  auto sp = [&](int t) { return colp + (long long)t * NO2; };
   const double2* qs = d.qsrc + (long long)n * d.nt * NO2;
   double myerr = 0.0;
   const int last = (d.rho_mode == 1) ? T - 1 : T;
   if (warp == 0 && lane < NO) {  // x(0) = -[G^tv(T, 0+)]^dagger
     const int m = lane;
     zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
-    double2* p = xp(0) + m * NO + jc;
-    myerr = fmax(myerr, (v - ld(p)).abs2());
-    st(p, v);
+    myerr = fmax(myerr, (v - ld(sp(0) + m * NO + jc)).abs2());
+    st(xp(0) + m * NO + jc, v);
   }
   __syncthreads();
   for (int cc = 0; cc * CK <= last; ++cc) {
@@ -364,12 +391,12 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         for (int p = 0; p < NO2; ++p) {
           const int nn = p % NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
-          const double2* V = Vp<NO>(d, 2, n, blk, p);
+          const S* V = Vp<NO, S>(d, 2, n, blk, p);
           zd part[4] = {zd(), zd(), zd(), zd()};
           for (int l = c0 + warp; l < c1; l += 8) {  // warps over columns, lanes over rank
             const double wl = (l <= k) ? W.omega[l] : 1.0;
             const zd xv = ld(xp(l) + nn * NO + jc) * wl;
-            const double2* vr = V + (long long)(l - c0) * d.rmax;
+            const S* vr = V + (long long)(l - c0) * d.rmax;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int q = lane + 32 * u;
@@ -404,14 +431,14 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
             for (int p = 0; p < NO2; ++p) {
               const int m = p / NO;
               const int rk = *Rk<NO>(d, 2, n, blk, p);
-              const double2* U = Up<NO>(d, 2, n, blk, p) + (long long)(t - r0) * d.rmax;
+              const S* U = Up<NO, S>(d, 2, n, blk, p) + (long long)(t - r0) * d.rmax;
               const double2* P = Pj<NO>(d, n, jc, lv, p);
               for (int q = sl; q < rk; q += 4) acc[m] = cfma(ld(U + q), ld(P + q), acc[m]);
             }
           }
           for (int l = max(t - k, 0) + sl; l < A; l += 4) {
             const double wl = rule_w(W, t, l) - 1.0;
-            const double2* bd = Bd<NO>(d, n, t, t - l);
+            const S* bd = Bd<NO, S>(d, n, t, t - l);
 #pragma unroll
             for (int y = 0; y < NO; ++y) {
               const zd xy = ld(xp(l) + y * NO + jc) * wl;
@@ -445,7 +472,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
               const zd xv = ld(xp(0) + y * NO + jc);
 #pragma unroll
               for (int m = 0; m < NO; ++m) {
-                zd cf = srx_any<NO>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
+                zd cf = srx_any<NO, S>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
                 if (m == y) cf += zd(0, W.D[t][0] / h);
                 acc[m] -= cf * xv;
               }
@@ -453,10 +480,10 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           }
         } else {
           const int l0 = comp ? A : 0;
-          const double2* srow = comp ? nullptr : el<NO>(d.SR, d, n, t, 0);
+          const S* srow = comp ? nullptr : el<NO, S>(d.SR, d, n, t, 0);
           for (int l = l0 + sl; l < a; l += 8) {
             const double wl = h * rule_w(W, t, l);
-            const double2* sr = comp ? Lf<NO>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
+            const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
 #pragma unroll
             for (int y = 0; y < NO; ++y) {
               const zd xy = ld(xp(l) + y * NO + jc) * wl;
@@ -500,9 +527,8 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         for (int off = 1; off < 8; off <<= 1)
           sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
         if (sl == 0 && ti < cn) {
-          double2* p = xp(a + ti) + m * NO + jc;
-          myerr = fmax(myerr, (sacc - ld(p)).abs2());
-          st(p, sacc);
+          myerr = fmax(myerr, (sacc - ld(sp(a + ti) + m * NO + jc)).abs2());
+          st(xp(a + ti) + m * NO + jc, sacc);
         }
       }
     } else if (warp == 0) {
@@ -519,7 +545,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         for (int e = lane; e < nsb * nsb; e += 32) {
           const int row = e / nsb, col = e % nsb;
           const int t = row / NO + 1, m = row % NO, l = col / NO + 1, y = col % NO;
-          zd v = srx_any<NO>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
+          zd v = srx_any<NO, S>(d, n, t, l, m, y) * (-h * W.I0[t][l]);
           if (m == y) v += zd(0, W.D[t][l] / h);
           if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + y);
           sA[row * nsb + col] = v;
@@ -530,16 +556,15 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         for (int row = lane; row < nsb; row += 32) {
           const int t = row / NO + 1, m = row % NO;
           if (t <= last) {
-            double2* p = xp(t) + m * NO + jc;
-            myerr = fmax(myerr, (sB[row] - ld(p)).abs2());
-            st(p, sB[row]);
+            myerr = fmax(myerr, (sB[row] - ld(sp(t) + m * NO + jc)).abs2());
+            st(xp(t) + m * NO + jc, sB[row]);
           }
         }
         __syncwarp();
         if (L0 < cn && tq > k) {  // rows below the start block remove its contribution
           for (int l = 1; l <= k; ++l) {
             const double wl = -h * rule_w(W, tq, l);
-            const double2* sr = comp ? Lf<NO>(d, 2, n, jl, tq, l) : el<NO>(d.SR, d, n, tq, l);
+            const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, tq, l) : el<NO, S>(d.SR, d, n, tq, l);
             const int dd = tq - l;
 #pragma unroll
             for (int m = 0; m < NO; ++m)
@@ -556,7 +581,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
       M<NO> Dinv;
       if (L0 < cn && L0 >= i0) {
         const double wt = h * rule_w(W, tq, tq);
-        const double2* sd = comp ? Lf<NO>(d, 2, n, jl, tq, tq) : el<NO>(d.SR, d, n, tq, tq);
+        const S* sd = comp ? Lf<NO, S>(d, 2, n, jl, tq, tq) : el<NO, S>(d.SR, d, n, tq, tq);
         const double2* ep = epsp<NO>(d, n, tq);
         M<NO> Mm;
 #pragma unroll
@@ -571,7 +596,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         zd cf[NO2];
         if (L0 > i && L0 < cn) {
           const double wl = -h * rule_w(W, tq, tp);
-          const double2* sr = comp ? Lf<NO>(d, 2, n, jl, tq, tp) : el<NO>(d.SR, d, n, tq, tp);
+          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, tq, tp) : el<NO, S>(d.SR, d, n, tq, tp);
           const int dd = tq - tp;
 #pragma unroll
           for (int q = 0; q < NO2; ++q) {
@@ -589,9 +614,8 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           }
 #pragma unroll
           for (int m = 0; m < NO; ++m) {
-            double2* p = xp(tp) + m * NO + jc;
-            myerr = fmax(myerr, (x[m] - ld(p)).abs2());
-            st(p, x[m]);
+            myerr = fmax(myerr, (x[m] - ld(sp(tp) + m * NO + jc)).abs2());
+            st(xp(tp) + m * NO + jc, x[m]);
           }
         }
 #pragma unroll
@@ -606,6 +630,11 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
     }
     __syncthreads();
   }
+  if (Row64<NO, S>::separate)  // copy the FP64 column out (rows 0..last), rounded
+    for (int e = tid; e < (last + 1) * NO; e += blockDim.x) {
+      const int t = e / NO, m = e % NO;
+      st(sp(t) + m * NO + jc, ld(xp(t) + m * NO + jc));
+    }
   myerr = sqrt(warp_max(myerr));
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
@@ -621,7 +650,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
 // unknowns x(t), rows t of the chunk; rows t <= k are the start equations with
 // D and I_{0,t,.}, other rows the BDF/Gregory equation with the weights w^(t)_l.
 // ---------------------------------------------------------------------------
-template <int NO>
+template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, double2* ws) {
   const int n = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -632,8 +661,9 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
   const int cnt = (which == 1 && cc == 0) ? CK - 1 : CK;
   const int nn = cnt * NO;
   constexpr int LD = CK * NO;
-  double2* B = Cinv<NO>(d, n, cc, which);
-  double2* Am = ws + (long long)n * LD * LD;
+  double2* Bout = Cinv<NO>(d, n, cc, which);
+  double2* Am = ws + (long long)n * 2 * LD * LD;   // FP64 work matrix
+  double2* B = Am + (long long)LD * LD;            // FP64 inverse under construction
   __shared__ zd fcol[CK * 4];
   __shared__ int s_piv;
   __shared__ zd s_inv;
@@ -645,7 +675,7 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
       const int s = a + ri, tp = a + ci, dd = s - tp;
       if (dd >= 0) {
         const double wf = (dd <= k) ? W.omega[dd] : 1.0;
-        v = sr_any<NO>(d, n, s, tp, m, j) * (-h * wf);
+        v = sr_any<NO, S>(d, n, s, tp, m, j) * (-h * wf);
         if (dd <= k && m == j) v += zd(0, W.a[dd] / h);
         if (dd == 0) v -= ld(epsp<NO>(d, n, tp) + m * NO + j);
       }
@@ -653,12 +683,12 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
       const int t = a + ri, l = a + ci;
       if (t <= k) {
         if (l <= k) {
-          v = srx_any<NO>(d, n, t, l, m, j) * (-h * W.I0[t][l]);
+          v = srx_any<NO, S>(d, n, t, l, m, j) * (-h * W.I0[t][l]);
           if (m == j) v += zd(0, W.D[t][l] / h);
           if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + j);
         }
       } else if (l <= t) {
-        v = sr_any<NO>(d, n, t, l, m, j) * (-h * rule_w(W, t, l));
+        v = sr_any<NO, S>(d, n, t, l, m, j) * (-h * rule_w(W, t, l));
         if (t - l <= k && m == j) v += zd(0, W.a[t - l] / h);
         if (l == t) v -= ld(epsp<NO>(d, n, t) + m * NO + j);
       }
@@ -709,30 +739,38 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
     }
     __syncthreads();
   }
+  for (int e = tid; e < nn * nn; e += blockDim.x) {
+    const int r = e / nn, col = e % nn;
+    st(Bout + (long long)r * LD + col, ld(B + (long long)r * LD + col));
+  }
 }
 
-#define HK_DISPATCH(NOV, CALL)                       \
-  switch (NOV) {                                     \
-    case 1: { constexpr int NO = 1; CALL; break; }   \
-    case 2: { constexpr int NO = 2; CALL; break; }   \
-    case 3: { constexpr int NO = 3; CALL; break; }   \
-    case 4: { constexpr int NO = 4; CALL; break; }   \
-    default: return cudaErrorInvalidValue;           \
+#define HK_DISPATCH(NOV, CALL)                                                  \
+  switch ((NOV) * 2 + d.prec) {                                                 \
+    case 2: { constexpr int NO = 1; using S = double2; CALL; break; }           \
+    case 3: { constexpr int NO = 1; using S = float2; CALL; break; }            \
+    case 4: { constexpr int NO = 2; using S = double2; CALL; break; }           \
+    case 5: { constexpr int NO = 2; using S = float2; CALL; break; }            \
+    case 6: { constexpr int NO = 3; using S = double2; CALL; break; }           \
+    case 7: { constexpr int NO = 3; using S = float2; CALL; break; }            \
+    case 8: { constexpr int NO = 4; using S = double2; CALL; break; }           \
+    case 9: { constexpr int NO = 4; using S = float2; CALL; break; }            \
+    default: return cudaErrorInvalidValue;                                      \
   }
 
 cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
   dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_ret2<NO><<<g, 256, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_ret2<NO, S><<<g, 256, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
   dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_les2<NO><<<g, 256, 0, s>>>(d, T)));
+  HK_DISPATCH(d.no, (k_les2<NO, S><<<g, 256, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s) {
   for (int cc = c0; cc < c1; ++cc) {
-    HK_DISPATCH(d.no, (k_chunk_inv<NO><<<d.n_inst, 256, 0, s>>>(d, which, cc, d.cinv_ws)));
+    HK_DISPATCH(d.no, (k_chunk_inv<NO, S><<<d.n_inst, 256, 0, s>>>(d, which, cc, d.cinv_ws)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

