@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   double2* Cm = Pm + (long long)d.L * rmax;           // [nb][nb]
   double2* Km = Cm + (long long)d.L * d.L;            // [ld_k cols][ld_k rows]
   double2* Vh = Km + (long long)ld_k * ld_k;          // [ld_k cols][ld_k rows]
-  __shared__ int s_ke, s_rnew;
+  __shared__ int s_rnew;
   __shared__ double s_wpart[32];
   __shared__ double s_sig[256];
   __shared__ int s_ord[256];
@@ -289,16 +289,17 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
     __syncthreads();
   }
   for (long long e = tid; e < (long long)d.L * d.L; e += blockDim.x) Cm[e] = make_double2(0, 0);
-  if (tid == 0) s_ke = 0;
   __syncthreads();
   // Two-pass Gram-Schmidt on the rows of E: E = C Q, rows of Q orthonormal.
   const double delta = 0.25 * d.svd_tol;
   __shared__ zd s_coef[64];
 
+  // ke, the number of accepted basis rows, is kept in a register: every thread
+  // takes the same accept decision from the same (fixed-order) norm.
+  int ke = 0;
   for (int i = 0; i < nb; ++i) {
     double2* v = Em + (long long)i * ncol;
     for (int pass = 0; pass < 2; ++pass) {
-      const int ke = s_ke;
       for (int e = warp; e < ke; e += nw) {  // coef_e = <Q_e, v>
         const double2* qe = Qm + (long long)e * ncol;
         zd s = zd();
@@ -326,17 +327,13 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
     double nsq = 0.0;  // fixed summation order: reproducible bit for bit
     for (int w2 = 0; w2 < nw; ++w2) nsq += s_wpart[w2];
     const double nrm = sqrt(nsq);
-    const int ke = s_ke;
     if (nrm > delta) {
       for (int l = tid; l < ncol; l += blockDim.x) st(Qm + (long long)ke * ncol + l, ld(v + l) * (1.0 / nrm));
-      if (tid == 0) {
-        st(Cm + (long long)i * d.L + ke, zd(nrm));
-        s_ke = ke + 1;
-      }
+      if (tid == 0) st(Cm + (long long)i * d.L + ke, zd(nrm));
+      ++ke;
     }
     __syncthreads();
   }
-  const int ke = s_ke;
   const int m = r + nb, nk = r + ke;  // core rows, columns
   // K = [[diag(S), 0], [P, C]] column-major; Vh = I
   for (long long e = tid; e < (long long)ld_k * ld_k; e += blockDim.x) {

@@ -90,3 +90,32 @@ def test_hodlr_rewind_reproduces():
     b = st.dense(0)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() < 1e-13
+
+
+@pytest.mark.parametrize("prec", [pk.PREC_FP64, pk.PREC_MIXED])
+def test_hodlr_batch_of_instances(prec):
+    """Three instances (different eps0) stepped together in the compressed
+    form: each must match its own oracle run and carry its own ranks."""
+    nt, h, seeds = 320, 0.02, (1, 2, 3)
+    ws = [wk.bethe_workload(nt=nt, h=h, k=5, beta=BETA, seed=s, quench=(0.0, 1.0, 3.0)) for s in seeds]
+    for w, s in zip(ws, seeds):  # distinct quench amplitudes per instance
+        w["eps"][0, 1:, 0, 0] *= 0.5 + 0.25 * s
+    st = pk.Stepper(nt, h, 5, BETA, n_inst=3, tol=1e-13 if prec == pk.PREC_FP64 else 1e-7, max_iter=60,
+                    svd_tol=1e-8, leaf=32, r_max=64, precision=prec)
+    mid, _ = pk.model_params_for(ws[0])
+    mp = np.concatenate([pk.model_params_for(w)[1] for w in ws])
+    st.set_inputs(ws[0]["tau"], ws[0]["omega"], np.concatenate([w["gm"] for w in ws]),
+                  np.concatenate([w["eps"] for w in ws]), mid, mp)
+    st.run()
+    nb = len(pk.hkbe_get_blocks(st.h)["r0"])
+    for i, w in enumerate(ws):
+        o = from_workload(w, tol=1e-13)
+        o.run()
+        GR, GL, GTV = st.dense(i)
+        n = GR.shape[0]
+        idx = np.tril_indices(n)
+        err = max(np.abs(GR[idx] - o.GR[:n, :n][idx]).max(), np.abs(GL[idx] - o.GLs[:n, :n][idx]).max(),
+                  np.abs(GTV - o.GTV[:n]).max())
+        ranks, _ = pk.hkbe_get_ranks(st.h, i, 2, nb, 1)
+        print("instance", i, "err", err, "max rank", ranks.max())
+        assert err < (1e-7 if prec == pk.PREC_FP64 else 1e-6), (i, err)
