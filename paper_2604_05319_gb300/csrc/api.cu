@@ -268,6 +268,10 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   std::memcpy(d.w.omega, w.omega, sizeof(w.omega));
   std::memcpy(d.w.D, w.D, sizeof(w.D));
   std::memcpy(d.w.I0, w.I0, sizeof(w.I0));
+  for (int i = 0; i < 6; ++i) {
+    d.w.omegaf[i] = (float)w.omega[i];
+    for (int j = 0; j < 6; ++j) d.w.I0f[i][j] = (float)w.I0[i][j];
+  }
   h->hodlr = p->svd_tol > 0;
   size_t tri = (size_t)d.n_inst * d.ntri * d.no * d.no;
   int rc = HKBE_OK;

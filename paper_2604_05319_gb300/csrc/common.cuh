@@ -17,6 +17,7 @@ struct cx {
   R re, im;
   cx() = default;
   HD cx(R r, R i = 0) : re(r), im(i) {}
+  template <typename Q> HD explicit cx(const cx<Q>& o) : re((R)o.re), im((R)o.im) {}
   HD cx operator+(const cx& o) const { return cx(re + o.re, im + o.im); }
   HD cx operator-(const cx& o) const { return cx(re - o.re, im - o.im); }
   HD cx operator-() const { return cx(-re, -im); }
@@ -42,6 +43,21 @@ HD void st(double2* p, const zd& z) { *p = make_double2(z.re, z.im); }
 // double, stores round to nearest float
 HD zd ld(const float2* p) { float2 v = *p; return zd((double)v.x, (double)v.y); }
 HD void st(float2* p, const zd& z) { *p = make_float2((float)z.re, (float)z.im); }
+
+// ---- bulk arithmetic of the history sums --------------------------------
+// Bulk<S>::R is the arithmetic type of the long history contractions for
+// storage type S: double for complex128 storage, float for complex64.  Short
+// runs of products are summed in R and folded into FP64 accumulators (fold),
+// so the rounding of a float partial sum covers a few terms only.
+template <typename S> struct Bulk;
+template <> struct Bulk<double2> { using R = double; };
+template <> struct Bulk<float2> { using R = float; };
+
+template <typename R> HD cx<R> ldr(const double2* p) { double2 v = *p; return cx<R>((R)v.x, (R)v.y); }
+template <typename R> HD cx<R> ldr(const float2* p) { float2 v = *p; return cx<R>((R)v.x, (R)v.y); }
+template <typename R> HD cx<R> ldr(const cx<R>* p) { return *p; }
+HD zd wide(const zd& z) { return z; }
+HD zd wide(const zf& z) { return zd((double)z.re, (double)z.im); }
 
 HD zd cdiv(const zd& a, const zd& b) {
   double d = b.re * b.re + b.im * b.im;

@@ -46,6 +46,30 @@ __device__ __forceinline__ double rule_w(const DevW& w, int n, int l) {
   return 1.0;
 }
 
+// The same rule in the arithmetic R of the bulk sums (float tables for float).
+template <typename R>
+__device__ __forceinline__ R rule_wr(const DevW& w, int n, int l) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return rule_w(w, n, l);
+  } else {
+    const int k = w.k;
+    if (n <= 0) return 0.0f;
+    if (n <= k) return (l >= 0 && l <= k) ? w.I0f[n][l] : 0.0f;
+    if (n < 2 * k + 1) {
+      float s = 0.0f;
+      if (l >= 0 && l <= k) s += w.I0f[n - k][l];
+      if (l >= n - k && l <= n) s += w.I0f[k][l - (n - k)];
+      return s;
+    }
+    if (l < 0 || l > n) return 0.0f;
+    if (l <= k) return w.omegaf[l];
+    if (l >= n - k) return w.omegaf[n - l];
+    return 1.0f;
+  }
+}
+
+constexpr int FOLD = 8;  // terms summed in R before folding into an FP64 accumulator
+
 __device__ __forceinline__ zd wshfl(zd v, int off) {
   return zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));
 }

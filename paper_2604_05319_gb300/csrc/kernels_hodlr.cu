@@ -43,6 +43,7 @@ __device__ __forceinline__ double2* Psrc(const Dev& d, int n, int b, int p, int 
 template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
   const int b = blockIdx.x, n = blockIdx.y;
   if (!d.active[n]) return;
   const int c = d.cdir;
@@ -60,14 +61,23 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
     const S* F = which == 0 ? Up<NO, S>(d, 3, n, b, p) : Vp<NO, S>(d, 3, n, b, p);
     const int lo = which == 0 ? r0 : c0, hi = which == 0 ? rl : c1;
     zd part[4] = {zd(), zd(), zd(), zd()};
-    for (int l = lo + warp; l < hi; l += 8) {
-      const zd g = ld(el<NO, S>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_w(W, T, l);
-      const S* fr = F + (long long)(l - lo) * d.rmax;
+    for (int l0 = lo + warp; l0 < hi; l0 += 8 * FOLD) {
+      cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = lane + 32 * u;
-        if (q < rk) part[u] = cfma(g, ld(fr + q), part[u]);
+      for (int jj = 0; jj < FOLD; ++jj) {
+        const int l = l0 + 8 * jj;
+        if (l < hi) {
+          const cx<R> g = ldr<R>(el<NO, S>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_wr<R>(W, T, l);
+          const S* fr = F + (long long)(l - lo) * d.rmax;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = lane + 32 * u;
+            if (q < rk) pp[u] = cfma(g, ldr<R>(fr + q), pp[u]);
+          }
+        }
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
@@ -84,6 +94,7 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
 template <int NO, typename S>
 __global__ void k_src_h(Dev d, int T) {
   constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int n = gw / (T + 1), t = gw % (T + 1);
@@ -95,21 +106,32 @@ __global__ void k_src_h(Dev d, int T) {
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
   const int jt = t / L, A = jt * L, E = min(A + L, d.nt);
+  // pa[x][y] += wl sum_z Sx[x][z] conj(G^R(T,l)[y][z]), Sx = S or S^dagger (in R)
+  auto sg = [&](cx<R>* pa, const S* sp, bool dagS, const S* gp, R wl) {
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int z = 0; z < NO; ++z) {
+        const cx<R> sxz = (dagS ? ldr<R>(sp + z * NO + x).conj() : ldr<R>(sp + x * NO + z)) * wl;
+#pragma unroll
+        for (int y = 0; y < NO; ++y) pa[x * NO + y] = cfma(sxz, ldr<R>(gp + y * NO + z).conj(), pa[x * NO + y]);
+      }
+  };
+  auto fold = [&](cx<R>* pa) {
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) { acc[q] += wide(pa[q]); pa[q] = cx<R>(0); }
+  };
+  cx<R> pa[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) pa[q] = cx<R>(0);
   // part 1, l >= t: S[l][t]
-  for (int l = max(t, c) + lane; l <= T; l += 32) {  // uncompressed rows
-    const double wl = rule_w(W, T, l);
-    M<NO> Sm = load<NO>(el<NO, S>(d.SL, d, n, l, t));
-    M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
-    mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(wl));
-  }
+  for (int l = max(t, c) + lane; l <= T; l += 32)  // uncompressed rows (at most a leaf and k+8)
+    sg(pa, el<NO, S>(d.SL, d, n, l, t), false, el<NO, S>(d.GR, d, n, T, l), rule_wr<R>(W, T, l));
   if (t < c) {
-    for (int l = t + lane; l < min(E, c); l += 32) {  // same leaf
-      const double wl = rule_w(W, T, l);
-      M<NO> Sm = load<NO>(Lf<NO, S>(d, 3, n, jt, l, t));
-      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(wl));
-    }
+    for (int l = t + lane; l < min(E, c); l += 32)  // same leaf
+      sg(pa, Lf<NO, S>(d, 3, n, jt, l, t), false, el<NO, S>(d.GR, d, n, T, l), rule_wr<R>(W, T, l));
   }
+  fold(pa);
   for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their columns
     const int b = d.colblk[jt * d.maxl + lv];
     if (b < 0 || d.b_r0[b] >= c) continue;
@@ -122,25 +144,26 @@ __global__ void k_src_h(Dev d, int T) {
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
         const double2* P = Psrc<NO>(d, n, b, p, y, 0);
-        for (int q = lane; q < rk; q += 32) acc[x * NO + y] = cfma(ld(P + q), ld(V + q).conj(), acc[x * NO + y]);
+        cx<R> sb = cx<R>(0);
+        for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), sb);
+        acc[x * NO + y] += wide(sb);
       }
     }
   }
   // part 2, l < t: -S[t][l]^dagger
   if (t >= c) {
-    for (int l = lane; l < t; l += 32) {
-      const double wl = rule_w(W, T, l);
-      M<NO> Sm = dag<NO>(load<NO>(el<NO, S>(d.SL, d, n, t, l)));
-      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(-wl));
+    for (int l0 = lane; l0 < t; l0 += 32 * FOLD) {  // the whole (uncompressed) row t
+#pragma unroll
+      for (int jj = 0; jj < FOLD; ++jj) {
+        const int l = l0 + 32 * jj;
+        if (l < t) sg(pa, el<NO, S>(d.SL, d, n, t, l), true, el<NO, S>(d.GR, d, n, T, l), -rule_wr<R>(W, T, l));
+      }
+      fold(pa);
     }
   } else {
-    for (int l = A + lane; l < t; l += 32) {
-      const double wl = rule_w(W, T, l);
-      M<NO> Sm = dag<NO>(load<NO>(Lf<NO, S>(d, 3, n, jt, t, l)));
-      M<NO> GA = dag<NO>(load<NO>(el<NO, S>(d.GR, d, n, T, l)));
-      mac<NO>(*reinterpret_cast<M<NO>*>(acc), Sm, GA, zd(-wl));
-    }
+    for (int l = A + lane; l < t; l += 32)
+      sg(pa, Lf<NO, S>(d, 3, n, jt, t, l), true, el<NO, S>(d.GR, d, n, T, l), -rule_wr<R>(W, T, l));
+    fold(pa);
     for (int lv = 0; lv < d.maxl; ++lv) {  // blocks with t in their rows
       const int b = d.rowblk[jt * d.maxl + lv];
       if (b < 0) continue;
@@ -153,9 +176,9 @@ __global__ void k_src_h(Dev d, int T) {
 #pragma unroll
         for (int y = 0; y < NO; ++y) {
           const double2* P = Psrc<NO>(d, n, b, p, y, 1);
-          zd s = zd();
-          for (int q = lane; q < rk; q += 32) s = cfma(ld(U + q).conj(), ld(P + q), s);
-          acc[x * NO + y] -= s;
+          cx<R> sb = cx<R>(0);
+          for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(U + q).conj(), ldr<R>(P + q), sb);
+          acc[x * NO + y] -= wide(sb);
         }
       }
     }
@@ -266,6 +289,14 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   for (int w2 = 0; w2 < nw; ++w2) emax = fmax(emax, s_wpart[w2]);
   emax = sqrt(emax);
   __syncthreads();
+  // Truncation threshold: eps_SVD, raised in the complex64 storage form to
+  // the rounding floor of the appended rows.  Their rounding is a matrix of
+  // independent entries below 2^-24 max|E|, whose largest singular value
+  // stays below 2^-24 max|E| (sqrt(nb) + sqrt(ncol)); directions under that
+  // level are storage noise, and keeping them would let the rank grow by the
+  // leaf size at every append.
+  double tol = d.svd_tol;
+  if (sizeof(S) == sizeof(float2)) tol = fmax(tol, kF32Unit * emax * (sqrt((double)nb) + sqrt((double)ncol)));
   // P = E V, E -= P V^dagger, twice (the second pass restores orthogonality
   // to V lost to rounding).  The per-pass coefficients are staged in Q's
   // storage (r <= ncol), which is free until the Gram-Schmidt below.
@@ -291,7 +322,8 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   for (long long e = tid; e < (long long)d.L * d.L; e += blockDim.x) Cm[e] = make_double2(0, 0);
   __syncthreads();
   // Two-pass Gram-Schmidt on the rows of E: E = C Q, rows of Q orthonormal.
-  const double delta = 0.25 * d.svd_tol;
+  // residual rows below a quarter of the threshold add no basis direction
+  const double delta = 0.25 * tol;
   __shared__ zd s_coef[64];
 
   // ke, the number of accepted basis rows, is kept in a register: every thread
@@ -424,14 +456,6 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
         if (s_sig[s_ord[q]] > s_sig[s_ord[best]]) best = q;
       int t2 = s_ord[i]; s_ord[i] = s_ord[best]; s_ord[best] = t2;
     }
-    // Truncation threshold: eps_SVD, raised in the complex64 storage form to
-    // the rounding floor of the appended rows.  Their rounding is a matrix of
-    // independent entries below 2^-24 max|E|, whose largest singular value
-    // stays below 2^-24 max|E| (sqrt(nb) + sqrt(ncol)); directions under that
-    // level are storage noise, and keeping them would let the rank grow by the
-    // leaf size at every append.
-    double tol = d.svd_tol;
-    if (sizeof(S) == sizeof(float2)) tol = fmax(tol, kF32Unit * emax * (sqrt((double)nb) + sqrt((double)ncol)));
     int rn = 0;
     while (rn < nk && s_sig[s_ord[rn]] > tol) ++rn;
     if (rn > rmax) { atomicAdd(d.status, 1); rn = rmax; }

@@ -26,6 +26,8 @@ namespace {
 
 constexpr int CK = 32;   // chunk length
 using Y = double2;       // element type of the row / column being solved
+template <int NO> constexpr bool kStage = NO <= 2;   // hot-chunk coefficients staged in shared memory
+template <int NO> constexpr size_t kStageBytes = kStage<NO> ? sizeof(zd) * CK * CK * NO * NO : 0;
 
 // Where a sweep keeps the row it solves: in place (FP64 storage) or in the
 // FP64 buffer row64[n][which] (complex64 storage).
@@ -61,6 +63,7 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
 template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
   const int n = blockIdx.y, irow = blockIdx.x;
   if (!d.active[n]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -73,6 +76,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
+  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2)
   if (tid == 0) serr = 0.0;
   // The row being solved lives in FP64 during the sweep (in the complex64
   // storage form a separate buffer, copied out rounded at the end), so the
@@ -134,14 +138,23 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
           const int rk = *Rk<NO>(d, 2, n, blk, p);
           const S* U = Up<NO, S>(d, 2, n, blk, p);
           zd part[4] = {zd(), zd(), zd(), zd()};
-          for (int s2 = r0 + warp; s2 < rl; s2 += 8) {  // warps over rows, lanes over rank
-            const zd yv = ld(yp(s2) + m);
-            const S* ur = U + (long long)(s2 - r0) * d.rmax;
+          for (int s0 = r0 + warp; s0 < rl; s0 += 8 * FOLD) {  // warps over rows, lanes over rank
+            cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = lane + 32 * u;
-              if (q < rk) part[u] = cfma(yv, ld(ur + q), part[u]);
+            for (int jj = 0; jj < FOLD; ++jj) {
+              const int s2 = s0 + 8 * jj;
+              if (s2 < rl) {
+                const cx<R> yv = ldr<R>(yp(s2) + m);
+                const S* ur = U + (long long)(s2 - r0) * d.rmax;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int q = lane + 32 * u;
+                  if (q < rk) pp[u] = cfma(yv, ldr<R>(ur + q), pp[u]);
+                }
+              }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
@@ -165,16 +178,27 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         for (int j = 0; j < NO; ++j) acc[j] = zd();
         const int tp = A + col;
         if (col < L) {
-          for (int s2 = c + sl; s2 <= T; s2 += 4) {
-            const double ws = rule_w(W, T - tp, T - s2);
-            const Y* yl = yp(s2);
-            const S* sr = el<NO, S>(d.SR, d, n, s2, tp);
+          for (int s0 = c + sl; s0 <= T; s0 += 4 * FOLD) {
+            cx<R> pa[NO];
 #pragma unroll
-            for (int m = 0; m < NO; ++m) {
-              const zd ym = ld(yl + m) * ws;
+            for (int j = 0; j < NO; ++j) pa[j] = cx<R>(0);
 #pragma unroll
-              for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+            for (int jj = 0; jj < FOLD; ++jj) {
+              const int s2 = s0 + 4 * jj;
+              if (s2 <= T) {
+                const R ws = rule_wr<R>(W, T - tp, T - s2);
+                const Y* yl = yp(s2);
+                const S* sr = el<NO, S>(d.SR, d, n, s2, tp);
+#pragma unroll
+                for (int m = 0; m < NO; ++m) {
+                  const cx<R> ym = ldr<R>(yl + m) * ws;
+#pragma unroll
+                  for (int j = 0; j < NO; ++j) pa[j] = cfma(ym, ldr<R>(sr + m * NO + j), pa[j]);
+                }
+              }
             }
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[j] += wide(pa[j]);
           }
           for (int lv = 0; lv < d.maxl; ++lv) {
             const int blk = d.colblk[jl * d.maxl + lv];
@@ -186,7 +210,9 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
               const int rk = *Rk<NO>(d, 2, n, blk, p);
               const S* V = Vp<NO, S>(d, 2, n, blk, p) + (long long)(tp - c0) * d.rmax;
               const double2* P = Pj<NO>(d, n, irow, lv, p);
-              for (int q = sl; q < rk; q += 4) acc[j] = cfma(ld(P + q), ld(V + q).conj(), acc[j]);
+              cx<R> pb = cx<R>(0);
+              for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), pb);
+              acc[j] += wide(pb);
             }
           }
           for (int s2 = E + sl; s2 <= tp + k && s2 < c; s2 += 4) {
@@ -221,16 +247,27 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
       for (int j = 0; j < NO; ++j) acc[j] = zd();
       if (col < cn) {
         const int s_end = comp ? E : T + 1;   // compressed: the rest of the leaf; else every later row
-        for (int s2 = b + sl; s2 < s_end; s2 += 8) {
-          const double ws = rule_w(W, T - tp, T - s2);
-          const Y* yl = yp(s2);
-          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, s2, tp) : el<NO, S>(d.SR, d, n, s2, tp);
+        for (int s0 = b + sl; s0 < s_end; s0 += 8 * FOLD) {
+          cx<R> pa[NO];
 #pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ld(yl + m) * ws;
+          for (int j = 0; j < NO; ++j) pa[j] = cx<R>(0);
 #pragma unroll
-            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
+          for (int jj = 0; jj < FOLD; ++jj) {
+            const int s2 = s0 + 8 * jj;
+            if (s2 < s_end) {
+              const R ws = rule_wr<R>(W, T - tp, T - s2);
+              const Y* yl = yp(s2);
+              const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, s2, tp) : el<NO, S>(d.SR, d, n, s2, tp);
+#pragma unroll
+              for (int m = 0; m < NO; ++m) {
+                const cx<R> ym = ldr<R>(yl + m) * ws;
+#pragma unroll
+                for (int j = 0; j < NO; ++j) pa[j] = cfma(ym, ldr<R>(sr + m * NO + j), pa[j]);
+              }
+            }
           }
+#pragma unroll
+          for (int j = 0; j < NO; ++j) acc[j] += wide(pa[j]);
         }
       }
 #pragma unroll
@@ -273,10 +310,31 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
           st(yp(a + ti) + j, sacc);
         }
       }
-    } else if (warp == 0) {
+    } else {
       // chunk near T: right-looking triangular solve in one warp.  Lane L owns
       // t'' = a + L; after point s is solved every lane with t'' < s removes
-      // y(s) C(s, t'') from its right-hand side.
+      // y(s) C(s, t'') from its right-hand side.  The coefficients C(s, t'')
+      // are first staged in shared memory by the whole block (N_o <= 2), so
+      // the 32 dependent steps of the solve wait on no global load.
+      auto coef = [&](int i, int L0, zd* cf) {
+        const int spt = a + i, tq = a + L0;
+        const double wl = -h * rule_w(W, T - tq, T - spt);
+        const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, spt, tq) : el<NO, S>(d.SR, d, n, spt, tq);
+        const int dd = spt - tq;
+#pragma unroll
+        for (int q = 0; q < NO2; ++q) {
+          cf[q] = ld(sr + q) * wl;
+          if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+        }
+      };
+      if constexpr (kStage<NO>) {
+        for (int e = tid; e < CK * CK; e += blockDim.x) {
+          const int i = e / CK, L0 = e % CK;
+          if (L0 < i && i < cn) coef(i, L0, ctile + (long long)e * NO2);
+        }
+        __syncthreads();
+      }
+      if (warp == 0) {
       const int L0 = lane, tq = a + L0;
       M<NO> Dinv;
       zd f[NO];
@@ -299,13 +357,11 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         // coefficient C(spt, tq) for this lane (only lanes with tq < spt use it)
         zd cf[NO2];
         if (L0 < i) {
-          const double wl = -h * rule_w(W, T - tq, T - spt);
-          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, spt, tq) : el<NO, S>(d.SR, d, n, spt, tq);
-          const int dd = spt - tq;
+          if constexpr (kStage<NO>) {
 #pragma unroll
-          for (int q = 0; q < NO2; ++q) {
-            cf[q] = ld(sr + q) * wl;
-            if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+            for (int q = 0; q < NO2; ++q) cf[q] = ctile[(long long)(i * CK + L0) * NO2 + q];
+          } else {
+            coef(i, L0, cf);
           }
         }
         zd y[NO];
@@ -331,6 +387,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
             for (int j = 0; j < NO; ++j) f[j] -= y[m] * cf[m * NO + j];
         }
       }
+      }
     }
     __syncthreads();
   }
@@ -348,6 +405,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
 template <int NO, typename S>
 __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
   constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
   const int n = blockIdx.y, jc = blockIdx.x;
   if (!d.active[n]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -360,6 +418,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
+  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2)
   if (tid == 0) serr = 0.0;
   // FP64 column during the sweep (see k_ret2); xp: as solved, sp: storage
   S* colp = el<NO, S>(d.GL, d, n, T, 0);
@@ -393,15 +452,24 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           const int rk = *Rk<NO>(d, 2, n, blk, p);
           const S* V = Vp<NO, S>(d, 2, n, blk, p);
           zd part[4] = {zd(), zd(), zd(), zd()};
-          for (int l = c0 + warp; l < c1; l += 8) {  // warps over columns, lanes over rank
-            const double wl = (l <= k) ? W.omega[l] : 1.0;
-            const zd xv = ld(xp(l) + nn * NO + jc) * wl;
-            const S* vr = V + (long long)(l - c0) * d.rmax;
+          for (int l0 = c0 + warp; l0 < c1; l0 += 8 * FOLD) {  // warps over columns, lanes over rank
+            cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = lane + 32 * u;
-              if (q < rk) part[u] = cfma(ld(vr + q).conj(), xv, part[u]);
+            for (int jj = 0; jj < FOLD; ++jj) {
+              const int l = l0 + 8 * jj;
+              if (l < c1) {
+                const R wl = (l <= k) ? (R)W.omega[l] : (R)1;
+                const cx<R> xv = ldr<R>(xp(l) + nn * NO + jc) * wl;
+                const S* vr = V + (long long)(l - c0) * d.rmax;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int q = lane + 32 * u;
+                  if (q < rk) pp[u] = cfma(ldr<R>(vr + q).conj(), xv, pp[u]);
+                }
+              }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
@@ -433,7 +501,9 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
               const int rk = *Rk<NO>(d, 2, n, blk, p);
               const S* U = Up<NO, S>(d, 2, n, blk, p) + (long long)(t - r0) * d.rmax;
               const double2* P = Pj<NO>(d, n, jc, lv, p);
-              for (int q = sl; q < rk; q += 4) acc[m] = cfma(ld(U + q), ld(P + q), acc[m]);
+              cx<R> pb = cx<R>(0);
+              for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(U + q), ldr<R>(P + q), pb);
+              acc[m] += wide(pb);
             }
           }
           for (int l = max(t - k, 0) + sl; l < A; l += 4) {
@@ -481,15 +551,27 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         } else {
           const int l0 = comp ? A : 0;
           const S* srow = comp ? nullptr : el<NO, S>(d.SR, d, n, t, 0);
-          for (int l = l0 + sl; l < a; l += 8) {
-            const double wl = h * rule_w(W, t, l);
-            const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
+          const R hr = (R)h;
+          for (int lb = l0 + sl; lb < a; lb += 8 * FOLD) {
+            cx<R> pa[NO];
 #pragma unroll
-            for (int y = 0; y < NO; ++y) {
-              const zd xy = ld(xp(l) + y * NO + jc) * wl;
+            for (int m = 0; m < NO; ++m) pa[m] = cx<R>(0);
 #pragma unroll
-              for (int m = 0; m < NO; ++m) acc[m] = cfma(ld(sr + m * NO + y), xy, acc[m]);
+            for (int jj = 0; jj < FOLD; ++jj) {
+              const int l = lb + 8 * jj;
+              if (l < a) {
+                const R wl = hr * rule_wr<R>(W, t, l);
+                const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
+#pragma unroll
+                for (int y = 0; y < NO; ++y) {
+                  const cx<R> xy = ldr<R>(xp(l) + y * NO + jc) * wl;
+#pragma unroll
+                  for (int m = 0; m < NO; ++m) pa[m] = cfma(ldr<R>(sr + m * NO + y), xy, pa[m]);
+                }
+              }
             }
+#pragma unroll
+            for (int m = 0; m < NO; ++m) acc[m] += wide(pa[m]);
           }
           if (sl == 1) {  // BDF terms reaching left of the chunk
             for (int jj = 1; jj <= k; ++jj) {
@@ -531,9 +613,30 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           st(xp(a + ti) + m * NO + jc, sacc);
         }
       }
-    } else if (warp == 0) {
+    } else {
       // chunk near T: right-looking triangular solve in one warp; lane L owns
-      // row t'' = a + L.  Chunk 0 first solves its start block t = 1..k.
+      // row t'' = a + L.  Chunk 0 first solves its start block t = 1..k.  The
+      // coefficients C(t'', tp) are staged in shared memory first (N_o <= 2).
+      auto coef = [&](int L0, int i, zd* cf) {
+        const int tq = a + L0, tp = a + i;
+        const double wl = -h * rule_w(W, tq, tp);
+        const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, tq, tp) : el<NO, S>(d.SR, d, n, tq, tp);
+        const int dd = tq - tp;
+#pragma unroll
+        for (int q = 0; q < NO2; ++q) {
+          cf[q] = ld(sr + q) * wl;
+          if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+        }
+      };
+      if constexpr (kStage<NO>) {
+        const int i0s = (cc == 0) ? k : 0;
+        for (int e = tid; e < CK * CK; e += blockDim.x) {
+          const int L0 = e / CK, i = e % CK;
+          if (i >= i0s && i < L0 && L0 < cn) coef(L0, i, ctile + (long long)e * NO2);
+        }
+        __syncthreads();
+      }
+      if (warp == 0) {
       const int L0 = lane, tq = a + L0;
       int i0 = 0;
       zd f[NO];
@@ -595,13 +698,11 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         const int tp = a + i;
         zd cf[NO2];
         if (L0 > i && L0 < cn) {
-          const double wl = -h * rule_w(W, tq, tp);
-          const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, tq, tp) : el<NO, S>(d.SR, d, n, tq, tp);
-          const int dd = tq - tp;
+          if constexpr (kStage<NO>) {
 #pragma unroll
-          for (int q = 0; q < NO2; ++q) {
-            cf[q] = ld(sr + q) * wl;
-            if (dd <= k && (q / NO) == (q % NO)) cf[q] += zd(0, W.a[dd] / h);
+            for (int q = 0; q < NO2; ++q) cf[q] = ctile[(long long)(L0 * CK + i) * NO2 + q];
+          } else {
+            coef(L0, i, cf);
           }
         }
         zd x[NO];
@@ -626,6 +727,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
 #pragma unroll
             for (int y = 0; y < NO; ++y) f[m] -= cf[m * NO + y] * x[y];
         }
+      }
       }
     }
     __syncthreads();
@@ -758,15 +860,33 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
     default: return cudaErrorInvalidValue;                                      \
   }
 
-cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
-  dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_ret2<NO, S><<<g, 256, 0, s>>>(d, T)));
+// Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
+template <typename K>
+static cudaError_t allow_smem(K kern, size_t bytes) {
+  if (bytes + 16 * 1024 <= 48 * 1024) return cudaSuccess;  // with the static arrays, under the default
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+template <int NO, typename S>
+static cudaError_t sweep_ret(const Dev& d, int T, cudaStream_t s) {
+  cudaError_t e = allow_smem(k_ret2<NO, S>, kStageBytes<NO>);
+  if (e != cudaSuccess) return e;
+  k_ret2<NO, S><<<dim3(d.no, d.n_inst), 256, kStageBytes<NO>, s>>>(d, T);
   return cudaGetLastError();
 }
-cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
-  dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_les2<NO, S><<<g, 256, 0, s>>>(d, T)));
+template <int NO, typename S>
+static cudaError_t sweep_les(const Dev& d, int T, cudaStream_t s) {
+  cudaError_t e = allow_smem(k_les2<NO, S>, kStageBytes<NO>);
+  if (e != cudaSuccess) return e;
+  k_les2<NO, S><<<dim3(d.no, d.n_inst), 256, kStageBytes<NO>, s>>>(d, T);
   return cudaGetLastError();
+}
+cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {
+  HK_DISPATCH(d.no, return (sweep_ret<NO, S>(d, T, s)));
+  return cudaSuccess;
+}
+cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s) {
+  HK_DISPATCH(d.no, return (sweep_les<NO, S>(d, T, s)));
+  return cudaSuccess;
 }
 cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s) {
   for (int cc = c0; cc < c1; ++cc) {

@@ -10,6 +10,7 @@ namespace hk {
 struct DevW {
   int k;
   double a[6], omega[6], D[6][6], I0[6][6];
+  float omegaf[6], I0f[6][6];   // float copies for the bulk sums of the complex64 form
 };
 
 constexpr int MP = 64;  // doubles of model parameters per instance
