@@ -117,6 +117,13 @@ int hkbe_set_matsubara(hkbe_t* h, const double* gm);
  * 0 holding the equilibrium branch eps(0_|). */
 int hkbe_set_hamiltonian(hkbe_t* h, const double* eps);
 
+/* The same for one time t only: eps_t[n_inst][N_o][N_o] complex replaces
+ * eps(t) of every instance (the per-step update of a time-dependent mean
+ * field or drive, Sec. 3.4).  Only times not yet computed may change:
+ * HKBE_ERR_RANGE unless current step < t <= nt-1; HKBE_ERR_ARG before
+ * hkbe_set_hamiltonian; HKBE_ERR_NAN for non-finite input.  Synchronous. */
+int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
+
 /* Self-energy functional and its parameters, params[n_inst][nparams]:
  *   HKBE_MODEL_NONE : nparams 0.
  *   HKBE_MODEL_BETHE: nparams >= 1, params[0] = v (Sigma = v^2 G).
@@ -160,6 +167,11 @@ int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl);
 /* Density matrix rho(t) = xi i G^<(t,t) (Sec. 3.3) for t = 0..T of every
  * instance: rho[n_inst][T+1][N_o][N_o] complex. */
 int hkbe_get_density(hkbe_t* h, double* rho);
+
+/* rho(t) of every instance at one time t <= current step:
+ * rho_t[n_inst][N_o][N_o] complex, gathered on the device and copied once.
+ * HKBE_ERR_RANGE outside 0..current step.  Synchronous. */
+int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t);
 
 /* Device bytes held by the handle. */
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);

@@ -66,6 +66,8 @@ def load(build_if_missing: bool = True):
         "hkbe_set_dlr": ([H, C.c_int, _D, _D], C.c_int),
         "hkbe_set_matsubara": ([H, _D], C.c_int),
         "hkbe_set_hamiltonian": ([H, _D], C.c_int),
+        "hkbe_set_hamiltonian_at": ([H, C.c_int, C.c_void_p], C.c_int),
+        "hkbe_get_density_at": ([H, C.c_int, C.c_void_p], C.c_int),
         "hkbe_set_model": ([H, C.c_int, _D, C.c_int], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
@@ -200,6 +202,30 @@ def hkbe_get_row(h, nao, inst, T):
     gl = np.zeros((T + 1, nao, nao), np.complex128)
     _check(load().hkbe_get_row(h, inst, T, _dp(gr.view(np.float64)), _dp(gl.view(np.float64))), h)
     return gr, gl
+
+
+def _ptr(a):
+    """Address of a host buffer: a numpy array (kept alive by the caller) or an int."""
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    return C.c_void_p(a.ctypes.data)
+
+
+def hkbe_set_hamiltonian_at(h, t, eps_t):
+    """eps(t) of every instance: complex [n_inst, nao, nao] array, or the
+    address of such a buffer of interleaved doubles (e.g. pinned memory)."""
+    if not isinstance(eps_t, int):
+        eps_t = _cplx(eps_t, np.shape(eps_t))
+    _check(load().hkbe_set_hamiltonian_at(h, int(t), _ptr(eps_t)), h)
+
+
+def hkbe_get_density_at(h, t, out):
+    """rho(t) of every instance into `out` (complex [n_inst, nao, nao] numpy
+    array, C-contiguous, or the address of such a buffer); returns out."""
+    if not isinstance(out, int) and not (out.dtype == np.complex128 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous complex128 array")
+    _check(load().hkbe_get_density_at(h, int(t), _ptr(out)), h)
+    return out
 
 
 def hkbe_get_density(h, n_inst, nao, T):

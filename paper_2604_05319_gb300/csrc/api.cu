@@ -41,9 +41,10 @@ struct hkbe_s {
   // HODLR geometry (host copies) and row read-out buffers
   bool hodlr = false;
   std::vector<int> g_r0, g_r1, g_c0, g_c1, g_lvl, g_rowblk, g_colblk;
-  std::vector<long long> g_uoff, g_voff, g_leafoff;
+  std::vector<long long> g_uoff, g_voff, g_leafoff, g_wslv;
   double2 *rowbuf_r = nullptr, *rowbuf_l = nullptr;
   int* status_dev = nullptr;
+  double2* diagbuf = nullptr;  // [n_inst][no2] density matrices of one time
   // device arrays that make up the propagation state, zeroed by hkbe_rewind so
   // that a rewound run starts from exactly the state that followed bootstrap
   std::vector<std::pair<void*, size_t>> state_arrays;
@@ -283,11 +284,18 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
     d.svd_tol = p->svd_tol;
     tri = (size_t)d.n_inst * d.ring * d.nt * d.no * d.no;
     const size_t n2 = (size_t)d.no * d.no, N = d.n_inst;
-    int ncolmax = 1;
-    for (size_t b = 0; b < h->g_c0.size(); ++b) ncolmax = std::max(ncolmax, h->g_c1[b] - h->g_c0[b]);
+    // TSVD workspace: one slot per (instance, component, orbital pair, level),
+    // each sized for the widest block of its level
     const int ldk = d.rmax + d.L;
-    d.tsvd_ws_per = 2LL * d.L * ncolmax + (long long)d.L * d.rmax + (long long)d.L * d.L + 2LL * ldk * ldk;
-    const size_t ctas = N * 4 * d.maxl * n2;
+    h->g_wslv.assign(d.maxl + 1, 0);
+    for (int lv = 0; lv < d.maxl; ++lv) {
+      int ncl = 1;
+      for (size_t b = 0; b < h->g_c0.size(); ++b)
+        if (h->g_lvl[b] == lv) ncl = std::max(ncl, h->g_c1[b] - h->g_c0[b]);
+      h->g_wslv[lv + 1] = h->g_wslv[lv] + 2LL * d.L * ncl + (long long)d.L * d.rmax + (long long)d.L * d.L + 2LL * ldk * ldk;
+    }
+    d.tsvd_ws_per = h->g_wslv[d.maxl];
+    const size_t ctas = N * 4 * n2;
     for (int X = 0; X < 4; ++X) {
       if ((rc = dalloc_el(h, &d.hod[X].U, N * d.utot * d.rmax)) || (rc = dalloc_el(h, &d.hod[X].V, N * d.vtot * d.rmax)) ||
           (rc = dalloc(h, &d.hod[X].S, N * d.nblk * n2 * d.rmax)) ||
@@ -306,7 +314,8 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
         (rc = upload(h, &d.b_c0, h->g_c0)) || (rc = upload(h, &d.b_c1, h->g_c1)) ||
         (rc = upload(h, &d.b_lvl, h->g_lvl)) || (rc = upload(h, &d.b_uoff, h->g_uoff)) ||
         (rc = upload(h, &d.b_voff, h->g_voff)) || (rc = upload(h, &d.leafoff, h->g_leafoff)) ||
-        (rc = upload(h, &d.rowblk, h->g_rowblk)) || (rc = upload(h, &d.colblk, h->g_colblk))) {
+        (rc = upload(h, &d.rowblk, h->g_rowblk)) || (rc = upload(h, &d.colblk, h->g_colblk)) ||
+        (rc = upload(h, &d.ws_lvoff, h->g_wslv))) {
       g_create_error = h->err;
       hkbe_destroy(h);
       return rc;
@@ -340,7 +349,8 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
       (rc = dalloc(h, &d.mpar, (size_t)d.n_inst * hk::MP)) ||
       (rc = dalloc(h, &d.qsrc, (size_t)d.n_inst * d.nt * d.no * d.no)) ||
       (rc = dalloc(h, &d.x0, (size_t)d.n_inst * d.no * d.no)) || (rc = dalloc(h, &d.err, (size_t)d.n_inst)) ||
-      (rc = dalloc(h, &d.active, (size_t)d.n_inst)) || (rc = dalloc(h, &h->any_dev, 1))) {
+      (rc = dalloc(h, &d.active, (size_t)d.n_inst)) || (rc = dalloc(h, &h->any_dev, 1)) ||
+      (rc = dalloc(h, &h->diagbuf, (size_t)d.n_inst * d.no * d.no))) {
     g_create_error = h->err;
     hkbe_destroy(h);
     return rc;
@@ -433,6 +443,25 @@ int hkbe_set_hamiltonian(hkbe_t* h, const double* eps) {
   HK_CUDA(h, cudaMemcpyAsync(d.eps, eps, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->have_eps = true;
+  return HKBE_OK;
+}
+
+int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t) {
+  if (!h || !eps_t) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (!h->have_eps) return fail(h, HKBE_ERR_ARG, "hkbe_set_hamiltonian must precede hkbe_set_hamiltonian_at");
+  Dev& d = h->d;
+  if (t <= h->cur || t > d.nt - 1) return fail(h, HKBE_ERR_RANGE, "t must satisfy current step < t <= nt-1");
+  const int n2 = no2(h);
+  for (int i = 0; i < d.n_inst * n2 * 2; ++i)
+    if (!std::isfinite(eps_t[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in eps_t");
+  // eps is [n][nt+1][no2], index t+1: one strided copy of n_inst pieces
+  HK_CUDA(h, cudaMemcpy2DAsync(d.eps + (size_t)(t + 1) * n2, (size_t)(d.nt + 1) * n2 * sizeof(double2), eps_t,
+                               (size_t)n2 * sizeof(double2), (size_t)n2 * sizeof(double2), d.n_inst,
+                               cudaMemcpyHostToDevice, h->s));
+  for (int n = 0; n < d.n_inst; ++n)
+    std::memcpy(&h->eps_host[(((size_t)n * (d.nt + 1)) + t + 1) * n2 * 2], eps_t + (size_t)n * n2 * 2,
+                n2 * 2 * sizeof(double));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
 }
 
@@ -848,6 +877,17 @@ int hkbe_get_density(hkbe_t* h, double* rho) {
         o[2 * q + 1] = h->p.xi * re;
       }
     }
+  return HKBE_OK;
+}
+
+int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t) {
+  if (!h || !rho_t) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
+  const hk::Dev& d = h->d;
+  const size_t cnt = (size_t)d.n_inst * no2(h);
+  HK_CUDA(h, hk::launch_density_at(d, t, h->diagbuf, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(rho_t, h->diagbuf, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
 }
 

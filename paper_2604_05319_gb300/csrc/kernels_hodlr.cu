@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   const int ncol = d.b_c1[b] - c0;
   const int rmax = d.rmax;
   const int ld_k = rmax + d.L;  // leading dimension of K and Vh
-  double2* ws = d.tsvd_ws + ((long long)n * gridDim.x + blockIdx.x) * d.tsvd_ws_per;
+  double2* ws = d.tsvd_ws + (((long long)n * 4 + X) * NO2 + p) * d.tsvd_ws_per + d.ws_lvoff[lv];
   double2* Em = ws;                                   // [nb][ncol]
   double2* Qm = Em + (long long)d.L * ncol;           // [nb][ncol]
   double2* Pm = Qm + (long long)d.L * ncol;           // [nb][rmax]
@@ -553,6 +553,17 @@ __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
   }
 }
 
+// rho(t) = xi i G^<(t, t) of every instance, from a row (dense or ring) or a leaf.
+template <int NO, typename S>
+__global__ void k_density_at(Dev d, int t, double2* out) {
+  constexpr int NO2 = NO * NO;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_inst * NO2) return;
+  const int n = e / NO2, q = e % NO2;
+  const S* p = (!d.ring || t >= d.cdir) ? el<NO, S>(d.GL, d, n, t, t) : Lf<NO, S>(d, 1, n, t / d.L, t, t);
+  st(out + e, ld(p + q) * zd(0, (double)d.xi));
+}
+
 #define HK_DISPATCH(NOV, CALL)                                                  \
   switch ((NOV) * 2 + d.prec) {                                                 \
     case 2: { constexpr int NO = 1; using S = double2; CALL; break; }           \
@@ -582,6 +593,10 @@ cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s) {
   }
   dim3 g(4 * d.maxl * d.no * d.no, d.n_inst);
   HK_DISPATCH(d.no, (k_tsvd<NO, S><<<g, 256, 0, s>>>(d, A, nb)));
+  return cudaGetLastError();
+}
+cudaError_t launch_density_at(const Dev& d, int t, double2* out, cudaStream_t s) {
+  HK_DISPATCH(d.no, (k_density_at<NO, S><<<(d.n_inst * d.no * d.no + 127) / 128, 128, 0, s>>>(d, t, out)));
   return cudaGetLastError();
 }
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s) {

@@ -44,8 +44,9 @@ struct Dev {
   Hod hod[4];          // 0 G^R, 1 G^<, 2 Sigma^R, 3 Sigma^<
   void* band;          // [n][nt][k][no2] Sigma^R(t, t-d), d = 1..k
   double2* proj;       // sweep projections [n][no][maxl][no2][rmax] (+ source: see kernels)
-  double2* tsvd_ws;    // TSVD workspace, tsvd_ws_per entries per CTA
-  long long tsvd_ws_per;
+  double2* tsvd_ws;    // TSVD workspace: [n][4][no2] groups of tsvd_ws_per entries,
+  long long tsvd_ws_per;  // level lv of a group at offset ws_lvoff[lv]
+  const long long* ws_lvoff;
   int* status;         // [0] rank overflow count, [1] Jacobi non-convergence count
   // frozen 32-point chunk inverses of the two sweeps (FP64): [n][nchunk][2][(32 no)^2]
   double2* cinv;
@@ -92,6 +93,7 @@ cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s);
+cudaError_t launch_density_at(const Dev& d, int t, double2* out, cudaStream_t s);  // rho(t), every instance
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s);
 // inverses of the frozen chunks [c0, c1) of sweep `which` (0 retarded, 1 lesser)
 cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s);
