@@ -726,7 +726,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                    if ((e = run_phase(h, HKBE_PHASE_MIXED, 1, [&]() { return hk::launch_mixed(d, T, h->s); })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_VT, 1, [&]() { return hk::launch_vt(d, T, h->s); }))) return e;
-                   if ((e = run_phase(h, HKBE_PHASE_SRC, (h->hodlr && d.cdir > 0) ? 2 : 1, [&]() {
+                   if ((e = run_phase(h, HKBE_PHASE_SRC, (h->hodlr && d.cdir > 0) ? 3 : 1, [&]() {
                           return h->hodlr ? hk::launch_src_h(d, T, h->s) : hk::launch_src(d, T, h->s);
                         })))
                      return e;

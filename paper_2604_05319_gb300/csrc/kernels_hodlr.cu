@@ -91,13 +91,161 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   }
 }
 
+// q(t) for the compressed columns t < c, one thread per t (adjacent threads
+// read adjacent elements of every row).  The weighted G^A(l, T) of the
+// uncompressed rows l in [c, T] (at most a leaf plus k+1 rows) is staged in
+// shared memory once per block.
+constexpr int kSrcRing = 80;   // >= leaf + k + 1 uncompressed rows
+template <int NO, typename S>
+__global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
+  constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
+  const int n = blockIdx.y;
+  if (!d.active[n]) return;
+  const int c = d.cdir, L = d.L;
+  const DevW& W = d.w;
+  __shared__ cx<R> gs[kSrcRing][NO2];  // gs[l - c][z][y] = w_l conj(G^R(T, l)[y][z])
+  const int nr = T + 1 - c;
+  for (int e = threadIdx.x; e < nr * NO2; e += blockDim.x) {
+    const int li = e / NO2, q = e % NO2, z = q / NO, y = q % NO, l = c + li;
+    gs[li][q] = ldr<R>(el<NO, S>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_wr<R>(W, T, l);
+  }
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= c) return;
+  const int jt = t / L, A = jt * L, E = min(A + L, c);
+  zd acc[NO2];
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  cx<R> pa[NO2];
+  auto zero = [&]() {
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) pa[q] = cx<R>(0);
+  };
+  auto fold = [&]() {
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) acc[q] += wide(pa[q]);
+    zero();
+  };
+  // pa[x][y] += sum_z Sx[x][z] g[z][y], Sx = S or S^dagger
+  auto mac_g = [&](const S* sp, bool dagS, const cx<R>* g) {
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int z = 0; z < NO; ++z) {
+        const cx<R> sxz = dagS ? ldr<R>(sp + z * NO + x).conj() : ldr<R>(sp + x * NO + z);
+#pragma unroll
+        for (int y = 0; y < NO; ++y) pa[x * NO + y] = cfma(sxz, g[z * NO + y], pa[x * NO + y]);
+      }
+  };
+  auto gload = [&](int l, cx<R>* g) {  // g[z][y] = w_l conj(G^R(T,l)[y][z])
+    const R wl = rule_wr<R>(W, T, l);
+    const S* gp = el<NO, S>(d.GR, d, n, T, l);
+#pragma unroll
+    for (int z = 0; z < NO; ++z)
+#pragma unroll
+      for (int y = 0; y < NO; ++y) g[z * NO + y] = ldr<R>(gp + y * NO + z).conj() * wl;
+  };
+  zero();
+  // l >= t: Sigma^<(t, l) = S[l][t]; the uncompressed rows [c, T] (coalesced over t)
+  for (int l0 = 0; l0 < nr; l0 += FOLD) {
+#pragma unroll
+    for (int jj = 0; jj < FOLD; ++jj)
+      if (l0 + jj < nr) mac_g(el<NO, S>(d.SL, d, n, c + l0 + jj, t), false, gs[l0 + jj]);
+    fold();
+  }
+  // the same leaf, l in [t, E)
+  cx<R> g[NO2];
+  for (int l0 = t; l0 < E; l0 += FOLD) {
+#pragma unroll
+    for (int jj = 0; jj < FOLD; ++jj) {
+      const int l = l0 + jj;
+      if (l < E) {
+        gload(l, g);
+        mac_g(Lf<NO, S>(d, 3, n, jt, l, t), false, g);
+      }
+    }
+    fold();
+  }
+  // l < t in the same leaf: -S[t][l]^dagger
+  for (int l0 = A; l0 < t; l0 += FOLD) {
+#pragma unroll
+    for (int jj = 0; jj < FOLD; ++jj) {
+      const int l = l0 + jj;
+      if (l < t) {
+        gload(l, g);
+#pragma unroll
+        for (int q = 0; q < NO2; ++q) g[q] = -g[q];
+        mac_g(Lf<NO, S>(d, 3, n, jt, t, l), true, g);
+      }
+    }
+    fold();
+  }
+  // blocks with t in their columns (P1 . conj V) and in their rows (-conj U . P2)
+  for (int lv = 0; lv < d.maxl; ++lv) {
+    const int b = d.colblk[jt * d.maxl + lv];
+    if (b < 0 || d.b_r0[b] >= c) continue;
+    const int c0 = d.b_c0[b];
+#pragma unroll
+    for (int p = 0; p < NO2; ++p) {
+      const int x = p / NO;
+      const int rk = *Rk<NO>(d, 3, n, b, p);
+      const S* V = Vp<NO, S>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
+#pragma unroll
+      for (int y = 0; y < NO; ++y) {
+        const double2* P = Psrc<NO>(d, n, b, p, y, 0);
+        cx<R> sb = cx<R>(0);
+        for (int q = 0; q < rk; ++q) sb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), sb);
+        acc[x * NO + y] += wide(sb);
+      }
+    }
+  }
+  for (int lv = 0; lv < d.maxl; ++lv) {
+    const int b = d.rowblk[jt * d.maxl + lv];
+    if (b < 0) continue;
+    const int r0 = d.b_r0[b];
+#pragma unroll
+    for (int p = 0; p < NO2; ++p) {  // p = (z, x)
+      const int x = p % NO;
+      const int rk = *Rk<NO>(d, 3, n, b, p);
+      const S* U = Up<NO, S>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
+#pragma unroll
+      for (int y = 0; y < NO; ++y) {
+        const double2* P = Psrc<NO>(d, n, b, p, y, 1);
+        cx<R> sb = cx<R>(0);
+        for (int q = 0; q < rk; ++q) sb = cfma(ldr<R>(U + q).conj(), ldr<R>(P + q), sb);
+        acc[x * NO + y] -= wide(sb);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] = acc[q] * d.h;
+  for (int a = 0; a < d.r; ++a) {  // -i sum_a Sigma^tv(t, tau_a) v_a
+    const double2* sv = tv<NO>(d.STV, d, n, t, a);
+    const double2* vv = d.vvec + ((long long)n * d.r + a) * NO2;
+#pragma unroll
+    for (int x = 0; x < NO; ++x)
+#pragma unroll
+      for (int z = 0; z < NO; ++z) {
+        const zd sxz = ld(sv + x * NO + z) * zd(0, -1);
+#pragma unroll
+        for (int y = 0; y < NO; ++y) acc[x * NO + y] = cfma(sxz, ld(vv + z * NO + y), acc[x * NO + y]);
+      }
+  }
+  double2* qp = d.qsrc + ((long long)n * d.nt + t) * NO2;
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) st(qp + q, acc[q]);
+}
+
+// q(t) for the uncompressed rows t in [c, T]: one warp per t (lanes along the row).
 template <int NO, typename S>
 __global__ void k_src_h(Dev d, int T) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int n = gw / (T + 1), t = gw % (T + 1);
+  const int nrow = T + 1 - d.cdir;
+  const int n = gw / nrow, t = d.cdir + gw % nrow;
   if (n >= d.n_inst || !d.active[n]) return;
   const int c = d.cdir, L = d.L;
   const double h = d.h;
@@ -582,7 +730,12 @@ cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s) {
     dim3 g(d.nblk, d.n_inst);
     HK_DISPATCH(d.no, (k_src_proj<NO, S><<<g, 256, 0, s>>>(d, T)));
   }
-  const long long warps = (long long)d.n_inst * (T + 1);
+  if (d.cdir > 0) {
+    if (T + 1 - d.cdir > kSrcRing) return cudaErrorInvalidValue;
+    dim3 g((d.cdir + 127) / 128, d.n_inst);
+    HK_DISPATCH(d.no, (k_src_c<NO, S><<<g, 128, 0, s>>>(d, T)));
+  }
+  const long long warps = (long long)d.n_inst * (T + 1 - d.cdir);
   HK_DISPATCH(d.no, (k_src_h<NO, S><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
