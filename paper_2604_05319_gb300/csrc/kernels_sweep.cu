@@ -79,10 +79,11 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2)
   if (tid == 0) serr = 0.0;
   // The row being solved lives in FP64 during the sweep (in the complex64
-  // storage form a separate buffer, copied out rounded at the end), so the
-  // point-to-point recursion of the sweep does not accumulate storage rounding.
-  // yp: the row as the sweep reads and writes it; sp: its storage (previous
-  // iterate, for the convergence measure).
+  // storage form a separate buffer), so the point-to-point recursion of the
+  // sweep (BDF terms, point solves) does not accumulate storage rounding.
+  // yp: the FP64 row; sp: its storage, written at the same time (rounded in
+  // the complex64 form), which the FP32 bulk sums read; it holds the previous
+  // iterate until an element is overwritten (the convergence measure).
   S* rowp = el<NO, S>(d.GR, d, n, T, 0);
   Y* rowy = Row64<NO, S>::get(d, n, 0, rowp);
   auto yp = [&](int tp) { return rowy + (long long)tp * NO2 + irow * NO; };
@@ -111,12 +112,14 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
       const int s = row / NO + 1, j = row % NO;
       myerr = fmax(myerr, (sB[row] - ld(sp(T - s) + j)).abs2());
       st(yp(T - s) + j, sB[row]);
+      if constexpr (Row64<NO, S>::separate) st(sp(T - s) + j, sB[row]);
     }
     if (lane == 0) {
       for (int j = 0; j < NO; ++j) {
         zd v = (j == irow) ? zd(0, -1) : zd();
         myerr = fmax(myerr, (ld(sp(T) + j) - v).abs2());
         st(yp(T) + j, v);
+        if constexpr (Row64<NO, S>::separate) st(sp(T) + j, v);
       }
     }
   }
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
             for (int jj = 0; jj < FOLD; ++jj) {
               const int s2 = s0 + 8 * jj;
               if (s2 < rl) {
-                const cx<R> yv = ldr<R>(yp(s2) + m);
+                const cx<R> yv = ldr<R>(sp(s2) + m);
                 const S* ur = U + (long long)(s2 - r0) * d.rmax;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
               const int s2 = s0 + 4 * jj;
               if (s2 <= T) {
                 const R ws = rule_wr<R>(W, T - tp, T - s2);
-                const Y* yl = yp(s2);
+                const S* yl = sp(s2);
                 const S* sr = el<NO, S>(d.SR, d, n, s2, tp);
 #pragma unroll
                 for (int m = 0; m < NO; ++m) {
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
             const int s2 = s0 + 8 * jj;
             if (s2 < s_end) {
               const R ws = rule_wr<R>(W, T - tp, T - s2);
-              const Y* yl = yp(s2);
+              const S* yl = sp(s2);
               const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, s2, tp) : el<NO, S>(d.SR, d, n, s2, tp);
 #pragma unroll
               for (int m = 0; m < NO; ++m) {
@@ -308,6 +311,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         if (sl == 0) {
           myerr = fmax(myerr, (sacc - ld(sp(a + ti) + j)).abs2());
           st(yp(a + ti) + j, sacc);
+          if constexpr (Row64<NO, S>::separate) st(sp(a + ti) + j, sacc);
         }
       }
     } else {
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
           for (int j = 0; j < NO; ++j) {
             myerr = fmax(myerr, (y[j] - ld(sp(spt) + j)).abs2());
             st(yp(spt) + j, y[j]);
+            if constexpr (Row64<NO, S>::separate) st(sp(spt) + j, y[j]);
           }
         }
 #pragma unroll
@@ -391,8 +396,6 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
     }
     __syncthreads();
   }
-  if (Row64<NO, S>::separate)  // copy the FP64 row out to its storage, rounded
-    for (int e = tid; e < (T + 1) * NO; e += blockDim.x) st(sp(e / NO) + e % NO, ld(yp(e / NO) + e % NO));
   myerr = sqrt(warp_max(myerr));
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
     zd v = ld(d.x0 + (long long)n * NO2 + m * NO + jc);
     myerr = fmax(myerr, (v - ld(sp(0) + m * NO + jc)).abs2());
     st(xp(0) + m * NO + jc, v);
+    if constexpr (Row64<NO, S>::separate) st(sp(0) + m * NO + jc, v);
   }
   __syncthreads();
   for (int cc = 0; cc * CK <= last; ++cc) {
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
               const int l = l0 + 8 * jj;
               if (l < c1) {
                 const R wl = (l <= k) ? (R)W.omega[l] : (R)1;
-                const cx<R> xv = ldr<R>(xp(l) + nn * NO + jc) * wl;
+                const cx<R> xv = ldr<R>(sp(l) + nn * NO + jc) * wl;
                 const S* vr = V + (long long)(l - c0) * d.rmax;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
                 const S* sr = comp ? Lf<NO, S>(d, 2, n, jl, t, l) : srow + (long long)l * NO2;
 #pragma unroll
                 for (int y = 0; y < NO; ++y) {
-                  const cx<R> xy = ldr<R>(xp(l) + y * NO + jc) * wl;
+                  const cx<R> xy = ldr<R>(sp(l) + y * NO + jc) * wl;
 #pragma unroll
                   for (int m = 0; m < NO; ++m) pa[m] = cfma(ldr<R>(sr + m * NO + y), xy, pa[m]);
                 }
@@ -611,6 +615,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         if (sl == 0 && ti < cn) {
           myerr = fmax(myerr, (sacc - ld(sp(a + ti) + m * NO + jc)).abs2());
           st(xp(a + ti) + m * NO + jc, sacc);
+          if constexpr (Row64<NO, S>::separate) st(sp(a + ti) + m * NO + jc, sacc);
         }
       }
     } else {
@@ -661,6 +666,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           if (t <= last) {
             myerr = fmax(myerr, (sB[row] - ld(sp(t) + m * NO + jc)).abs2());
             st(xp(t) + m * NO + jc, sB[row]);
+            if constexpr (Row64<NO, S>::separate) st(sp(t) + m * NO + jc, sB[row]);
           }
         }
         __syncwarp();
@@ -717,6 +723,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
           for (int m = 0; m < NO; ++m) {
             myerr = fmax(myerr, (x[m] - ld(sp(tp) + m * NO + jc)).abs2());
             st(xp(tp) + m * NO + jc, x[m]);
+            if constexpr (Row64<NO, S>::separate) st(sp(tp) + m * NO + jc, x[m]);
           }
         }
 #pragma unroll
@@ -732,11 +739,6 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
     }
     __syncthreads();
   }
-  if (Row64<NO, S>::separate)  // copy the FP64 column out (rows 0..last), rounded
-    for (int e = tid; e < (last + 1) * NO; e += blockDim.x) {
-      const int t = e / NO, m = e % NO;
-      st(sp(t) + m * NO + jc, ld(xp(t) + m * NO + jc));
-    }
   myerr = sqrt(warp_max(myerr));
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
