@@ -407,6 +407,8 @@ def from_workload(w, inst=0, **kw):
     from .models import make_model
     wl = w["wl"]
     params = dict(wl.params)
+    if "drive_A" in w:   # per-instance drive arrays (Nambu model)
+        params.update({"A": w["drive_A"][inst], "U": w["drive_U"][inst]})
     params.update(kw.pop("model_params", {}))
     model = make_model(wl.model, params)
     return KBEOracle(wl.nt, wl.h, wl.k, wl.beta, w["eps"][inst], w["gm"][inst],

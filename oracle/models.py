@@ -15,6 +15,8 @@ Sigma^tv(T, tau_i) on the DLR nodes.
          g_b^<(t,t') = i n_b e^{-i eps_b (t-t')},
          g_b^tv(t, tau) = -xi i n_b e^{-i eps_b t} e^{eps_b tau}
          with n_b the Fermi occupation at beta (Sec. 3.3 forms of G^HF).
+  nambu  driven Nambu DMFT: hybridisation (Eq. Hybrid) + second Born (Eq.
+         Sigma2B) + Fock (Eq. SigmaF), see Nambu
 """
 from __future__ import annotations
 
@@ -70,5 +72,73 @@ class Bath(Model):
                           * np.exp(np.outer(st.tau, eb)))
 
 
+def _bar_products(X, Y):
+    """Eq. Sigma2B index pattern for 2 x 2 Nambu matrices (bar i = 1 - i):
+    out_ij = X_ij X_{bi bj} Y_{bj bi} - X_{bi j} X_{i bj} Y_{bj bi},
+    for stacks X[..., 2, 2] (the two equal-time-order factors) and Y (the
+    reversed-time factor)."""
+    out = np.zeros_like(X)
+    for i in range(2):
+        for j in range(2):
+            bi, bj = 1 - i, 1 - j
+            out[..., i, j] = (X[..., i, j] * X[..., bi, bj] - X[..., bi, j] * X[..., i, bj]) * Y[..., bj, bi]
+    return out
+
+
+class Nambu(Model):
+    """Nambu (2 x 2) impurity of a Bethe-lattice DMFT with the driven
+    hybridisation of Eq. Hybrid, the second-Born bubble and exchange diagrams
+    of Eq. Sigma2B and the Fock term of Eq. SigmaF (Sec. 4.1).
+
+    params: v   hopping scale (Delta carries v^2; the paper's case is v = 1)
+            A   vector potential, array [nt+1]: A[0] on the equilibrium branch,
+                A[t+1] at time t (Peierls phases t0-bar = diag(e^{iA}, e^{-iA}))
+            U   interaction, array [nt+1], same indexing (U(t) U(t') in Eq.
+                Sigma2B; the equilibrium-branch value enters the mixed part)
+
+    With s = (1, -1) the hybridisation of Eq. Hybrid is, element by element,
+        Delta_ij(t, t') = v^2 s_i s_j G_ij(t, t') cos(s_i A(t) - s_j A(t')).
+    The bubble and exchange give Sigma^>(T, t) from G^>(T, t) and G^<(t, T),
+    Sigma^<(T, t) from G^<(T, t) and G^>(t, T); Sigma^R = Sigma^> - Sigma^< on
+    t <= T.  The mixed part uses G^tv(T, tau) and G^vt(tau, T) the same way
+    (the imaginary branch is latest on the contour).  The Fock term
+    Sigma^F_ij(t) = -U(t) rho_ij(t) [i = bar j] is time-local: it is added to
+    the external eps(t) every time Sigma is evaluated."""
+    name = "nambu"
+    self_consistent = True
+
+    def eval_step(self, st, T):
+        if not hasattr(self, "eps_ext"):
+            self.eps_ext = st.eps.copy()
+        v2 = float(self.params.get("v", 1.0)) ** 2
+        A = np.asarray(self.params.get("A", np.zeros(st.nt + 1)), dtype=float)
+        U = np.asarray(self.params.get("U", np.zeros(st.nt + 1)), dtype=float)
+        s = np.array([1.0, -1.0])
+        ss = np.outer(s, s)
+
+        def dag(x):
+            return np.conj(np.swapaxes(x, -1, -2))
+        GR = st.GR[T, :T + 1]                     # G^R(T, t)
+        GLc = st.GLs[T, :T + 1]                   # G^<(t, T)
+        GLr = -dag(GLc)                           # G^<(T, t)
+        GGr = GR + GLr                            # G^>(T, t)
+        GGc = -dag(GGr)                           # G^>(t, T)
+        uu = (U[T + 1] * U[1:T + 2])[:, None, None]
+        Sg = uu * _bar_products(GGr, GLc)         # Sigma^>(T, t)
+        Sl = uu * _bar_products(GLr, GGc)         # Sigma^<(T, t)
+        ph = np.cos(s[None, :, None] * A[T + 1] - s[None, None, :] * A[1:T + 2][:, None, None])
+        st.SR[T, :T + 1] = Sg - Sl + v2 * ss * GR * ph
+        st.SLs[T, :T + 1] = -dag(Sl + v2 * ss * GLr * ph)
+        Gtv = st.GTV[T]                           # G^tv(T, tau_i)
+        Gvt = st.gvt(T)                           # G^vt(tau_i, T)
+        ph0 = np.cos(s[:, None] * A[T + 1] - s[None, :] * A[0])
+        st.STV[T] = U[T + 1] * U[0] * _bar_products(Gtv, Gvt) + v2 * ss * Gtv * ph0
+        rho = st.rho(T)
+        sf = np.zeros((2, 2), complex)
+        sf[0, 1] = -U[T + 1] * rho[0, 1]
+        sf[1, 0] = -U[T + 1] * rho[1, 0]
+        st.eps[T + 1] = self.eps_ext[T + 1] + sf
+
+
 def make_model(name, params=None):
-    return {"none": Model, "bethe": Bethe, "bath": Bath}[name](params)
+    return {"none": Model, "bethe": Bethe, "bath": Bath, "nambu": Nambu}[name](params)
