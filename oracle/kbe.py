@@ -58,7 +58,7 @@ class KBEOracle:
         self.k = int(k)
         self.beta = float(beta)
         self.xi = int(xi)
-        self.eps = np.asarray(eps, dtype=complex)        # (nt+1, No, No)
+        self.eps = np.array(eps, dtype=complex)          # (nt+1, No, No), own copy (a Fock term updates it)
         self.no = self.eps.shape[-1]
         self.tau = np.asarray(tau, dtype=float)
         self.r = len(self.tau)
