@@ -50,7 +50,8 @@ enum {
 enum {
   HKBE_MODEL_NONE = 0,   /* Sigma = 0                                              */
   HKBE_MODEL_BETHE = 1,  /* Bethe-lattice DMFT: Sigma = v^2 G (Eq. Hybrid, N_o=1)  */
-  HKBE_MODEL_BATH = 2    /* fixed bath: Sigma = V g_b V^dagger, bath levels eps_b   */
+  HKBE_MODEL_BATH = 2,   /* fixed bath: Sigma = V g_b V^dagger, bath levels eps_b   */
+  HKBE_MODEL_NAMBU = 3   /* Nambu DMFT (N_o = 2): Eq. Hybrid + Eq. Sigma2B + Eq. SigmaF */
 };
 
 /* Storage / arithmetic of the history integrals. */
@@ -129,8 +130,23 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
  *   HKBE_MODEL_BETHE: nparams >= 1, params[0] = v (Sigma = v^2 G).
  *   HKBE_MODEL_BATH : nparams = 1 + nb + 2*N_o*nb with
  *       params[0] = nb (1..4 bath levels), params[1..nb] = eps_b,
- *       then V[N_o][nb] complex interleaved (Sigma = V g_b V^dagger). */
+ *       then V[N_o][nb] complex interleaved (Sigma = V g_b V^dagger).
+ *   HKBE_MODEL_NAMBU: N_o = 2 (Nambu spinor (d_up, d_dn^dagger), Sec. 4.1),
+ *       nparams >= 1, params[0] = v (hopping scale, Delta carries v^2).
+ *       Sigma = Delta + Sigma^2B with, element by element and s = (1, -1),
+ *       Delta_ij(t,t') = v^2 s_i s_j G_ij(t,t') cos(s_i A(t) - s_j A(t'))
+ *       (Eq. Hybrid, Peierls phases diag(e^{iA}, e^{-iA})), the bubble and
+ *       exchange diagrams of Eq. Sigma2B with U(t)U(t'), and the Fock term
+ *       of Eq. SigmaF added to eps(t) at every evaluation (eps as set by the
+ *       caller is kept apart).  A(t), U(t) come from hkbe_set_drive. */
 int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams);
+
+/* Drive of the Nambu model: A[n_inst][nt+1] (vector potential) and
+ * U[n_inst][nt+1] (interaction), index 0 the equilibrium branch, index t+1
+ * time t (Sec. 4.1: A(t) = -int_0^t E, U(t) of the Hamiltonian).  Either may
+ * be NULL (zero).  Must precede hkbe_bootstrap.  HKBE_ERR_NAN for non-finite
+ * values. */
+int hkbe_set_drive(hkbe_t* h, const double* A, const double* U);
 
 /* Bootstrap the first k+1 time steps (Sec. 3.3, dyson_start_ntti): mean-field
  * guess (green_from_H) followed by global iterations of Sigma and the start

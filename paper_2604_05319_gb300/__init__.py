@@ -21,7 +21,7 @@ from . import _build
 HKBE_OK = 0
 ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "HKBE_ERR_RANGE",
           -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM"}
-MODEL_NONE, MODEL_BETHE, MODEL_BATH = 0, 1, 2
+MODEL_NONE, MODEL_BETHE, MODEL_BATH, MODEL_NAMBU = 0, 1, 2, 3
 PREC_FP64 = 0
 PREC_MIXED = 1
 
@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
         "hkbe_set_hamiltonian_at": ([H, C.c_int, C.c_void_p], C.c_int),
         "hkbe_get_density_at": ([H, C.c_int, C.c_void_p], C.c_int),
         "hkbe_set_model": ([H, C.c_int, _D, C.c_int], C.c_int),
+        "hkbe_set_drive": ([H, _D, _D], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
         "hkbe_current_step": ([H, _I], C.c_int),
@@ -209,6 +210,13 @@ def _ptr(a):
     if isinstance(a, int):
         return C.c_void_p(a)
     return C.c_void_p(a.ctypes.data)
+
+
+def hkbe_set_drive(h, A=None, U=None):
+    """Nambu drive: A[n_inst, nt+1], U[n_inst, nt+1] (None: zero)."""
+    a = None if A is None else np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    u = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.float64))
+    _check(load().hkbe_set_drive(h, _dp(a) if a is not None else None, _dp(u) if u is not None else None), h)
 
 
 def hkbe_set_hamiltonian_at(h, t, eps_t):
@@ -393,4 +401,6 @@ def model_params_for(workload_dict):
         return MODEL_BETHE, np.asarray(workload_dict["model_params"], dtype=float)
     if wl.model == "none":
         return MODEL_NONE, None
+    if wl.model == "nambu":
+        return MODEL_NAMBU, np.asarray(workload_dict["model_params"], dtype=float)
     raise ValueError(wl.model)

@@ -346,6 +346,8 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   if ((rc = dalloc_el(h, &d.GR, tri)) || (rc = dalloc_el(h, &d.GL, tri)) || (rc = dalloc_el(h, &d.SR, tri)) ||
       (rc = dalloc_el(h, &d.SL, tri)) ||
       (rc = dalloc(h, &d.eps, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
+      (rc = dalloc(h, &d.eps_ext, (size_t)d.n_inst * (d.nt + 1) * d.no * d.no)) ||
+      (rc = dalloc(h, &d.drA, (size_t)d.n_inst * (d.nt + 1))) || (rc = dalloc(h, &d.drU, (size_t)d.n_inst * (d.nt + 1))) ||
       (rc = dalloc(h, &d.mpar, (size_t)d.n_inst * hk::MP)) ||
       (rc = dalloc(h, &d.qsrc, (size_t)d.n_inst * d.nt * d.no * d.no)) ||
       (rc = dalloc(h, &d.x0, (size_t)d.n_inst * d.no * d.no)) || (rc = dalloc(h, &d.err, (size_t)d.n_inst)) ||
@@ -441,6 +443,7 @@ int hkbe_set_hamiltonian(hkbe_t* h, const double* eps) {
     if (!std::isfinite(eps[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in eps");
   h->eps_host.assign(eps, eps + cnt);
   HK_CUDA(h, cudaMemcpyAsync(d.eps, eps, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.eps_ext, eps, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->have_eps = true;
   return HKBE_OK;
@@ -455,12 +458,33 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t) {
   for (int i = 0; i < d.n_inst * n2 * 2; ++i)
     if (!std::isfinite(eps_t[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in eps_t");
   // eps is [n][nt+1][no2], index t+1: one strided copy of n_inst pieces
-  HK_CUDA(h, cudaMemcpy2DAsync(d.eps + (size_t)(t + 1) * n2, (size_t)(d.nt + 1) * n2 * sizeof(double2), eps_t,
-                               (size_t)n2 * sizeof(double2), (size_t)n2 * sizeof(double2), d.n_inst,
-                               cudaMemcpyHostToDevice, h->s));
+  for (double2* dst : {d.eps, d.eps_ext})
+    HK_CUDA(h, cudaMemcpy2DAsync(dst + (size_t)(t + 1) * n2, (size_t)(d.nt + 1) * n2 * sizeof(double2), eps_t,
+                                 (size_t)n2 * sizeof(double2), (size_t)n2 * sizeof(double2), d.n_inst,
+                                 cudaMemcpyHostToDevice, h->s));
   for (int n = 0; n < d.n_inst; ++n)
     std::memcpy(&h->eps_host[(((size_t)n * (d.nt + 1)) + t + 1) * n2 * 2], eps_t + (size_t)n * n2 * 2,
                 n2 * 2 * sizeof(double));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_set_drive(hkbe_t* h, const double* A, const double* U) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "hkbe_set_drive must precede hkbe_bootstrap");
+  Dev& d = h->d;
+  const size_t cnt = (size_t)d.n_inst * (d.nt + 1);
+  for (int w = 0; w < 2; ++w) {
+    const double* src = w == 0 ? A : U;
+    double* dst = w == 0 ? d.drA : d.drU;
+    if (!src) {
+      HK_CUDA(h, cudaMemsetAsync(dst, 0, cnt * sizeof(double), h->s));
+      continue;
+    }
+    for (size_t i = 0; i < cnt; ++i)
+      if (!std::isfinite(src[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in the drive");
+    HK_CUDA(h, cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
 }
@@ -486,6 +510,11 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
       std::memcpy(&mp[(size_t)n * hk::MP], q, nparams * sizeof(double));
     }
     h->self_consistent = false;
+  } else if (model == HKBE_MODEL_NAMBU) {
+    if (no != 2) return fail(h, HKBE_ERR_ARG, "NAMBU needs nao = 2");
+    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "NAMBU needs params[0] = v");
+    for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = params[(size_t)n * nparams];
+    h->self_consistent = true;
   } else {
     return fail(h, HKBE_ERR_ARG, "unknown model");
   }
@@ -923,6 +952,8 @@ int hkbe_rewind(hkbe_t* h) {
     return cudaSuccess;
   };
   for (auto& a : h->state_arrays) HK_CUDA(h, cudaMemsetAsync(a.first, 0, a.second, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(d.eps, d.eps_ext, (size_t)d.n_inst * (d.nt + 1) * n2 * sizeof(double2),
+                             cudaMemcpyDeviceToDevice, h->s));
   HK_CUDA(h, put(h->snap_gr, d.GR));
   HK_CUDA(h, put(h->snap_gl, d.GL));
   HK_CUDA(h, put(h->snap_sr, d.SR));

@@ -55,6 +55,99 @@ __device__ void bath_sigma(const double* mp, zd g0, double eb_dt_sign, int which
   (void)g0; (void)eb_dt_sign;
 }
 
+// Nambu DMFT self-energy (N_o = 2): driven hybridisation of Eq. Hybrid plus
+// the second-Born bubble and exchange of Eq. Sigma2B, element by element
+//   Delta_ij(t,t') = v^2 s_i s_j G_ij(t,t') cos(s_i A(t) - s_j A(t')), s = (1,-1),
+//   Sigma^>(T,t)_ij = U(T)U(t) [X_ij X_{bi bj} - X_{bi j} X_{i bj}] Y_{bj bi},
+//   X = G^>(T,t), Y = G^<(t,T); Sigma^< likewise with X = G^<(T,t), Y = G^>(t,T);
+// Sigma^R = Sigma^> - Sigma^< for t <= T.  bar i = 1 - i.
+__device__ __forceinline__ void nambu_bar(const zd* X, const zd* Y, double u, zd* out) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int bi = 1 - i, bj = 1 - j;
+      out[i * 2 + j] = (X[i * 2 + j] * X[bi * 2 + bj] - X[bi * 2 + j] * X[i * 2 + bj]) * Y[bj * 2 + bi] * u;
+    }
+}
+template <typename S>
+__device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
+  const double* mp = d.mpar + (long long)n * MP;
+  const double v2 = mp[0] * mp[0];
+  const double* A = d.drA + (long long)n * (d.nt + 1);
+  const double* U = d.drU + (long long)n * (d.nt + 1);
+  const double s[2] = {1.0, -1.0};
+  if (idx <= T) {
+    const int t = idx;
+    zd GR[4], GLc[4], GLr[4], GGr[4], GGc[4], Sg[4], Sl[4];
+    const S* pr = el<2, S>(d.GR, d, n, T, t);
+    const S* pl = el<2, S>(d.GL, d, n, T, t);            // G^<(t, T)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { GR[q] = ld(pr + q); GLc[q] = ld(pl + q); }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) GLr[i * 2 + j] = -GLc[j * 2 + i].conj();     // G^<(T, t)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) GGr[q] = GR[q] + GLr[q];                       // G^>(T, t)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) GGc[i * 2 + j] = -GGr[j * 2 + i].conj();     // G^>(t, T)
+    const double uu = U[T + 1] * U[t + 1];
+    nambu_bar(GGr, GLc, uu, Sg);
+    nambu_bar(GLr, GGc, uu, Sl);
+    S* sr = el<2, S>(d.SR, d, n, T, t);
+    zd slr[4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double w = v2 * s[i] * s[j] * cos(s[i] * A[T + 1] - s[j] * A[t + 1]);
+        st(sr + i * 2 + j, Sg[i * 2 + j] - Sl[i * 2 + j] + GR[i * 2 + j] * w);
+        slr[i * 2 + j] = Sl[i * 2 + j] + GLr[i * 2 + j] * w;                    // Sigma^<(T, t)
+      }
+    S* sl = el<2, S>(d.SL, d, n, T, t);                                         // stores Sigma^<(t, T)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) st(sl + i * 2 + j, -slr[j * 2 + i].conj());
+    if (t == T) {  // Fock term of Eq. SigmaF, Sigma^F_ij = -U(T) rho_ij [i = bar j], rho = xi i G^<(T,T)
+      const zd rxi(0, (double)d.xi);
+      const double2* ee = d.eps_ext + ((long long)n * (d.nt + 1) + T + 1) * 4;
+      double2* e = d.eps + ((long long)n * (d.nt + 1) + T + 1) * 4;
+      st(e + 0, ld(ee + 0));
+      st(e + 3, ld(ee + 3));
+      st(e + 1, ld(ee + 1) - GLc[1] * rxi * U[T + 1]);
+      st(e + 2, ld(ee + 2) - GLc[2] * rxi * U[T + 1]);
+    }
+  } else if (idx > 2 * T + 1) {
+    const int i = idx - 2 * (T + 1), r = d.r;
+    zd Gtv[4], Gvt[4], Sb[4];
+    const double2* pt = tv<2>(d.GTV, d, n, T, i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Gtv[q] = ld(pt + q);
+    zd gb[4] = {zd(), zd(), zd(), zd()};          // G^tv(T, beta - tau_i)
+    for (int c = 0; c < r; ++c) {
+      const double rv = d.rev[i * r + c];
+      const double2* pc = tv<2>(d.GTV, d, n, T, c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) gb[q] += ld(pc + q) * rv;
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) Gvt[x * 2 + y] = gb[y * 2 + x].conj() * (-(double)d.xi);  // G^vt(tau_i, T)
+    nambu_bar(Gtv, Gvt, U[T + 1] * U[0], Sb);
+    double2* so = tv<2>(d.STV, d, n, T, i);
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y)
+        st(so + x * 2 + y, Sb[x * 2 + y] + Gtv[x * 2 + y] * (v2 * s[x] * s[y] * cos(s[x] * A[T + 1] - s[y] * A[0])));
+  }
+}
+
 template <int NO, typename S>
 __global__ void k_sigma(Dev d, int T) {
   constexpr int NO2 = NO * NO;
@@ -63,6 +156,12 @@ __global__ void k_sigma(Dev d, int T) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int total = 2 * (T + 1) + d.r;
   if (idx >= total) return;
+  if constexpr (NO == 2) {
+    if (d.model == 3) {
+      nambu_sigma<S>(d, n, T, idx);
+      return;
+    }
+  }
   const double* mp = d.mpar + (long long)n * MP;
   // src / dst are S* for the two-time rows, double2* for the mixed row
   auto apply = [&](const auto* src, auto* dst, int which, double tph, double tauv) {

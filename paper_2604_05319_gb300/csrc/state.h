@@ -59,7 +59,9 @@ struct Dev {
   int prec;                    // 0: double2 storage, 1: float2 storage (mixed form)
   void *GR, *GL, *SR, *SL;     // lower-triangular (or ring), GL(T,t) = G^<(t,T)
   void *GTV, *STV;             // [n][nt][r][no2], complex128 in both forms
-  double2 *eps;                // [n][nt+1][no2], index t+1
+  double2 *eps;                // [n][nt+1][no2], index t+1 (external eps plus any Fock term)
+  double2 *eps_ext;            // [n][nt+1][no2] external eps as set by the caller
+  double *drA, *drU;           // [n][nt+1] drive: vector potential A(t), interaction U(t)
   double2 *gm;                 // [n][r][no2]
   double2 *wconv;              // [n][r(a)][r(i)][no2]
   double *tau, *e0, *ebeta, *rev, *q;  // [r], [r], [r], [r*r], [r*r]
