@@ -1,0 +1,93 @@
+"""Pins of the oracle's 2D Hubbard second-Born lattice (Sec. 4.2):
+- U = 0: every k-point is a free level with the Peierls-shifted dispersion,
+  G^R_k = -i e^{-i int eps_k}, G^<_k = i f(eps_k(0_|)) e^{-i int eps_k};
+- the real-space (FFT) second-Born self-energy equals the momentum double sum
+  U^2/N_k^2 sum_{k1,k2} G_{k1} G_{k2} G_{k1+k2-k} (brute force, 4 x 4);
+- with the drive along x the state keeps the k_y -> -k_y reflection symmetry;
+- the particle number per spin stays at 1/2 (half filling, conserving
+  approximation) to the discretisation error, in both density-matrix schemes.
+"""
+import numpy as np
+import pytest
+
+import kbe_workloads as wk
+from oracle.lattice import LatticeOracle, lattice_sigma
+
+
+def _make(w, tol=1e-13):
+    wl = w["wl"]
+    return LatticeOracle(w["L"], wl.nt, wl.h, wl.k, wl.beta, w["eps"], w["gm"], w["tau"], w["omega"],
+                         w["drive_U"][0], rho_mode=wl.rho_mode, tol=tol)
+
+
+def test_u0_free_levels_with_peierls_phase():
+    errs = []
+    for nt, h in [(60, 0.05), (120, 0.025)]:
+        w = wk.lattice_workload(L=4, nt=nt, h=h, k=5, beta=10.0, U=0.0, A0=0.6, Omega=1.5, tc=1.0,
+                                width=0.3, dlr_eps=1e-12)
+        o = _make(w).run()
+        sub = 400                                    # fine trapezoid for int eps_k(t) dt
+        tf = np.linspace(0, (nt - 1) * h, sub * (nt - 1) + 1)
+        Af = 0.6 * np.sin(1.5 * tf) * np.exp(-(tf - 1.0) ** 2 / 0.3)
+        e = 0.0
+        for q in (0, 5, 11):
+            ef = -2 * (np.cos(w["kx"][q] - Af) + np.cos(w["ky"][q]))
+            cum = np.concatenate([[0.0], np.cumsum(0.5 * (ef[1:] + ef[:-1]) * (tf[1] - tf[0]))])[::sub]
+            ph = np.exp(-1j * (cum[:, None] - cum[None, :]))
+            f = 1 / (1 + np.exp(10.0 * w["eps"][q, 0, 0, 0].real))
+            idx = np.tril_indices(nt)
+            e = max(e, np.abs(o.orcs[q].GR[..., 0, 0][idx] - (-1j * ph)[idx]).max(),
+                    np.abs(o.orcs[q].GLs[..., 0, 0][idx] - (1j * f * ph).T[idx]).max())
+        errs.append(e)
+    assert errs[1] < 1e-4
+    assert errs[0] / errs[1] > 2 ** 4                 # order-5 convergence (a steep pulse)
+
+
+def test_fft_sigma_equals_momentum_double_sum():
+    L = 4
+    w = wk.lattice_workload(L=L, nt=12, h=0.05, k=2, beta=10.0, U=1.3, A0=0.4)
+    o = _make(w)
+    rng = np.random.default_rng(2)
+    T = 9
+    for orc in o.orcs:              # random current rows
+        orc.GR[T, :T + 1, 0, 0] = rng.normal(size=T + 1) + 1j * rng.normal(size=T + 1)
+        orc.GLs[T, :T + 1, 0, 0] = rng.normal(size=T + 1) + 1j * rng.normal(size=T + 1)
+    U = w["drive_U"][0]
+    lattice_sigma(o.orcs, L, U, T)
+    nk = L * L
+    GR = np.array([x.GR[T, :T + 1, 0, 0] for x in o.orcs])
+    GLc = np.array([x.GLs[T, :T + 1, 0, 0] for x in o.orcs])
+    GLr = -np.conj(GLc)
+    GGr = GR + GLr
+    GGc = -np.conj(GGr)
+    uu = U[T + 1] * U[1:T + 2]
+    mx, my = np.divmod(np.arange(nk), L)
+    for q in (0, 3, 6, 13):
+        sg = np.zeros(T + 1, complex)
+        sl = np.zeros(T + 1, complex)
+        for k1 in range(nk):
+            for k2 in range(nk):
+                k3 = ((mx[k1] + mx[k2] - mx[q]) % L) * L + (my[k1] + my[k2] - my[q]) % L
+                sg += GGr[k1] * GGr[k2] * GLc[k3]
+                sl += GLr[k1] * GLr[k2] * GGc[k3]
+        sg *= uu / nk ** 2
+        sl *= uu / nk ** 2
+        assert np.allclose(o.orcs[q].SR[T, :T + 1, 0, 0], sg - sl, rtol=1e-12, atol=1e-12)
+        assert np.allclose(o.orcs[q].SLs[T, :T + 1, 0, 0], -np.conj(sl), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("rho_mode", [0, 1])
+def test_reflection_symmetry_and_half_filling(rho_mode):
+    L = 4
+    w = wk.lattice_workload(L=L, nt=50, h=0.05, k=4, beta=10.0, U=2.0, t_quench=0.2, A0=0.5, Omega=1.2,
+                            tc=1.0, width=0.4, rho_mode=rho_mode)
+    o = _make(w).run()
+    for mx in range(L):
+        for my in range(1, L):
+            a = o.orcs[mx * L + my].GLs[..., 0, 0]
+            b = o.orcs[mx * L + (L - my) % L].GLs[..., 0, 0]
+            assert np.abs(a - b).max() < 1e-12
+    n, ekin, j = o.observables(w["drive_A"][0])
+    # conserved to the discretisation error (h = 0.05, a steep pulse and a quench of U)
+    assert np.abs(n - 0.5).max() < 5e-3
+    assert np.abs(j).max() > 1e-3            # the pulse drives a current
