@@ -51,7 +51,8 @@ enum {
   HKBE_MODEL_NONE = 0,   /* Sigma = 0                                              */
   HKBE_MODEL_BETHE = 1,  /* Bethe-lattice DMFT: Sigma = v^2 G (Eq. Hybrid, N_o=1)  */
   HKBE_MODEL_BATH = 2,   /* fixed bath: Sigma = V g_b V^dagger, bath levels eps_b   */
-  HKBE_MODEL_NAMBU = 3   /* Nambu DMFT (N_o = 2): Eq. Hybrid + Eq. Sigma2B + Eq. SigmaF */
+  HKBE_MODEL_NAMBU = 3,  /* Nambu DMFT (N_o = 2): Eq. Hybrid + Eq. Sigma2B + Eq. SigmaF */
+  HKBE_MODEL_LATTICE2B = 4  /* 2D Hubbard, second Born through real space (Sec. 4.2)   */
 };
 
 /* Storage / arithmetic of the history integrals. */
@@ -138,7 +139,15 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
  *       (Eq. Hybrid, Peierls phases diag(e^{iA}, e^{-iA})), the bubble and
  *       exchange diagrams of Eq. Sigma2B with U(t)U(t'), and the Fock term
  *       of Eq. SigmaF added to eps(t) at every evaluation (eps as set by the
- *       caller is kept apart).  A(t), U(t) come from hkbe_set_drive. */
+ *       caller is kept apart).  A(t), U(t) come from hkbe_set_drive.
+ *   HKBE_MODEL_LATTICE2B: N_o = 1, one instance per k-point of an L x L grid,
+ *       k = 2 pi (m_x, m_y)/L at instance m_x L + m_y, n_inst = L^2, L <= 16;
+ *       params[n][0] = L.  Sigma^≷_k from Sigma^≷_r(T,t) =
+ *       U(T)U(t) G^≷_r(T,t)^2 G^≶_{-r}(t,T) (G_r the lattice Fourier
+ *       transform over k; the mixed part with the imaginary branch latest),
+ *       U(t) from hkbe_set_drive (instance 0; the same for every k).  The
+ *       dispersion with its Peierls shift eps_{k-A(t)} is the caller's eps.
+ *       The k-points iterate together (all or none). */
 int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams);
 
 /* Drive of the Nambu model: A[n_inst][nt+1] (vector potential) and
@@ -188,6 +197,14 @@ int hkbe_get_density(hkbe_t* h, double* rho);
  * rho_t[n_inst][N_o][N_o] complex, gathered on the device and copied once.
  * HKBE_ERR_RANGE outside 0..current step.  Synchronous. */
 int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t);
+
+/* Observables of the LATTICE2B model at time t <= current step (Sec. 4.2,
+ * spin summed where the paper does): out[0] = n = -(i/N_k) sum_k G^<_k(t,t)
+ * (per spin), out[1] = E_kin = -(2i/N_k) sum_k eps_k G^<_k(t,t) with
+ * eps_k = -2(cos k_x + cos k_y), out[2] = j = -(2i/N_k) sum_k
+ * 2 sin(k_x - A(t)) G^<_k(t,t).  Reduced on the device.  HKBE_ERR_ARG for
+ * another model, HKBE_ERR_RANGE for t outside 0..current step. */
+int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out);
 
 /* Device bytes held by the handle. */
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);

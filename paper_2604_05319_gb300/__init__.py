@@ -21,7 +21,7 @@ from . import _build
 HKBE_OK = 0
 ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "HKBE_ERR_RANGE",
           -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM"}
-MODEL_NONE, MODEL_BETHE, MODEL_BATH, MODEL_NAMBU = 0, 1, 2, 3
+MODEL_NONE, MODEL_BETHE, MODEL_BATH, MODEL_NAMBU, MODEL_LATTICE2B = 0, 1, 2, 3, 4
 PREC_FP64 = 0
 PREC_MIXED = 1
 
@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
         "hkbe_get_density_at": ([H, C.c_int, C.c_void_p], C.c_int),
         "hkbe_set_model": ([H, C.c_int, _D, C.c_int], C.c_int),
         "hkbe_set_drive": ([H, _D, _D], C.c_int),
+        "hkbe_get_lattice_observables": ([H, C.c_int, _D], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
         "hkbe_current_step": ([H, _I], C.c_int),
@@ -217,6 +218,13 @@ def hkbe_set_drive(h, A=None, U=None):
     a = None if A is None else np.ascontiguousarray(np.asarray(A, dtype=np.float64))
     u = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.float64))
     _check(load().hkbe_set_drive(h, _dp(a) if a is not None else None, _dp(u) if u is not None else None), h)
+
+
+def hkbe_get_lattice_observables(h, t):
+    """(n, E_kin, j) of a LATTICE2B handle at time t."""
+    out = np.zeros(3)
+    _check(load().hkbe_get_lattice_observables(h, int(t), _dp(out)), h)
+    return out
 
 
 def hkbe_set_hamiltonian_at(h, t, eps_t):
@@ -403,4 +411,6 @@ def model_params_for(workload_dict):
         return MODEL_NONE, None
     if wl.model == "nambu":
         return MODEL_NAMBU, np.asarray(workload_dict["model_params"], dtype=float)
+    if wl.model == "lattice2b":
+        return MODEL_LATTICE2B, np.asarray(workload_dict["model_params"], dtype=float)
     raise ValueError(wl.model)

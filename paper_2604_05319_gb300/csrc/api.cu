@@ -510,6 +510,14 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
       std::memcpy(&mp[(size_t)n * hk::MP], q, nparams * sizeof(double));
     }
     h->self_consistent = false;
+  } else if (model == HKBE_MODEL_LATTICE2B) {
+    if (no != 1) return fail(h, HKBE_ERR_ARG, "LATTICE2B needs nao = 1");
+    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "LATTICE2B needs params[0] = L");
+    const int L = (int)params[0];
+    if (L < 1 || L > 16 || L * L != d.n_inst || (double)L != params[0])
+      return fail(h, HKBE_ERR_ARG, "LATTICE2B needs an integer L in 1..16 with n_inst = L*L");
+    for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = L;
+    h->self_consistent = true;
   } else if (model == HKBE_MODEL_NAMBU) {
     if (no != 2) return fail(h, HKBE_ERR_ARG, "NAMBU needs nao = 2");
     if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "NAMBU needs params[0] = v");
@@ -648,6 +656,10 @@ static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, 
     HK_CUDA(h, cudaStreamSynchronize(h->s));
     drain(h);
     if (!any) break;
+    if (d.model == HKBE_MODEL_LATTICE2B) {  // k-points are coupled through Sigma: iterate all or none
+      std::fill(act.begin(), act.end(), 1);
+      HK_CUDA(h, cudaMemcpyAsync(d.active, act.data(), N * sizeof(int), cudaMemcpyHostToDevice, h->s));
+    }
   }
   *any_failed = false;
   for (int n = 0; n < N; ++n) {
@@ -916,6 +928,17 @@ int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t) {
   const size_t cnt = (size_t)d.n_inst * no2(h);
   HK_CUDA(h, hk::launch_density_at(d, t, h->diagbuf, h->s));
   HK_CUDA(h, cudaMemcpyAsync(rho_t, h->diagbuf, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out) {
+  if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (h->d.model != HKBE_MODEL_LATTICE2B) return fail(h, HKBE_ERR_ARG, "not a LATTICE2B handle");
+  if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
+  double* dev = reinterpret_cast<double*>(h->diagbuf);   // >= 3 doubles (n_inst >= 1 complex)
+  HK_CUDA(h, hk::launch_lattice_obs(h->d, t, dev, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(out, dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   return HKBE_OK;
 }

@@ -1043,6 +1043,7 @@ cudaError_t launch_extrapolate(const Dev& d, int T, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_sigma(const Dev& d, int T, cudaStream_t s) {
+  if (d.model == 4) return launch_sigma_lattice(d, T, s);
   dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
   HK_DISPATCH(d.no, (k_sigma<NO, S><<<g, 128, 0, s>>>(d, T)));
   return cudaGetLastError();

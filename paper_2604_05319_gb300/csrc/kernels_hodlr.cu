@@ -712,6 +712,130 @@ __global__ void k_density_at(Dev d, int t, double2* out) {
   st(out + e, ld(p + q) * zd(0, (double)d.xi));
 }
 
+
+// ---------------------------------------------------------------------------
+// 2D Hubbard lattice, second Born (Sec. 4.2), N_o = 1, one instance per
+// k = 2 pi (m_x, m_y)/L (instance m_x L + m_y).  One CTA per time t of the
+// current row (and per DLR node for the mixed row); thread q owns k-point q
+// and real-space point r = (q / L, q % L):
+//   X_r = (1/N_k) sum_k e^{+i k.r} X_k,  Y_{-r} = (1/N_k) sum_k e^{-i k.r} Y_k,
+//   Sigma^>_r = U(T)U(t) G^>_r(T,t)^2 G^<_{-r}(t,T),
+//   Sigma^<_r = U(T)U(t) G^<_r(T,t)^2 G^>_{-r}(t,T),
+//   Sigma_k = sum_r e^{-i k.r} Sigma_r,  Sigma^R = Sigma^> - Sigma^<;
+// mixed: Sigma^tv_r = U(T)U(0_|) G^tv_r(T,tau)^2 G^vt_{-r}(tau,T).
+// The 2D transforms are done as two passes of L-point sums (rows, columns).
+// ---------------------------------------------------------------------------
+constexpr int kLatMaxK = 256;
+// in-place 2D DFT of a[N] (N = L*L, index m_x L + m_y) with sign sg (+1: e^{+i}),
+// scaled by sc; tw[m] = e^{2 pi i m / L}; every thread of the CTA must call it
+__device__ void lat_dft2(zd* a, zd* tmp, const zd* tw, int L, int sg, double sc) {
+  const int N = L * L, q = threadIdx.x;
+  const int x = q / L, y = q % L;
+  if (q < N) {  // along m_y: tmp[x][y] = sum_m a[x][m] e^{sg i 2pi m y / L}
+    zd s = zd();
+    for (int m = 0; m < L; ++m) {
+      const zd w = tw[(m * y) % L];
+      s += a[x * L + m] * (sg > 0 ? w : w.conj());
+    }
+    tmp[q] = s;
+  }
+  __syncthreads();
+  if (q < N) {  // along m_x
+    zd s = zd();
+    for (int m = 0; m < L; ++m) {
+      const zd w = tw[(m * x) % L];
+      s += tmp[m * L + y] * (sg > 0 ? w : w.conj());
+    }
+    a[q] = s * sc;
+  }
+  __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
+  __shared__ zd X1[kLatMaxK], X2[kLatMaxK], Y1[kLatMaxK], Y2[kLatMaxK], tmp[kLatMaxK], tw[16];
+  const int L = (int)d.mpar[0], N = L * L, q = threadIdx.x;
+  if (q < L) {
+    double sn, cs;
+    sincospi(2.0 * q / L, &sn, &cs);
+    tw[q] = zd(cs, sn);
+  }
+  const double* U = d.drU;   // U(t) of instance 0 (the same for every k)
+  const double invN = 1.0 / N;
+  const int b = blockIdx.x;
+  __syncthreads();
+  if (b <= T) {
+    const int t = b;
+    if (q < N) {
+      const zd gr = ld(el<1, S>(d.GR, d, q, T, t));
+      const zd glc = ld(el<1, S>(d.GL, d, q, T, t));     // G^<(t, T)
+      const zd glr = -glc.conj();                         // G^<(T, t)
+      const zd ggr = gr + glr;                            // G^>(T, t)
+      X1[q] = ggr; X2[q] = glr; Y1[q] = glc; Y2[q] = -ggr.conj();
+    }
+    __syncthreads();
+    lat_dft2(X1, tmp, tw, L, +1, invN);
+    lat_dft2(X2, tmp, tw, L, +1, invN);
+    lat_dft2(Y1, tmp, tw, L, -1, invN);
+    lat_dft2(Y2, tmp, tw, L, -1, invN);
+    const double uu = U[T + 1] * U[t + 1];
+    if (q < N) {
+      X1[q] = X1[q] * X1[q] * Y1[q] * uu;    // Sigma^>_r
+      X2[q] = X2[q] * X2[q] * Y2[q] * uu;    // Sigma^<_r
+    }
+    __syncthreads();
+    lat_dft2(X1, tmp, tw, L, -1, 1.0);
+    lat_dft2(X2, tmp, tw, L, -1, 1.0);
+    if (q < N) {
+      st(el<1, S>(d.SR, d, q, T, t), X1[q] - X2[q]);
+      st(el<1, S>(d.SL, d, q, T, t), -X2[q].conj());
+    }
+  } else {
+    const int i = b - (T + 1), r = d.r;
+    if (q < N) {
+      X1[q] = ld(tv<1>(d.GTV, d, q, T, i));
+      zd gb = zd();                                        // G^tv(T, beta - tau_i)
+      for (int c = 0; c < r; ++c) gb += ld(tv<1>(d.GTV, d, q, T, c)) * d.rev[i * r + c];
+      Y1[q] = gb.conj() * (-(double)d.xi);                 // G^vt(tau_i, T)
+    }
+    __syncthreads();
+    lat_dft2(X1, tmp, tw, L, +1, invN);
+    lat_dft2(Y1, tmp, tw, L, -1, invN);
+    if (q < N) X1[q] = X1[q] * X1[q] * Y1[q] * (U[T + 1] * U[0]);
+    __syncthreads();
+    lat_dft2(X1, tmp, tw, L, -1, 1.0);
+    if (q < N) st(tv<1>(d.STV, d, q, T, i), X1[q]);
+  }
+}
+
+// Lattice observables at time t (Sec. 4.2): n = -(i/N) sum_k G^<_k(t,t),
+// E_kin = -(2i/N) sum_k eps_k G^<_k(t,t), eps_k = -2(cos k_x + cos k_y),
+// j = -(2i/N) sum_k 2 sin(k_x - A(t)) G^<_k(t,t); out = (n, E_kin, j).
+template <typename S>
+__global__ void __launch_bounds__(kLatMaxK) k_lattice_obs(Dev d, int t, double* out) {
+  __shared__ double red[3][kLatMaxK];
+  const int L = (int)d.mpar[0], N = L * L, q = threadIdx.x;
+  double v[3] = {0, 0, 0};
+  if (q < N) {
+    const S* p = (!d.ring || t >= d.cdir) ? el<1, S>(d.GL, d, q, t, t) : Lf<1, S>(d, 1, q, t / d.L, t, t);
+    const double mi = (-ld(p) * zd(0, 1)).re;            // Re(-i G^<(t,t))
+    const double kx = 2.0 * M_PI * (q / L) / L, ky = 2.0 * M_PI * (q % L) / L;
+    const double A = d.drA[t + 1];
+    v[0] = mi / N;
+    v[1] = 2.0 * (-2.0 * (cos(kx) + cos(ky))) * mi / N;
+    v[2] = 2.0 * 2.0 * sin(kx - A) * mi / N;
+  }
+  for (int c = 0; c < 3; ++c) red[c][q] = v[c];
+  __syncthreads();
+  if (q == 0) {
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int e = 0; e < N; ++e) s += red[c][e];   // fixed order
+      out[c] = s;
+    }
+  }
+}
+
 #define HK_DISPATCH(NOV, CALL)                                                  \
   switch ((NOV) * 2 + d.prec) {                                                 \
     case 2: { constexpr int NO = 1; using S = double2; CALL; break; }           \
@@ -750,6 +874,18 @@ cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s) {
 }
 cudaError_t launch_density_at(const Dev& d, int t, double2* out, cudaStream_t s) {
   HK_DISPATCH(d.no, (k_density_at<NO, S><<<(d.n_inst * d.no * d.no + 127) / 128, 128, 0, s>>>(d, t, out)));
+  return cudaGetLastError();
+}
+cudaError_t launch_sigma_lattice(const Dev& d, int T, cudaStream_t s) {
+  if (d.no != 1 || d.n_inst > kLatMaxK) return cudaErrorInvalidValue;
+  if (d.prec) k_sigma_lattice<float2><<<T + 1 + d.r, kLatMaxK, 0, s>>>(d, T);
+  else k_sigma_lattice<double2><<<T + 1 + d.r, kLatMaxK, 0, s>>>(d, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_lattice_obs(const Dev& d, int t, double* out, cudaStream_t s) {
+  if (d.no != 1 || d.n_inst > kLatMaxK) return cudaErrorInvalidValue;
+  if (d.prec) k_lattice_obs<float2><<<1, kLatMaxK, 0, s>>>(d, t, out);
+  else k_lattice_obs<double2><<<1, kLatMaxK, 0, s>>>(d, t, out);
   return cudaGetLastError();
 }
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s) {

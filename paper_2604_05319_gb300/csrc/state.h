@@ -96,6 +96,8 @@ cudaError_t launch_les_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_src_h(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s);
 cudaError_t launch_density_at(const Dev& d, int t, double2* out, cudaStream_t s);  // rho(t), every instance
+cudaError_t launch_sigma_lattice(const Dev& d, int T, cudaStream_t s);   // model 4, all k at once
+cudaError_t launch_lattice_obs(const Dev& d, int t, double* out, cudaStream_t s);
 cudaError_t launch_row_out(const Dev& d, int n, int T, double2* out_r, double2* out_l, cudaStream_t s);
 // inverses of the frozen chunks [c0, c1) of sweep `which` (0 retarded, 1 lesser)
 cudaError_t launch_chunk_inv(const Dev& d, int which, int c0, int c1, cudaStream_t s);
