@@ -53,6 +53,12 @@ WORKLOADS = {
     "C2": dict(desc="C2: Bethe lattice, beta=5, N_t=4096, h=0.02, order 5, quench eps0 0->1 at t=5, "
                     "HODLR leaf 64, eps_SVD 1e-8, one instance",
                make=lambda n_inst, seed=0: wk.c2_workload(n_inst=n_inst), n_inst=1, precision="fp64"),
+    "C3": dict(desc="C3-shaped: 2D Hubbard second Born on a 16 x 16 k-grid (256 coupled instances), J=1, "
+                    "half filling, beta=10, N_t=2048, h=0.02, order 5, interaction quenched 0 -> U=2 at t=0 "
+                    "(the free lattice as initial state), undriven, HODLR leaf 64, eps_SVD 1e-6",
+               make=lambda n_inst, seed=0: wk.lattice_workload(L=16, nt=2048, h=0.02, k=5, beta=10.0, U=2.0,
+                                                                t_quench=0.0, svd_tol=1e-6, leaf=64),
+               n_inst=256, precision="mixed"),
     "C1": dict(desc="C1: Bethe lattice, beta=5, N_t=256, h=0.025, order 5, undriven, dense storage",
                make=lambda n_inst, seed=0: wk.c1_workload(seed=seed, n_inst=n_inst), n_inst=1, precision="fp64"),
 }
@@ -144,9 +150,27 @@ class ClockSampler:
 
 def oracle_sample(spec, seconds=15.0, seed=0):
     """Time the FP64 oracle stepping instance 0 of the workload on the host
-    for about `seconds` (from the bootstrap: the early, cheapest steps)."""
-    from oracle.kbe import from_workload
+    for about `seconds` (from the bootstrap: the early, cheapest steps).  For
+    the lattice the sample is all k-points (they are coupled), on a grid of
+    64 time steps; the rate is counted in instance time steps."""
     w = spec["make"](n_inst=1, seed=seed)
+    if w["wl"].model == "lattice2b":
+        from oracle.lattice import LatticeOracle
+        wl = w["wl"]
+        nts = 64
+        o = LatticeOracle(w["L"], nts, wl.h, wl.k, wl.beta, w["eps"][:, :nts + 1], w["gm"], w["tau"], w["omega"],
+                          w["drive_U"][0][:nts + 1], tol=wl.tol)
+        o.bootstrap()
+        t0 = time.perf_counter()
+        steps, T = 0, wl.k
+        for T in range(wl.k + 1, nts):
+            o.step(T)
+            steps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        dt = time.perf_counter() - t0
+        return steps * len(o.orcs) / dt, steps, dt, T
+    from oracle.kbe import from_workload
     o = from_workload(w)
     o.bootstrap()
     k, nt = w["wl"].k, w["wl"].nt
@@ -217,6 +241,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n_inst = args.n_inst or spec["n_inst"]
+    if args.workload == "C3" and n_inst != 256:
+        raise SystemExit("C3 has one instance per k-point of its 16 x 16 grid: --n-inst must be 256")
     prec_name = args.precision or spec["precision"]
     prec = pk.PREC_MIXED if prec_name == "mixed" else pk.PREC_FP64
     w = spec["make"](n_inst=n_inst, seed=1000 * rank)   # each rank its own instances
@@ -230,6 +256,8 @@ def main():
                     max_iter=wl.max_iter, tol=tol, precision=prec, svd_tol=wl.svd_tol, leaf=wl.leaf, r_max=64)
     mid, mp = pk.model_params_for(w)
     st.set_inputs(w["tau"], w["omega"], w["gm"], w["eps"], mid, mp)
+    if "drive_U" in w:
+        pk.hkbe_set_drive(st.h, w["drive_A"], w["drive_U"])
     st.bootstrap()
     # ---- untimed propagation (at least `warmup` time steps) ----
     t_prop0 = time.perf_counter()

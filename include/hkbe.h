@@ -133,7 +133,11 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
  *       params[0] = nb (1..4 bath levels), params[1..nb] = eps_b,
  *       then V[N_o][nb] complex interleaved (Sigma = V g_b V^dagger).
  *   HKBE_MODEL_NAMBU: N_o = 2 (Nambu spinor (d_up, d_dn^dagger), Sec. 4.1),
- *       nparams >= 1, params[0] = v (hopping scale, Delta carries v^2).
+ *       nparams 1 or 3: params[0] = v (hopping scale, Delta carries v^2),
+ *       params[1] = g, params[2] = w0 (optional Holstein coupling: the
+ *       unrenormalised Migdal Sigma^≷ += i g^2 D0^≷ sigma_z G^≷ sigma_z with
+ *       the free phonon propagator of frequency w0 at beta; the paper names
+ *       this approximation without printing it).
  *       Sigma = Delta + Sigma^2B with, element by element and s = (1, -1),
  *       Delta_ij(t,t') = v^2 s_i s_j G_ij(t,t') cos(s_i A(t) - s_j A(t'))
  *       (Eq. Hybrid, Peierls phases diag(e^{iA}, e^{-iA})), the bubble and

@@ -224,26 +224,30 @@ def nambu_drive(nt, h, A0=0.0, Omega=1.0, tc=2.0, width=1.0, U=0.0, U_eq=0.0, t_
 
 def nambu_workload(nt=200, h=0.02, k=5, beta=5.0, n_inst=1, v=1.0, eps0=0.0, pairing=0.0,
                    U=0.0, t_quench=0.0, A0=0.0, Omega=1.0, tc=2.0, width=1.0,
-                   dlr_lambda=100.0, dlr_eps=1e-10, tol=1e-12, max_iter=50, rho_mode=0, seed=0):
+                   dlr_lambda=100.0, dlr_eps=1e-10, tol=1e-12, max_iter=50, rho_mode=0, seed=0,
+                   g=0.0, w0=0.6):
     """Nambu (2 x 2) Bethe-lattice DMFT impurity (Sec. 4.1): level matrix
     eps = [[eps0, pairing], [pairing, -eps0]], hopping scale v, Peierls drive
     A(t) and an interaction quench U_eq = 0 -> U at t_quench (so the initial
     state is non-interacting and its G^M is known in closed form):
       v != 0, pairing = 0: G^M = diag(semicircle(eps0), semicircle(-eps0));
       v = 0:               G^M of the free 2 x 2 level (any pairing).
-    Per instance i > 0 the interaction is U * (1 + 0.25 i) (distinct instances)."""
+    Per instance i > 0 the interaction is U * (1 + 0.25 i) (distinct instances).
+    g, w0: optional Holstein coupling and phonon frequency (model parameters
+    [v, g, w0]; with g != 0 the closed-form G^M is only a start, not the
+    coupled equilibrium)."""
     if v != 0.0 and pairing != 0.0:
         raise ValueError("closed-form initial state needs pairing = 0 when v != 0")
     tau, om = dlr_grid(dlr_lambda, dlr_eps, beta)
     em = np.array([[eps0, pairing], [pairing, -eps0]], dtype=complex)
     eps = np.broadcast_to(em, (n_inst, nt + 1, 2, 2)).astype(complex).copy()
     if v != 0.0:
-        g = np.zeros((len(tau), 2, 2), complex)
-        g[:, 0, 0] = semicircle_gm(tau, beta, eps0, v)
-        g[:, 1, 1] = semicircle_gm(tau, beta, -eps0, v)
+        g0 = np.zeros((len(tau), 2, 2), complex)
+        g0[:, 0, 0] = semicircle_gm(tau, beta, eps0, v)
+        g0[:, 1, 1] = semicircle_gm(tau, beta, -eps0, v)
     else:
-        g = free_level_gm(tau, beta, em)
-    gm = np.broadcast_to(g, (n_inst,) + g.shape).astype(complex).copy()
+        g0 = free_level_gm(tau, beta, em)
+    gm = np.broadcast_to(g0, (n_inst,) + g0.shape).astype(complex).copy()
     As, Us = [], []
     for i in range(n_inst):
         A, Uv = nambu_drive(nt, h, A0, Omega, tc, width, U * (1.0 + 0.25 * i), 0.0, t_quench)
@@ -251,9 +255,11 @@ def nambu_workload(nt=200, h=0.02, k=5, beta=5.0, n_inst=1, v=1.0, eps0=0.0, pai
         Us.append(Uv)
     wl = Workload(name="nambu", model="nambu", nt=nt, h=h, k=k, beta=beta, nao=2, n_inst=n_inst,
                   dlr_lambda=dlr_lambda, dlr_eps=dlr_eps, svd_tol=0.0, leaf=64, tol=tol,
-                  max_iter=max_iter, seed=seed, rho_mode=rho_mode, params={"v": v})
+                  max_iter=max_iter, seed=seed, rho_mode=rho_mode,
+                  params={"v": v, "g": g, "w0": w0} if g else {"v": v})
+    mp = np.array([[v, g, w0]] * n_inst) if g else np.array([[v]] * n_inst)
     return {"wl": wl, "tau": tau, "omega": om, "eps": eps, "gm": gm,
-            "model_params": np.array([[v]] * n_inst), "drive_A": np.array(As), "drive_U": np.array(Us)}
+            "model_params": mp, "drive_A": np.array(As), "drive_U": np.array(Us)}
 
 
 def lattice_workload(L=4, nt=120, h=0.02, k=5, beta=10.0, U=2.0, t_quench=0.0, A0=0.0, Omega=1.0,

@@ -103,7 +103,16 @@ class Nambu(Model):
     t <= T.  The mixed part uses G^tv(T, tau) and G^vt(tau, T) the same way
     (the imaginary branch is latest on the contour).  The Fock term
     Sigma^F_ij(t) = -U(t) rho_ij(t) [i = bar j] is time-local: it is added to
-    the external eps(t) every time Sigma is evaluated."""
+    the external eps(t) every time Sigma is evaluated.
+
+    Optional Holstein coupling (params g, w0; the C4 configuration): the
+    unrenormalised Migdal self-energy Sigma^≷(t,t') = i g^2 D0^≷(t,t')
+    sigma_z G^≷(t,t') sigma_z with the free phonon propagator
+    D0^>(t,t') = -i[(n_B+1) e^{-i w0 (t-t')} + n_B e^{i w0 (t-t')}],
+    D0^<(t,t') = D0^>(t',t), n_B = 1/(e^{beta w0} - 1), and on the mixed
+    branch D0^tv(t,tau) = -i[(n_B+1) e^{i w0 t - w0 tau} + n_B e^{-i w0 t + w0 tau}].
+    The paper names this approximation but prints no formula for it: parity
+    unpinned (only its g = 0 limit is pinned)."""
     name = "nambu"
     self_consistent = True
 
@@ -133,6 +142,20 @@ class Nambu(Model):
         Gvt = st.gvt(T)                           # G^vt(tau_i, T)
         ph0 = np.cos(s[:, None] * A[T + 1] - s[None, :] * A[0])
         st.STV[T] = U[T + 1] * U[0] * _bar_products(Gtv, Gvt) + v2 * ss * Gtv * ph0
+        g = float(self.params.get("g", 0.0))
+        if g != 0.0:
+            w0 = float(self.params["w0"])
+            nb = 1.0 / np.expm1(st.beta * w0)
+            dt = (T - np.arange(T + 1)) * st.h                  # t_T - t
+            dg = -1j * ((nb + 1) * np.exp(-1j * w0 * dt) + nb * np.exp(1j * w0 * dt))   # D0^>(T, t)
+            dl = -1j * ((nb + 1) * np.exp(1j * w0 * dt) + nb * np.exp(-1j * w0 * dt))   # D0^<(T, t)
+            sg = 1j * g * g * dg[:, None, None] * ss * GGr
+            sl = 1j * g * g * dl[:, None, None] * ss * GLr
+            st.SR[T, :T + 1] += sg - sl
+            st.SLs[T, :T + 1] += -dag(sl)
+            tT = T * st.h
+            dtv = -1j * ((nb + 1) * np.exp(1j * w0 * tT - w0 * st.tau) + nb * np.exp(-1j * w0 * tT + w0 * st.tau))
+            st.STV[T] += 1j * g * g * dtv[:, None, None] * ss * Gtv
         rho = st.rho(T)
         sf = np.zeros((2, 2), complex)
         sf[0, 1] = -U[T + 1] * rho[0, 1]

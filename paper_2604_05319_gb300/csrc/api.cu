@@ -520,8 +520,13 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
     h->self_consistent = true;
   } else if (model == HKBE_MODEL_NAMBU) {
     if (no != 2) return fail(h, HKBE_ERR_ARG, "NAMBU needs nao = 2");
-    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "NAMBU needs params[0] = v");
-    for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = params[(size_t)n * nparams];
+    if (!params || (nparams != 1 && nparams != 3)) return fail(h, HKBE_ERR_ARG, "NAMBU needs params [v] or [v, g, w0]");
+    for (int n = 0; n < d.n_inst; ++n)
+      for (int c = 0; c < nparams; ++c) mp[(size_t)n * hk::MP + c] = params[(size_t)n * nparams + c];
+    if (nparams == 3)
+      for (int n = 0; n < d.n_inst; ++n)
+        if (mp[(size_t)n * hk::MP + 1] != 0.0 && !(mp[(size_t)n * hk::MP + 2] > 0.0))
+          return fail(h, HKBE_ERR_ARG, "NAMBU phonon frequency w0 must be > 0");
     h->self_consistent = true;
   } else {
     return fail(h, HKBE_ERR_ARG, "unknown model");

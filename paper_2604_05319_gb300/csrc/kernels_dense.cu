@@ -97,6 +97,17 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
     const double uu = U[T + 1] * U[t + 1];
     nambu_bar(GGr, GLc, uu, Sg);
     nambu_bar(GLr, GGc, uu, Sl);
+    // optional Holstein coupling (unrenormalised Migdal, free phonon of w0):
+    // Sigma^≷ += i g^2 D0^≷(T,t) s_i s_j G^≷_ij(T,t)
+    const double g = mp[1], w0 = mp[2];
+    zd dg = zd(), dl = zd();
+    if (g != 0.0) {
+      const double nb = 1.0 / expm1(d.beta * w0), x = w0 * (T - t) * d.h;
+      double sx, cx;
+      sincos(x, &sx, &cx);
+      dg = zd(0, -1) * (zd(cx, -sx) * (nb + 1.0) + zd(cx, sx) * nb) * zd(0, g * g);
+      dl = zd(0, -1) * (zd(cx, sx) * (nb + 1.0) + zd(cx, -sx) * nb) * zd(0, g * g);
+    }
     S* sr = el<2, S>(d.SR, d, n, T, t);
     zd slr[4];
 #pragma unroll
@@ -104,8 +115,10 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const double w = v2 * s[i] * s[j] * cos(s[i] * A[T + 1] - s[j] * A[t + 1]);
-        st(sr + i * 2 + j, Sg[i * 2 + j] - Sl[i * 2 + j] + GR[i * 2 + j] * w);
-        slr[i * 2 + j] = Sl[i * 2 + j] + GLr[i * 2 + j] * w;                    // Sigma^<(T, t)
+        const double ssij = s[i] * s[j];
+        const zd mg = dg * GGr[i * 2 + j] * ssij, ml = dl * GLr[i * 2 + j] * ssij;
+        st(sr + i * 2 + j, Sg[i * 2 + j] - Sl[i * 2 + j] + GR[i * 2 + j] * w + mg - ml);
+        slr[i * 2 + j] = Sl[i * 2 + j] + GLr[i * 2 + j] * w + ml;               // Sigma^<(T, t)
       }
     S* sl = el<2, S>(d.SL, d, n, T, t);                                         // stores Sigma^<(t, T)
 #pragma unroll
@@ -139,12 +152,21 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
 #pragma unroll
       for (int y = 0; y < 2; ++y) Gvt[x * 2 + y] = gb[y * 2 + x].conj() * (-(double)d.xi);  // G^vt(tau_i, T)
     nambu_bar(Gtv, Gvt, U[T + 1] * U[0], Sb);
+    const double g = mp[1], w0 = mp[2];
+    zd dtv = zd();
+    if (g != 0.0) {  // i g^2 D0^tv(T, tau_i)
+      const double nb = 1.0 / expm1(d.beta * w0), tT = T * d.h, ta = d.tau[i];
+      double sx, cx;
+      sincos(w0 * tT, &sx, &cx);
+      dtv = zd(0, -1) * (zd(cx, sx) * ((nb + 1.0) * exp(-w0 * ta)) + zd(cx, -sx) * (nb * exp(w0 * ta))) * zd(0, g * g);
+    }
     double2* so = tv<2>(d.STV, d, n, T, i);
 #pragma unroll
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int y = 0; y < 2; ++y)
-        st(so + x * 2 + y, Sb[x * 2 + y] + Gtv[x * 2 + y] * (v2 * s[x] * s[y] * cos(s[x] * A[T + 1] - s[y] * A[0])));
+        st(so + x * 2 + y, Sb[x * 2 + y] + Gtv[x * 2 + y] * (v2 * s[x] * s[y] * cos(s[x] * A[T + 1] - s[y] * A[0])) +
+                               dtv * Gtv[x * 2 + y] * (s[x] * s[y]));
   }
 }
 

@@ -95,3 +95,19 @@ def test_nambu_batch_distinct_u():
     st = _run(w)
     for i, o in enumerate(orc):
         assert _err(st, o, i)[1] < 1e-10, i
+
+
+@pytest.mark.parametrize("prec", [pk.PREC_FP64, pk.PREC_MIXED])
+def test_nambu_holstein_migdal(prec):
+    """The optional Holstein term (C4's g = 0.5, w0 = 0.6) on top of the
+    hybridisation and a pulse: GPU vs oracle."""
+    key = ("migdal",)
+    if key not in _CACHE:
+        w = wk.nambu_workload(nt=160, h=0.02, k=5, beta=BETA, v=1.0, eps0=0.1, A0=0.5, Omega=1.0, tc=1.5,
+                              width=0.5, g=0.5, w0=0.6)
+        o = from_workload(w, tol=1e-14)
+        o.run()
+        _CACHE[key] = (w, o)
+    w, o = _CACHE[key]
+    st = _run(w, tol=1e-13 if prec == pk.PREC_FP64 else 1e-7, precision=prec)
+    assert _err(st, o)[1] < (1e-10 if prec == pk.PREC_FP64 else 1e-6)

@@ -118,3 +118,15 @@ def test_fock_term_enters_eps_with_pairing():
     assert abs(rho[0, 1]) > 1e-2
     assert np.allclose(o.eps[T + 1][0, 1], 0.3 - 0.8 * rho[0, 1], atol=1e-12)
     assert np.allclose(o.eps[T + 1][0, 0], 0.1, atol=1e-15)
+
+
+def test_holstein_term_g0_limit_and_effect():
+    """g = 0 reproduces the plain model bit for bit; g = 0.5 changes it."""
+    kw = dict(nt=40, h=0.05, k=4, beta=BETA, v=1.0, eps0=0.1, A0=0.3, Omega=1.0, tc=1.0, width=0.5)
+    a = from_workload(wk.nambu_workload(**kw), tol=1e-13).run()
+    w0 = wk.nambu_workload(**kw)
+    w0["wl"].params.update({"g": 0.0, "w0": 0.6})
+    b = from_workload(w0, tol=1e-13).run()
+    assert np.array_equal(a.GR, b.GR) and np.array_equal(a.GLs, b.GLs)
+    c = from_workload(wk.nambu_workload(g=0.5, w0=0.6, **kw), tol=1e-13).run()
+    assert np.abs(c.GLs[-1, :, 0, 0] - a.GLs[-1, :, 0, 0]).max() > 1e-3
