@@ -45,7 +45,27 @@ def _batch_c2(n_inst, seed=0, nt=4096):
     return w
 
 
+def _batch_c4(n_inst, seed=0, nt=8192):
+    """C4-shaped batch: Nambu Bethe DMFT with the Holstein-Migdal term (g=0.5,
+    w0=0.6), beta=50, N_t=8192, h=0.01, pulse A(t) = A0 sin(t) exp(-(t-20)^2/50)
+    with A0 = 0.3 for instance 0 and A0 ~ 0.3 U[0.5, 1.5] for the others,
+    HODLR leaf 64, eps_SVD 1e-7.  Initial state: the normal non-interacting
+    Bethe lattice (closed-form G^M), not the coupled superconducting
+    equilibrium (no Matsubara solver here)."""
+    w = wk.nambu_workload(nt=nt, h=0.01, k=5, beta=50.0, n_inst=n_inst, v=1.0, eps0=0.0, A0=0.3, Omega=1.0,
+                          tc=20.0, width=50.0, g=0.5, w0=0.6, dlr_lambda=200.0, dlr_eps=1e-10)
+    amp = np.concatenate([[1.0], np.random.default_rng(seed).uniform(0.5, 1.5, size=n_inst - 1)])
+    w["drive_A"] = w["drive_A"] * amp[:, None]
+    w["wl"].svd_tol = 1e-7
+    return w
+
+
 WORKLOADS = {
+    "C4-batch": dict(desc="C4-shaped: Nambu Bethe-lattice DMFT, hybridisation with Peierls phases + Holstein-Migdal "
+                          "(g=0.5, w0=0.6), beta=50, N_t=8192, h=0.01, order 5, DLR Lambda=200 eps=1e-10, pulse "
+                          "A(t)=A0 sin(t) exp(-(t-20)^2/50) (A0=0.3 instance 0, 0.3 U[0.5,1.5] others), HODLR "
+                          "leaf 64, eps_SVD 1e-7, normal non-interacting initial state",
+                     make=_batch_c4, n_inst=76, precision="mixed"),
     "C2-batch": dict(desc="Bethe lattice (Sigma=v^2 G, v=1), beta=5, N_t=4096, h=0.02, order 5, DLR Lambda=100 "
                           "eps=1e-10, level quench 0 -> A at t=5 (A=1 for instance 0, U[0.5,1.5] for the others), "
                           "HODLR leaf 64, eps_SVD 1e-8, r_max 64",
