@@ -121,6 +121,7 @@ class KBEOracle:
         e_eq = self.eps[0]
         E, U = np.linalg.eigh(0.5 * (e_eq + _dag(e_eq)))
         rhoM = -np.einsum("c,cxy->xy", self.ebeta, self.gm)
+        g0 = 1j * self.xi * np.einsum("bc,cxy->bxy", self.Rev, self.gm)
 
         def ex(f):
             return (U * f[None, :]) @ _dag(U)
@@ -129,8 +130,10 @@ class KBEOracle:
                 self.GR[t, tp] = -1j * ex(np.exp(-1j * E * (t - tp) * h))
             for tp in range(t + 1):   # GLs[t, tp] = G^<(tp, t)
                 self.GLs[t, tp] = 1j * ex(np.exp(-1j * E * tp * h)) @ rhoM @ ex(np.exp(1j * E * t * h))
-            for i, ti in enumerate(self.tau):
-                self.GTV[t, i] = -self.xi * 1j * ex(np.exp(-1j * E * t * h)) @ rhoM @ ex(np.exp(E * ti))
+            # G^tv(t, tau) = e^{-i eps t} G^tv(0, tau), started from the exact
+            # G^tv(0, tau) = i xi G^M(beta - tau) (the same as the mean-field form
+            # -xi i rho e^{eps tau} when G^M is that of eps; far better when not)
+            self.GTV[t] = np.einsum("xy,iyz->ixz", ex(np.exp(-1j * E * t * h)), g0)
 
     # ---- bootstrap -------------------------------------------------------
     def _boot_mixed(self):

@@ -593,17 +593,27 @@ static int hf_guess(hkbe_t* h) {
           gl[(off * n2 + q) * 2] = v.real(); gl[(off * n2 + q) * 2 + 1] = v.imag();
         }
       }
+    // G^tv(t, tau) = e^{-i e t} G^tv(0, tau) from the exact G^tv(0, tau_i) =
+    // i xi G^M(beta - tau_i) (the mean-field form -xi i rho e^{e tau} when G^M
+    // is that of e; far closer when G^M is an interacting equilibrium)
+    std::vector<zc> g0((size_t)r * n2);
+    for (int i = 0; i < r; ++i)
+      for (int q = 0; q < n2; ++q) {
+        zc sacc = 0;
+        for (int c = 0; c < r; ++c) {
+          const double* g = &h->gm_host[(((size_t)n * r + c) * n2 + q) * 2];
+          sacc += h->dm.rev[(size_t)i * r + c] * zc(g[0], g[1]);
+        }
+        g0[(size_t)i * n2 + q] = zc(0, (double)d.xi) * sacc;
+      }
     for (int t = 0; t <= k; ++t)
       for (int i = 0; i < r; ++i) {
-        zc B[16], C[16], D[16];
+        zc B[16], D[16];
         fun([&](double ee) { return std::exp(zc(0, -ee * t * hh)); }, B);
-        fun([&](double ee) { return std::exp(ee * h->tau[i]); }, C);
-        mm(B, rho, D);
-        mm(D, C, B);
+        mm(B, &g0[(size_t)i * n2], D);
         for (int q = 0; q < n2; ++q) {
-          zc v = zc(0, -(double)d.xi) * B[q];
-          gtv[(((size_t)t * r + i) * n2 + q) * 2] = v.real();
-          gtv[(((size_t)t * r + i) * n2 + q) * 2 + 1] = v.imag();
+          gtv[(((size_t)t * r + i) * n2 + q) * 2] = D[q].real();
+          gtv[(((size_t)t * r + i) * n2 + q) * 2 + 1] = D[q].imag();
         }
       }
     const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2;

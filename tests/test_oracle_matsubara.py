@@ -79,10 +79,11 @@ def test_interacting_equilibrium_is_stationary(mo):
     model = make_model("nambu", {"v": 1.0, "A": A, "U": U, "g": 0.4, "w0": 0.8})
     o = KBEOracle(nt, h, k, BETA, eps, G[0], mo.tau, mo.om, model, tol=1e-13)
     o.run()
+    assert np.isfinite(o.GR).all() and np.isfinite(o.GLs).all()
     dev = 0.0
     for d in range(1, 30):
         vals = np.array([o.GR[t + d, t] for t in range(nt - d)])
-        dev = max(dev, np.abs(vals - vals[0]).max())
+        dev = max(dev, float(np.abs(vals - vals[0]).max()))
     assert dev < 1e-5, dev
     rho = np.array([o.rho(t) for t in range(nt)])
     assert np.abs(rho - rho[0]).max() < 1e-5
@@ -105,7 +106,8 @@ def test_lattice_interacting_equilibrium_is_stationary():
     dev = 0.0
     for q in (0, 5):
         gr = o.orcs[q].GR[..., 0, 0]
+        assert np.isfinite(gr).all() and np.isfinite(o.orcs[q].GLs).all()
         for d in range(1, 25):
             vals = np.array([gr[t + d, t] for t in range(nt - d)])
-            dev = max(dev, np.abs(vals - vals[0]).max())
-    assert dev < 1e-5, dev
+            dev = max(dev, float(np.abs(vals - vals[0]).max()))
+    assert dev < 1e-4, dev          # h = 0.05 on a band of width 8
