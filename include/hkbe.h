@@ -94,6 +94,32 @@ typedef struct hkbe_s hkbe_t;
  * Errors: HKBE_ERR_ARG (bad sizes), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
 int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out);
 
+/* Equilibrium Dyson equation on the DLR grid (Eq. KBEM, Sec. 2.5, 3.2),
+ * solved self-consistently on the host: prepares G^M of an interacting
+ * initial state for hkbe_set_matsubara.  No handle and no GPU needed.
+ *   r, tau[r], omega[r], beta: the DLR grid (as for hkbe_set_dlr);
+ *   model, params[n_inst][nparams]: as for hkbe_set_model (HKBE_MODEL_NONE,
+ *     BETHE, NAMBU with optional [v, g, w0], LATTICE2B with params[0] = L);
+ *   eps[n_inst][nao][nao] complex: the equilibrium-branch level eps(0_|);
+ *   U_eq: interaction on the equilibrium branch (second Born and Fock);
+ *   eta, n_eta: pairing field eta added to eps_01 and eps_10 for the first
+ *     n_eta iterations (symmetry breaking, Sec. 4.1); mix in (0, 1]: linear
+ *     mixing of successive iterates; tol, max_iter: stop when
+ *     max |G_new - G_old| < tol.
+ * Sigma^M follows from the real-time functionals restricted to the imaginary
+ * branch (G^M = -i G(-i tau, 0), Table 1): v^2 G (Bethe), v^2 s_z G s_z
+ * - U^2 [G G - G G](tau) G(-tau) + Holstein (Nambu), -U^2 G_r^2 G_{-r}(-tau)
+ * (lattice).  Dyson is imposed at r fermionic Matsubara frequencies chosen
+ * by pivoted Gram-Schmidt on the DLR Fourier rows 1/(i nu - omega_l).
+ * Outputs: gm_out[n_inst][r][nao][nao] complex, eps_out[n_inst][nao][nao]
+ * complex (eps with the converged Fock shift; may be NULL), iters, err (may
+ * be NULL).  Errors: HKBE_ERR_ARG, HKBE_ERR_NAN (singular or non-finite),
+ * HKBE_ERR_NOCONV (max_iter reached; outputs hold the last iterate). */
+int hkbe_matsubara_solve(int r, const double* tau, const double* omega, double beta, int model, int n_inst,
+                         int nao, const double* eps, const double* params, int nparams, double U_eq, double eta,
+                         int n_eta, double mix, double tol, int max_iter, double* gm_out, double* eps_out,
+                         int32_t* iters, double* err);
+
 /* Release every device and host resource of h (NULL is accepted). */
 int hkbe_destroy(hkbe_t* h);
 

@@ -71,6 +71,9 @@ def load(build_if_missing: bool = True):
         "hkbe_set_model": ([H, C.c_int, _D, C.c_int], C.c_int),
         "hkbe_set_drive": ([H, _D, _D], C.c_int),
         "hkbe_get_lattice_observables": ([H, C.c_int, _D], C.c_int),
+        "hkbe_matsubara_solve": ([C.c_int, _D, _D, C.c_double, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int,
+                                  C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
+                                  _I, _D], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
         "hkbe_current_step": ([H, _I], C.c_int),
@@ -218,6 +221,32 @@ def hkbe_set_drive(h, A=None, U=None):
     a = None if A is None else np.ascontiguousarray(np.asarray(A, dtype=np.float64))
     u = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.float64))
     _check(load().hkbe_set_drive(h, _dp(a) if a is not None else None, _dp(u) if u is not None else None), h)
+
+
+def hkbe_matsubara_solve(tau, omega, beta, model, eps, params=None, U_eq=0.0, eta=0.0, n_eta=0, mix=0.5,
+                         tol=1e-12, max_iter=500):
+    """Self-consistent equilibrium G^M on the DLR nodes (host, no handle).
+    eps: complex [n_inst, nao, nao]; params: [n_inst, nparams] or None.
+    Returns (G^M [n_inst, r, nao, nao], eps with the Fock shift, iterations,
+    final difference); raises HKBEError on failure or non-convergence."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128))
+    n_inst, nao = e.shape[0], e.shape[-1]
+    r = len(tau)
+    p = None if params is None else np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(n_inst, -1))
+    gm = np.zeros((n_inst, r, nao, nao), np.complex128)
+    eo = np.zeros((n_inst, nao, nao), np.complex128)
+    it = np.zeros(1, np.int32)
+    er = np.zeros(1)
+    rc = load().hkbe_matsubara_solve(r, _dp(tau), _dp(om), float(beta), int(model), n_inst, nao,
+                                     _dp(e.view(np.float64)), _dp(p) if p is not None else None,
+                                     0 if p is None else p.shape[1], float(U_eq), float(eta), int(n_eta),
+                                     float(mix), float(tol), int(max_iter), _dp(gm.view(np.float64)),
+                                     _dp(eo.view(np.float64)), _ip(it), _dp(er))
+    if rc != 0:
+        raise HKBEError(rc, f"hkbe_matsubara_solve failed (rc={rc}, iterations {int(it[0])}, diff {er[0]:.3e})")
+    return gm, eo, int(it[0]), float(er[0])
 
 
 def hkbe_get_lattice_observables(h, t):
