@@ -19,9 +19,15 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 """
 from __future__ import annotations
 
+import os
+
+# The CPU baseline is the single-threaded oracle: keep numpy's BLAS on one
+# thread (the GPU arm uses numpy only to build its inputs).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
