@@ -211,6 +211,22 @@ def oracle_sample(spec, seconds=15.0, seed=0):
     return steps / dt, steps, dt, T
 
 
+def rank_seed(rank):
+    """Seed of a rank's instances: every rank propagates its own batch
+    (weak scaling; the instances need no data-path communication)."""
+    return 1000 * rank
+
+
+def max_over_ranks(values, dist, device):
+    """Wall times of the timed regions, reduced to their maximum over ranks
+    (the job ends when its slowest rank does)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 METRIC = "KBE time steps/s"
 UNIT = "instance time steps/s"
 
@@ -271,7 +287,7 @@ def main():
         raise SystemExit("C3 has one instance per k-point of its 16 x 16 grid: --n-inst must be 256")
     prec_name = args.precision or spec["precision"]
     prec = pk.PREC_MIXED if prec_name == "mixed" else pk.PREC_FP64
-    w = spec["make"](n_inst=n_inst, seed=1000 * rank)   # each rank its own instances
+    w = spec["make"](n_inst=n_inst, seed=rank_seed(rank))   # each rank its own instances
     wl = w["wl"]
     nt, k, no, r = wl.nt, wl.k, wl.nao, len(w["tau"])
     hod = wl.svd_tol > 0
@@ -334,10 +350,7 @@ def main():
     pk.hkbe_set_profiling(st.h, False)
     prof = st.timing()
     launches = sum(v[1] for v in prof.values())
-    tt = torch.tensor([t_win, t_e2e], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_win, t_e2e = tt.tolist()
+    t_win, t_e2e = max_over_ranks([t_win, t_e2e], dist, "cuda")
     units = n_inst * K * world
     value = units / t_win
     # ---- roofline of the dominant history kernel over the window ----
