@@ -138,3 +138,28 @@ class LatticeOracle:
         vx = 2 * np.sin(kx[:, None] - np.asarray(A)[None, 1:self.nt + 1])
         j = (-2j / nk * (vx * gl).sum(0)).real
         return n, ekin, j
+
+    def interaction_energy(self):
+        """Correlation part of the interaction energy per site for t > k (NaN
+        for t <= k, where the start rules reach past t) (Galitskii-Migdal on
+        the contour, spin summed):
+            E_int(t) = -(i/N_k) sum_k (Sigma_k * G_k)^<(t, t),
+            (Sigma * G)^<(t, t) = int_0^t [Sigma^R(t,s) G^<(s,t) + Sigma^<(t,s) G^A(s,t)] ds
+                                  - i int_0^beta Sigma^tv(t,tau) G^vt(tau,t) dtau,
+        the time integrals with the scheme's rule w^(t) (Appendix A), the
+        imaginary-time one with the DLR product weights Q (zero after a quench
+        from U = 0, where Sigma^tv vanishes)."""
+        nk = len(self.orcs)
+        out = np.full(self.nt, np.nan)
+        for t in range(self.k + 1, self.nt):
+            acc = 0.0
+            for o in self.orcs:
+                wt = o.W.rule(t)[:t + 1]
+                sr = o.SR[t, :t + 1, 0, 0]
+                gl = o.GLs[t, :t + 1, 0, 0]              # G^<(s, t)
+                sl = -np.conj(o.SLs[t, :t + 1, 0, 0])    # Sigma^<(t, s)
+                ga = np.conj(o.GR[t, :t + 1, 0, 0])      # G^A(s, t)
+                acc += o.h * np.sum(wt * (sr * gl + sl * ga))
+                acc += -1j * np.einsum("a,ab,b->", o.STV[t, :, 0, 0], o.Q, o.gvt(t)[:, 0, 0])
+            out[t] = (-1j * acc / nk).real
+        return out

@@ -5,7 +5,10 @@
   U^2/N_k^2 sum_{k1,k2} G_{k1} G_{k2} G_{k1+k2-k} (brute force, 4 x 4);
 - with the drive along x the state keeps the k_y -> -k_y reflection symmetry;
 - the particle number per spin stays at 1/2 (half filling, conserving
-  approximation) to the discretisation error, in both density-matrix schemes.
+  approximation) to the discretisation error, in both density-matrix schemes;
+- after an interaction quench the total energy E_kin + E_int (Galitskii-
+  Migdal) is conserved to the discretisation error, converging at order 5,
+  while E_kin itself changes; the opposite sign of E_int would drift.
 """
 import numpy as np
 import pytest
@@ -91,3 +94,19 @@ def test_reflection_symmetry_and_half_filling(rho_mode):
     # conserved to the discretisation error (h = 0.05, a steep pulse and a quench of U)
     assert np.abs(n - 0.5).max() < 5e-3
     assert np.abs(j).max() > 1e-3            # the pulse drives a current
+
+
+def test_energy_conserved_after_quench():
+    drift = []
+    for nt, h in [(40, 0.05), (80, 0.025)]:
+        w = wk.lattice_workload(L=4, nt=nt, h=h, k=5, beta=10.0, U=1.0, t_quench=0.5)
+        o = _make(w).run()
+        n, ekin, j = o.observables(w["drive_A"][0])
+        eint = o.interaction_energy()
+        i0 = int(round(0.8 / h))
+        E = ekin + eint
+        drift.append(np.abs(E[i0:] - E[i0]).max())
+        assert np.abs(ekin[i0:] - ekin[i0]).max() > 1e-2            # energy moves between the parts
+        assert np.abs((ekin - eint)[i0:] - (ekin - eint)[i0]).max() > 1e-2
+    assert drift[1] < 5e-5
+    assert drift[0] / drift[1] > 2 ** 4
