@@ -45,3 +45,45 @@ def bethe(eps_of_t, h, nt, beta, eps_eq, v=1.0, nquad=4000):
     f = _fermi(eps_eq + xx, beta)
     GL = 1j * phase * np.einsum("q,q,tsq->ts", wq, f, np.exp(-1j * xx[None, None, :] * d[:, :, None]))
     return GR, GL
+
+
+
+def nambu_site(eps, delta, beta, ts, taus, U=0.0, g=0.0, w0=1.0, nph=16):
+    """One site with level eps, pairing field delta, a Hubbard term and a
+    Holstein phonon,
+        H = eps (n - 1) + delta (c_up^+ c_dn^+ + c_dn c_up) + U (n_up - 1/2)(n_dn - 1/2)
+            + w0 b^+ b + g (b + b^+)(n - 1),
+    solved by exact diagonalisation in the Fock space of the two spins times
+    nph phonon states (one state when g = 0).  With the Nambu spinor
+    psi = (c_up, c_dn^+) it returns G^R(t, 0), G^<(t, 0) on ts and G^M(tau)
+    on taus, each (len, 2, 2):
+        G^>_ij(t) = -i <psi_i(t) psi_j^+>,  G^<_ij(t) = i <psi_j^+ psi_i(t)>,
+        G^M_ij(tau) = -<psi_i(tau) psi_j^+>  (0 < tau < beta)."""
+    if g == 0.0:
+        nph = 1
+    a = np.array([[0.0, 1.0], [0.0, 0.0]])
+    cu = np.kron(a, np.eye(2))
+    cd = np.kron(np.diag([1.0, -1.0]), a)          # Jordan-Wigner sign
+    nu, nd = cu.T @ cu, cd.T @ cd
+    n1 = nu + nd - np.eye(4)
+    He = eps * n1 + delta * (cu.T @ cd.T + cd @ cu) + U * (nu - 0.5 * np.eye(4)) @ (nd - 0.5 * np.eye(4))
+    b = np.diag(np.sqrt(np.arange(1.0, nph)), 1)
+    H = np.kron(He, np.eye(nph)) + w0 * np.kron(np.eye(4), b.T @ b) + g * np.kron(n1, b + b.T)
+    E, V = np.linalg.eigh(H)
+    E = E - E.min()
+    P = [V.T @ np.kron(cu, np.eye(nph)) @ V, V.T @ np.kron(cd.T, np.eye(nph)) @ V]
+    w = np.exp(-beta * E)
+    w = w / w.sum()
+    def corr(wgt, ph):                             # sum_mn wgt_mn ph_mn P_i[m,n] P_j[m,n]^*
+        return np.array([[np.sum(wgt * ph * P[i] * P[j].conj()) for j in range(2)] for i in range(2)])
+    dE = E[:, None] - E[None, :]
+    GR, GL = [], []
+    for t in ts:
+        ph = np.exp(1j * t * dE)
+        gg = -1j * corr(w[:, None], ph)
+        gl = 1j * corr(w[None, :], ph)
+        GR.append(gg - gl)
+        GL.append(gl)
+    Z = np.exp(-beta * E).sum()
+    GM = [-corr(np.exp(-(beta - s) * E[:, None] - s * E[None, :]) / Z, 1.0).real for s in taus]
+    return np.array(GR), np.array(GL), np.array(GM)
