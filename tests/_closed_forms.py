@@ -87,3 +87,52 @@ def nambu_site(eps, delta, beta, ts, taus, U=0.0, g=0.0, w0=1.0, nph=16):
     Z = np.exp(-beta * E).sum()
     GM = [-corr(np.exp(-(beta - s) * E[:, None] - s * E[None, :]) / Z, 1.0).real for s in taus]
     return np.array(GR), np.array(GL), np.array(GM)
+
+
+def hubbard_cluster(L, U, beta, ts, taus):
+    """The L x L periodic Hubbard cluster (L = 2: 8 spin orbitals, 256 states),
+        H = -sum_<ij>,s c_is^+ c_js + U sum_i (n_i,up - 1/2)(n_i,dn - 1/2),
+    the hopping summed over the four neighbour directions with wrap-around,
+    solved by exact diagonalisation.  Returns, per k = 2 pi (m_x, m_y) / L
+    (index m_x L + m_y) and for spin up, G^R_k(t, 0), G^<_k(t, 0) on ts and
+    G^M_k(tau) on taus, with c_k = N^{-1/2} sum_i e^{-i k.r_i} c_i."""
+    ns = L * L
+    nm = 2 * ns                                    # mode 2 i + s: site i, spin s
+    a = np.array([[0.0, 1.0], [0.0, 0.0]])
+    z = np.diag([1.0, -1.0])
+    c = []
+    for m in range(nm):                            # Jordan-Wigner
+        op = np.ones((1, 1))
+        for q in range(nm):
+            op = np.kron(op, z if q < m else (a if q == m else np.eye(2)))
+        c.append(op)
+    xy = [(i // L, i % L) for i in range(ns)]
+    dim = 2 ** nm
+    H = np.zeros((dim, dim))
+    for i, (x, y) in enumerate(xy):
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            j = ((x + dx) % L) * L + (y + dy) % L
+            for s in range(2):
+                H -= c[2 * i + s].T @ c[2 * j + s]
+    for i in range(ns):
+        H += U * (c[2 * i].T @ c[2 * i] - 0.5 * np.eye(dim)) @ (c[2 * i + 1].T @ c[2 * i + 1] - 0.5 * np.eye(dim))
+    E, V = np.linalg.eigh(H)
+    E = E - E.min()
+    w = np.exp(-beta * E)
+    Z = w.sum()
+    dE = E[:, None] - E[None, :]
+    GR = np.zeros((ns, len(ts)), complex)
+    GL = np.zeros((ns, len(ts)), complex)
+    GM = np.zeros((ns, len(taus)))
+    for q in range(ns):
+        kx, ky = 2 * np.pi * np.array(xy[q]) / L
+        ck = sum(np.exp(-1j * (kx * x + ky * y)) * c[2 * i] for i, (x, y) in enumerate(xy)) / np.sqrt(ns)
+        A = np.abs(V.T @ ck @ V) ** 2              # |<m| c_k |n>|^2
+        for n, t in enumerate(ts):
+            ph = np.exp(1j * t * dE)
+            gl = 1j * np.sum(w[None, :] * ph * A) / Z
+            GR[q, n] = -1j * np.sum(w[:, None] * ph * A) / Z - gl
+            GL[q, n] = gl
+        for n, s in enumerate(taus):
+            GM[q, n] = -np.sum(np.exp(-(beta - s) * E[:, None] - s * E[None, :]) * A) / Z
+    return GR, GL, GM
