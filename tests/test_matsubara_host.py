@@ -1,12 +1,15 @@
 """The library's host Matsubara solver (hkbe_matsubara_solve, no GPU needed)
-against closed forms and against the independent oracle solver (which picks
-its Matsubara frequencies differently: the two agree to the DLR accuracy)."""
+against closed forms, against exact diagonalisation (paired site, 2 x 2
+Hubbard cluster: agreement through second order in the coupling), and against
+the independent oracle solver (which picks its Matsubara frequencies
+differently: the two agree to the DLR accuracy)."""
 import numpy as np
 import pytest
 
 import kbe_workloads as wk
 import paper_2604_05319_gb300 as pk
 from oracle.matsubara import MatsubaraOracle
+from _closed_forms import hubbard_cluster, nambu_site
 
 
 @pytest.fixture(scope="module")
@@ -76,3 +79,44 @@ def test_errors(grid5):
     with pytest.raises(pk.HKBEError):      # not converged in 2 iterations
         pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_BETHE, np.array([[[0.3]]]), [[1.0]], max_iter=2,
                                 tol=1e-14)
+
+
+def _residual_ratio(solve, exact, couplings):
+    r = [np.abs(solve(c) - exact(c)).max() for c in couplings]
+    return r, r[0] / r[1]
+
+
+def test_paired_site_matches_exact_diagonalisation(grid5):
+    """One site with a pairing field (v = 0): the library's G^M agrees with
+    exact diagonalisation through U^2 (Fock + second Born, attractive Hubbard
+    term of Eq. Model) and through g^2 (Holstein-Migdal); the residual falls
+    as U^3 and g^4."""
+    beta, tau, om, _ = grid5
+    em = np.array([[0.0, 0.3], [0.3, 0.0]])
+    def lib(U=0.0, g=0.0):
+        p = [0.0, g, 0.6] if g else [0.0]
+        G, _, _, err = pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_NAMBU, em[None], [p], U_eq=U, mix=0.7,
+                                               tol=1e-13)
+        assert err < 1e-12
+        return G[0]
+    r, q = _residual_ratio(lambda U: lib(U=U), lambda U: nambu_site(0.0, 0.3, beta, [], tau, U=-U)[2], (0.1, 0.05))
+    assert r[0] < 5e-4 and 6 < q < 10, (r, q)
+    r, q = _residual_ratio(lambda g: lib(g=g), lambda g: nambu_site(0.0, 0.3, beta, [], tau, g=g, w0=0.6)[2],
+                           (0.06, 0.03))
+    assert r[0] < 1e-4 and 12 < q < 20, (r, q)
+
+
+def test_lattice_2x2_matches_exact_diagonalisation():
+    """Half-filled 2 x 2 Hubbard cluster: the library's lattice G^M_k agrees
+    with exact diagonalisation through U^2."""
+    beta, L = 4.0, 2
+    tau, om = wk.dlr_grid(60.0, 1e-12, beta)
+    m = np.arange(L) * 2 * np.pi / L
+    ek = (-2 * (np.cos(np.repeat(m, L)) + np.cos(np.tile(m, L))))[:, None, None].astype(complex)
+    def lib(U):
+        G, _, _, err = pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_LATTICE2B, ek, [[L]] * (L * L), U_eq=U,
+                                               mix=0.6, tol=1e-13)
+        assert err < 1e-12
+        return G[:, :, 0, 0]
+    r, q = _residual_ratio(lib, lambda U: hubbard_cluster(L, U, beta, [], tau)[2], (0.4, 0.2))
+    assert r[0] < 1e-3 and 6 < q < 20, (r, q)
