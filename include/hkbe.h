@@ -43,7 +43,9 @@ enum {
   HKBE_ERR_RANGE = -4,    /* time index outside the stored/allowed region   */
   HKBE_ERR_RANK = -5,     /* HODLR block rank exceeded its capacity r_max   */
   HKBE_ERR_NAN = -6,      /* non-finite value met during a step             */
-  HKBE_ERR_NOMEM = -7     /* device or host allocation failed               */
+  HKBE_ERR_NOMEM = -7,    /* device or host allocation failed               */
+  HKBE_ERR_IO = -8        /* checkpoint file cannot be written, read, or does
+                             not match the handle it is loaded into          */
 };
 
 /* Self-energy functionals (evaluated on the device at every step). */
@@ -194,6 +196,20 @@ int hkbe_set_drive(hkbe_t* h, const double* A, const double* U);
  * reached without err < tol (state is kept), HKBE_ERR_ARG (call order). */
 int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* err);
 
+/* Start from given rows 0..k instead of hkbe_bootstrap (the start square of
+ * Sec. 3.3 supplied by the caller, e.g. from another solver or a previous
+ * run).  Per instance n, packed row by row for t = 0..k, s = 0..t:
+ *   gr [n_inst][(k+1)(k+2)/2][N_o][N_o]  G^R(t, s)
+ *   gl [n_inst][(k+1)(k+2)/2][N_o][N_o]  G^<(s, t)   (column t, the layout
+ *                                                     hkbe_get_row returns)
+ *   gtv[n_inst][k+1][r][N_o][N_o]        G^tv(t, tau_i)
+ * The library then evaluates Sigma on the square and leaves the handle
+ * exactly where hkbe_bootstrap would (current step k, hkbe_rewind returns
+ * here).  The mixed form rounds the rows to complex64 storage.  Errors:
+ * HKBE_ERR_ARG (null, call order: set_dlr, set_matsubara, set_hamiltonian,
+ * set_model first, and no bootstrap yet), HKBE_ERR_NAN (non-finite input). */
+int hkbe_set_initial_slices(hkbe_t* h, const double* gr, const double* gl, const double* gtv);
+
 /* Advance every instance by n_steps time steps (Sec. 3.4: extrapolate, then
  * per iteration Sigma, retarded row, mixed, lesser column, density matrix,
  * until max |G^(i) - G^(i-1)| < tol or max_iter).  Outputs (may be NULL):
@@ -236,6 +252,14 @@ int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t);
  * another model, HKBE_ERR_RANGE for t outside 0..current step. */
 int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out);
 
+/* Observables at time t <= current step in one call (Sec. 4.2):
+ * rho[n_inst][N_o][N_o] complex as hkbe_get_density_at; ekin[1] and
+ * current[1] as out[1] and out[2] of hkbe_get_lattice_observables.  Any
+ * output may be NULL.  ekin and current exist for LATTICE2B only: asking for
+ * them on another model is HKBE_ERR_ARG.  HKBE_ERR_RANGE for t outside
+ * 0..current step.  Synchronous. */
+int hkbe_get_observables(hkbe_t* h, int t, double* rho, double* ekin, double* current);
+
 /* Device bytes held by the handle. */
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);
 
@@ -257,6 +281,23 @@ int hkbe_get_ranks(hkbe_t* h, int inst, int comp, int32_t* ranks, int32_t* first
  * to propagate again after changing eps(t) for t > k with hkbe_set_hamiltonian).
  * Errors: HKBE_ERR_ARG before the bootstrap. */
 int hkbe_rewind(hkbe_t* h);
+
+/* Checkpoint (Sec. 3.6, checkpoint files: the full simulation state, restart
+ * through a constructor).  hkbe_save writes to `path` the parameters, the
+ * host-side set-up (DLR grid, G^M, eps, model, step counter, compression
+ * front, bootstrap snapshot) and every device buffer of the handle byte for
+ * byte (about hkbe_get_stats bytes), after finishing the work queued on the
+ * handle's stream.  hkbe_load creates a new handle on `stream` from such a
+ * file: propagating it continues the saved run bit for bit on the same
+ * build and GPU type.  The format is this library's own binary layout
+ * (magic "HKBECKP1", version 1), not HDF5, and is read on a machine of the
+ * same byte order.  Errors: HKBE_ERR_ARG (null), HKBE_ERR_IO (cannot open,
+ * short read or write, bad magic or version, or the file's buffers do not
+ * match the sizes the parameters give), HKBE_ERR_NOMEM, HKBE_ERR_CUDA.  After
+ * a failed hkbe_load, *out is NULL and hkbe_last_error(NULL) holds the
+ * message. */
+int hkbe_save(hkbe_t* h, const char* path);
+int hkbe_load(const char* path, void* stream, hkbe_t** out);
 
 /* ---- instrumentation (Sec. 3.5 write_timing / profiling) ---- */
 enum {

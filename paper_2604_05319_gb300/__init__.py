@@ -19,8 +19,9 @@ import numpy as np
 from . import _build
 
 HKBE_OK = 0
+HKBE_ERR_IO = -8
 ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "HKBE_ERR_RANGE",
-          -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM"}
+          -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM", -8: "HKBE_ERR_IO"}
 MODEL_NONE, MODEL_BETHE, MODEL_BATH, MODEL_NAMBU, MODEL_LATTICE2B = 0, 1, 2, 3, 4
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -75,6 +76,10 @@ def load(build_if_missing: bool = True):
                                   C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
                                   _I, _D], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
+        "hkbe_set_initial_slices": ([H, _D, _D, _D], C.c_int),
+        "hkbe_get_observables": ([H, C.c_int, _D, _D, _D], C.c_int),
+        "hkbe_save": ([H, C.c_char_p], C.c_int),
+        "hkbe_load": ([C.c_char_p, C.c_void_p, C.POINTER(H)], C.c_int),
         "hkbe_step": ([H, C.c_int, _I, _D], C.c_int),
         "hkbe_current_step": ([H, _I], C.c_int),
         "hkbe_get_ret": ([H, C.c_int, C.c_int, C.c_int, _D], C.c_int),
@@ -167,6 +172,34 @@ def hkbe_bootstrap(h, n_inst, max_iter, tol):
     rc = load().hkbe_bootstrap(h, int(max_iter), float(tol), _ip(it), _dp(er))
     _check(rc, h)
     return it, er
+
+
+def hkbe_set_initial_slices(h, gr, gl, gtv):
+    """Rows 0..k instead of the bootstrap: gr, gl complex
+    [n_inst, (k+1)(k+2)/2, nao, nao] (G^R(t, s) and G^<(s, t), packed row by
+    row for t = 0..k, s = 0..t), gtv complex [n_inst, k+1, r, nao, nao]."""
+    a, b, c = (_cplx(x, np.shape(x)) for x in (gr, gl, gtv))
+    _check(load().hkbe_set_initial_slices(h, _dp(a), _dp(b), _dp(c)), h)
+
+
+def hkbe_get_observables(h, t, n_inst, nao, lattice=False):
+    """(rho [n_inst, nao, nao], E_kin, j) at time t; E_kin and j only when
+    `lattice` (a LATTICE2B handle), else None."""
+    rho = np.zeros((n_inst, nao, nao), np.complex128)
+    ek = np.zeros(1) if lattice else None
+    cu = np.zeros(1) if lattice else None
+    _check(load().hkbe_get_observables(h, int(t), _dp(rho.view(np.float64)), _dp(ek), _dp(cu)), h)
+    return rho, (float(ek[0]) if lattice else None), (float(cu[0]) if lattice else None)
+
+
+def hkbe_save(h, path):
+    _check(load().hkbe_save(h, os.fsencode(path)), h)
+
+
+def hkbe_load(path, stream=None):
+    h = C.c_void_p()
+    _check(load().hkbe_load(os.fsencode(path), stream, C.byref(h)), None)
+    return h
 
 
 def hkbe_step(h, n_inst, n_steps, check=True):

@@ -28,6 +28,7 @@ struct hkbe_s {
   int* any_dev = nullptr;
   size_t bytes = 0;
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;  // bytes of each entry of allocs (checkpoint files)
   // instrumentation
   bool profiling = false;
   double phase_ms[HKBE_NPHASE] = {0};
@@ -109,6 +110,7 @@ int dalloc(hkbe_t* h, T** p, size_t count) {
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) return fail(h, HKBE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   h->allocs.push_back(*p);
+  h->alloc_bytes.push_back(count * sizeof(T));
   h->bytes += count * sizeof(T);
   cudaMemsetAsync(*p, 0, count * sizeof(T), h->s);
   return HKBE_OK;
@@ -686,19 +688,11 @@ static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, 
 
 extern "C" {
 
-int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* err) {
-  int rc = check_ready(h);
-  if (rc) return rc;
-  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "bootstrap already done");
-  if (max_iter < 1) return fail(h, HKBE_ERR_ARG, "max_iter must be >= 1");
-  if ((rc = hf_guess(h))) return rc;
+// Common end of hkbe_bootstrap and hkbe_set_initial_slices once rows 0..k of
+// G^R, G^< and G^tv are in place: Sigma of the start square (all instances),
+// the snapshot hkbe_rewind returns to, the diagonal-scheme seed, step k.
+static int finish_start(hkbe_t* h) {
   Dev& d = h->d;
-  bool failed = false;
-  rc = iterate(h, max_iter, tol,
-               [&]() { return run_phase(h, HKBE_PHASE_BOOT, d.k + 4, [&]() { return hk::launch_boot(d, h->s); }); },
-               iters, err, &failed);
-  if (rc) return rc;
-  // Sigma of the converged square (all instances)
   std::vector<int> ones(d.n_inst, 1);
   HK_CUDA(h, cudaMemcpyAsync(d.active, ones.data(), d.n_inst * sizeof(int), cudaMemcpyHostToDevice, h->s));
   for (int t = 0; t <= d.k; ++t) HK_CUDA(h, hk::launch_sigma(d, t, h->s));
@@ -739,8 +733,49 @@ int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* 
   }
   HK_CUDA(h, hk::launch_diag_seed(d, h->s));
   h->cur = d.k;
+  return HKBE_OK;
+}
+
+int hkbe_bootstrap(hkbe_t* h, int max_iter, double tol, int32_t* iters, double* err) {
+  int rc = check_ready(h);
+  if (rc) return rc;
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "bootstrap already done");
+  if (max_iter < 1) return fail(h, HKBE_ERR_ARG, "max_iter must be >= 1");
+  if ((rc = hf_guess(h))) return rc;
+  Dev& d = h->d;
+  bool failed = false;
+  rc = iterate(h, max_iter, tol,
+               [&]() { return run_phase(h, HKBE_PHASE_BOOT, d.k + 4, [&]() { return hk::launch_boot(d, h->s); }); },
+               iters, err, &failed);
+  if (rc) return rc;
+  if ((rc = finish_start(h))) return rc;
   if (failed) return fail(h, HKBE_ERR_NOCONV, "bootstrap did not converge");
   return HKBE_OK;
+}
+
+int hkbe_set_initial_slices(hkbe_t* h, const double* gr, const double* gl, const double* gtv) {
+  int rc = check_ready(h);
+  if (rc) return rc;
+  if (!gr || !gl || !gtv) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "the start square is already set");
+  Dev& d = h->d;
+  const int n2 = no2(h), k = d.k, r = d.r;
+  const size_t sq = (size_t)(k + 1) * (k + 2) / 2 * n2, tvn = (size_t)(k + 1) * r * n2;
+  for (size_t i = 0; i < 2 * sq * d.n_inst; ++i)
+    if (!std::isfinite(gr[i]) || !std::isfinite(gl[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in gr or gl");
+  for (size_t i = 0; i < 2 * tvn * d.n_inst; ++i)
+    if (!std::isfinite(gtv[i])) return fail(h, HKBE_ERR_NAN, "non-finite value in gtv");
+  for (int n = 0; n < d.n_inst; ++n) {
+    for (int t = 0; t <= k; ++t) {
+      const size_t o = (sq * n + (size_t)t * (t + 1) / 2 * n2) * 2, c = (size_t)(t + 1) * n2;
+      HK_CUDA(h, h2d_el(h, elp(h, d.GR, row_off(h, n, t)), gr + o, c));
+      HK_CUDA(h, h2d_el(h, elp(h, d.GL, row_off(h, n, t)), gl + o, c));
+    }
+    HK_CUDA(h, cudaMemcpyAsync(static_cast<double2*>(d.GTV) + (size_t)n * d.nt * r * n2, gtv + tvn * n * 2,
+                               tvn * sizeof(double2), cudaMemcpyHostToDevice, h->s));
+  }
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return finish_start(h);
 }
 
 int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
@@ -958,6 +993,22 @@ int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out) {
   return HKBE_OK;
 }
 
+int hkbe_get_observables(hkbe_t* h, int t, double* rho, double* ekin, double* current) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if ((ekin || current) && h->d.model != HKBE_MODEL_LATTICE2B)
+    return fail(h, HKBE_ERR_ARG, "ekin and current are defined for LATTICE2B only");
+  if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
+  int rc;
+  if (ekin || current) {
+    double o[3];
+    if ((rc = hkbe_get_lattice_observables(h, t, o))) return rc;
+    if (ekin) *ekin = o[1];
+    if (current) *current = o[2];
+  }
+  if (rho && (rc = hkbe_get_density_at(h, t, rho))) return rc;
+  return HKBE_OK;
+}
+
 int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes) {
   if (!h || !device_bytes) return HKBE_ERR_ARG;
   *device_bytes = h->bytes;
@@ -1008,6 +1059,150 @@ int hkbe_rewind(hkbe_t* h) {
   }
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->cur = k;
+  return HKBE_OK;
+}
+
+}  // extern "C"
+
+// ---- checkpoint files ----
+namespace {
+constexpr char kCkpMagic[8] = {'H', 'K', 'B', 'E', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkpVersion = 1;
+constexpr size_t kCkpChunk = size_t(64) << 20;  // host staging of device buffers
+
+struct CkpScalars {
+  int32_t cur, have_dlr, have_gm, have_eps, have_model, self_consistent;
+  int32_t model, r, cdir, nfrozR, nfrozL, pad;
+};
+
+bool wr(FILE* f, const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+bool rd(FILE* f, void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+template <typename T>
+bool wr_vec(FILE* f, const std::vector<T>& v) {
+  const uint64_t n = v.size();
+  return wr(f, &n, sizeof n) && wr(f, v.data(), n * sizeof(T));
+}
+// a vector whose length must be 0 (not set) or `expect`
+template <typename T>
+bool rd_vec(FILE* f, std::vector<T>& v, uint64_t expect) {
+  uint64_t n = 0;
+  if (!rd(f, &n, sizeof n) || (n != 0 && n != expect)) return false;
+  v.resize(n);
+  return rd(f, v.data(), n * sizeof(T));
+}
+}  // namespace
+
+extern "C" {
+
+int hkbe_save(hkbe_t* h, const char* path) {
+  if (!h || !path) return fail(h, HKBE_ERR_ARG, "null argument");
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  drain(h);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, HKBE_ERR_IO, std::string("cannot open ") + path + " for writing");
+  const Dev& d = h->d;
+  const CkpScalars sc{h->cur, h->have_dlr, h->have_gm, h->have_eps, h->have_model, h->self_consistent,
+                      d.model, d.r, d.cdir, d.nfrozR, d.nfrozL, 0};
+  const uint32_t ver = kCkpVersion, psz = sizeof(hkbe_params);
+  bool ok = wr(f, kCkpMagic, sizeof kCkpMagic) && wr(f, &ver, sizeof ver) && wr(f, &psz, sizeof psz) &&
+            wr(f, &h->p, sizeof(hkbe_params)) && wr(f, &sc, sizeof sc) && wr_vec(f, h->tau) && wr_vec(f, h->om) &&
+            wr_vec(f, h->gm_host) && wr_vec(f, h->eps_host) && wr_vec(f, h->snap_gr) && wr_vec(f, h->snap_gl) &&
+            wr_vec(f, h->snap_sr) && wr_vec(f, h->snap_sl) && wr_vec(f, h->snap_tv) && wr_vec(f, h->snap_stv);
+  const uint64_t na = h->allocs.size();
+  ok = ok && wr(f, &na, sizeof na);
+  std::vector<char> buf;
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; ok && i < na; ++i) {
+    const uint64_t nb = h->alloc_bytes[i];
+    ok = wr(f, &nb, sizeof nb);
+    for (size_t o = 0; ok && o < nb; o += kCkpChunk) {
+      const size_t c = std::min<size_t>(kCkpChunk, nb - o);
+      if (buf.size() < c) buf.resize(c);
+      e = cudaMemcpyAsync(buf.data(), static_cast<char*>(h->allocs[i]) + o, c, cudaMemcpyDeviceToHost, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) break;
+      ok = wr(f, buf.data(), c);
+    }
+    if (e != cudaSuccess) break;
+  }
+  const bool closed = std::fclose(f) == 0;
+  if (e != cudaSuccess) return fail(h, HKBE_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
+  if (!ok || !closed) return fail(h, HKBE_ERR_IO, std::string("short write to ") + path);
+  return HKBE_OK;
+}
+
+int hkbe_load(const char* path, void* stream, hkbe_t** out) {
+  if (!path || !out) return fail(nullptr, HKBE_ERR_ARG, "null argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(nullptr, HKBE_ERR_IO, std::string("cannot open ") + path);
+  hkbe_t* h = nullptr;
+  auto bad = [&](int code, std::string msg) {
+    std::fclose(f);
+    if (h) hkbe_destroy(h);
+    g_create_error = std::move(msg);
+    return code;
+  };
+  char mg[8];
+  uint32_t ver = 0, psz = 0;
+  hkbe_params p{};
+  CkpScalars sc{};
+  if (!rd(f, mg, sizeof mg) || std::memcmp(mg, kCkpMagic, sizeof mg) != 0)
+    return bad(HKBE_ERR_IO, "not a checkpoint file (bad magic)");
+  if (!rd(f, &ver, sizeof ver) || ver != kCkpVersion || !rd(f, &psz, sizeof psz) || psz != sizeof(hkbe_params))
+    return bad(HKBE_ERR_IO, "unsupported checkpoint version");
+  if (!rd(f, &p, sizeof p) || !rd(f, &sc, sizeof sc)) return bad(HKBE_ERR_IO, "short read (header)");
+  if (sc.r < 0 || sc.r > 128 || (sc.have_dlr != 0) != (sc.r > 0) || sc.cur < -1 || sc.cur >= p.nt || sc.model < 0 ||
+      sc.model > HKBE_MODEL_LATTICE2B || sc.cdir < 0 || sc.cdir > std::max(sc.cur, 0) || sc.nfrozR < 0 ||
+      sc.nfrozL < 0 || sc.nfrozR > (p.nt + 31) / 32 || sc.nfrozL > (p.nt + 31) / 32)
+    return bad(HKBE_ERR_IO, "inconsistent checkpoint header");
+  int rc = hkbe_create(&p, stream, &h);
+  if (rc) return bad(rc, g_create_error);
+  Dev& d = h->d;
+  std::vector<double> tau, om;
+  if (!rd_vec(f, tau, sc.r) || !rd_vec(f, om, sc.r) || tau.size() != (size_t)sc.r || om.size() != (size_t)sc.r)
+    return bad(HKBE_ERR_IO, "short read (DLR grid)");
+  if (sc.have_dlr && (rc = hkbe_set_dlr(h, sc.r, tau.data(), om.data()))) return bad(rc, h->err);
+  const size_t n2 = (size_t)no2(h), k = d.k, es = esz(h);
+  const uint64_t gm_n = (uint64_t)d.n_inst * sc.r * n2 * 2, eps_n = (uint64_t)d.n_inst * (d.nt + 1) * n2 * 2;
+  const uint64_t sq_b = (uint64_t)(k + 1) * (k + 2) / 2 * n2 * d.n_inst * es;
+  const uint64_t tv_b = (uint64_t)(k + 1) * sc.r * n2 * d.n_inst * sizeof(double2);
+  if (!rd_vec(f, h->gm_host, gm_n) || !rd_vec(f, h->eps_host, eps_n) || !rd_vec(f, h->snap_gr, sq_b) ||
+      !rd_vec(f, h->snap_gl, sq_b) || !rd_vec(f, h->snap_sr, sq_b) || !rd_vec(f, h->snap_sl, sq_b) ||
+      !rd_vec(f, h->snap_tv, tv_b) || !rd_vec(f, h->snap_stv, tv_b))
+    return bad(HKBE_ERR_IO, "short read or wrong size (host set-up)");
+  if ((sc.have_gm != 0) != !h->gm_host.empty() || (sc.have_eps != 0) != !h->eps_host.empty())
+    return bad(HKBE_ERR_IO, "inconsistent checkpoint header");
+  uint64_t na = 0;
+  if (!rd(f, &na, sizeof na) || na != h->allocs.size())
+    return bad(HKBE_ERR_IO, "the file's device buffers do not match its parameters");
+  std::vector<char> buf;
+  for (size_t i = 0; i < na; ++i) {
+    uint64_t nb = 0;
+    if (!rd(f, &nb, sizeof nb) || nb != h->alloc_bytes[i])
+      return bad(HKBE_ERR_IO, "the file's device buffers do not match its parameters");
+    for (size_t o = 0; o < nb; o += kCkpChunk) {
+      const size_t c = std::min<size_t>(kCkpChunk, nb - o);
+      if (buf.size() < c) buf.resize(c);
+      if (!rd(f, buf.data(), c)) return bad(HKBE_ERR_IO, "short read (device buffers)");
+      cudaError_t e = cudaMemcpyAsync(static_cast<char*>(h->allocs[i]) + o, buf.data(), c, cudaMemcpyHostToDevice, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) return bad(HKBE_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
+    }
+  }
+  char extra;
+  if (std::fread(&extra, 1, 1, f) != 0) return bad(HKBE_ERR_IO, "trailing bytes after the device buffers");
+  std::fclose(f);
+  h->have_gm = sc.have_gm != 0;
+  h->have_eps = sc.have_eps != 0;
+  h->have_model = sc.have_model != 0;
+  h->self_consistent = sc.self_consistent != 0;
+  h->cur = sc.cur;
+  d.model = sc.model;
+  d.cdir = sc.cdir;
+  d.nfrozR = sc.nfrozR;
+  d.nfrozL = sc.nfrozL;
+  *out = h;
   return HKBE_OK;
 }
 

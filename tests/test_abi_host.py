@@ -73,3 +73,36 @@ def test_create_rejects_bad_arguments_without_gpu():
         with pytest.raises(pk.HKBEError) as e:
             pk.hkbe_create(pk.hkbe_params(**p))
         assert e.value.code == -1
+
+
+def test_checkpoint_load_refuses_bad_files_without_gpu(tmp_path):
+    """hkbe_load checks the file's magic, version and header before any
+    device call; hkbe_save and hkbe_load reject null arguments."""
+    import ctypes as C
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "missing.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO
+    (tmp_path / "junk.ckp").write_bytes(b"not a checkpoint file at all")
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "junk.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO and "magic" in str(e.value)
+    p = pk.hkbe_params(nt=16, k=2, nao=1, xi=-1, n_inst=1, rho_mode=0, precision=0, max_iter=10,
+                       h=0.1, beta=1.0, tol=1e-10)
+    head = b"HKBECKP1" + (1).to_bytes(4, "little") + C.sizeof(p).to_bytes(4, "little") + bytes(p)
+    (tmp_path / "short.ckp").write_bytes(head[:-3])
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "short.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO
+    # scalars cur, have_dlr, have_gm, have_eps, have_model, self_consistent, model, r, cdir,
+    # nfrozR, nfrozL, pad: a grid of r = 200 nodes is out of range
+    sc = np.array([-1, 1, 0, 0, 0, 1, 1, 200, 0, 0, 0, 0], np.int32).tobytes()
+    (tmp_path / "badhead.ckp").write_bytes(head + sc)
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "badhead.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO and "inconsistent" in str(e.value)
+    (tmp_path / "v2.ckp").write_bytes(b"HKBECKP1" + (2).to_bytes(4, "little") + head[12:] + sc)
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "v2.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO and "version" in str(e.value)
+    assert pk.load().hkbe_save(None, b"x") == -1
+    assert pk.load().hkbe_load(None, None, None) == -1
