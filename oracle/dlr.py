@@ -25,7 +25,8 @@ import numpy as np
 
 
 def kernel(tau, om, beta):
-    """K(tau, w) for arrays tau (n,), om (m,) -> (n, m), overflow-safe."""
+    """K(tau, w) for arrays tau (n,), om (m,) -> (n, m), overflow-safe.
+    The fermionic Lehmann kernel of the DLR (Sec. 2.5)."""
     t = np.asarray(tau, dtype=float)[:, None]
     w = np.asarray(om, dtype=float)[None, :]
     wp = np.where(w >= 0, w, 0.0)
@@ -62,6 +63,9 @@ def _gl_composite(a, b, levels=24, npts=24):
 
 
 class DLROracle:
+    """Cardinal functions on the DLR nodes and the matrices built from them
+    (Sec. 2.5, Tables 4-5): evaluation rows, reversal, product and convolution."""
+
     def __init__(self, tau_nodes, omega_nodes, beta, xi=-1):
         self.tau = np.asarray(tau_nodes, dtype=float)
         self.om = np.asarray(omega_nodes, dtype=float)
@@ -81,12 +85,16 @@ class DLROracle:
         return sla.lu_solve(self._lu, rhs.T, trans=1).T
 
     def eval_row(self, tau):
+        """e(tau): f(tau) = e(tau) . f(nodes) (Table 4, get_mat_tau)."""
         return self.cardinal(np.atleast_1d(float(tau)))[0]
 
     def rev(self):
+        """Rev: f(beta - tau_i) = Rev . f(nodes) (Table 5, the reversed functions)."""
         return self.cardinal(self.beta - self.tau)
 
     def Q(self):
+        """Q_ab = int_0^beta l_a l_b dtau, the imaginary-time product of the
+        mixed terms of Eq. KBEL (Sec. 2.5)."""
         x, w = _gl_composite(0.0, self.beta)
         L = self.cardinal(x)
         return (L * w[:, None]).T @ L

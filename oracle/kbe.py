@@ -50,6 +50,9 @@ def _dag(x):
 
 
 class KBEOracle:
+    """The dense FP64 stepper of the discrete scheme above, for one instance
+    (Eqs. KBER, KBET, KBEL; weights of Appendix A; DLR thermal leg of Sec. 2.5)."""
+
     def __init__(self, nt, h, k, beta, eps, gm, tau, omega, model, xi=-1,
                  rho_mode=0, tol=1e-12, max_iter=50, boot_tol=None,
                  boot_max_iter=200):
@@ -90,6 +93,7 @@ class KBEOracle:
 
     # ---- accessors ---------------------------------------------------------
     def ep(self, t):
+        """eps(t) (index t + 1; t = -1 is the equilibrium branch, Sec. 3.2)."""
         return self.eps[t + 1]
 
     def sR_x(self, a, b):
@@ -105,6 +109,7 @@ class KBEOracle:
         return np.einsum("axy,aiyz->ixz", self.STV[t], self.Wconv)
 
     def gtv_at0(self, T):
+        """G^tv(T, 0+) from the DLR expansion on the nodes (Sec. 2.5)."""
         return np.einsum("c,cxy->xy", self.e0, self.GTV[T])
 
     def gvt(self, T):
@@ -113,10 +118,13 @@ class KBEOracle:
         return -self.xi * _dag(rev)
 
     def rho(self, t):
+        """rho(t) = xi i G^<(t, t) (Sec. 3.3)."""
         return self.xi * 1j * self.GLs[t, t]
 
     # ---- initial guess (green_from_H, Sec. 3.3) -----------------------------
     def hf_guess(self):
+        """Mean-field start square (green_from_H, Sec. 3.3): G^R, G^< and G^tv of
+        the levels eps(0_|) with rho = -G^M(beta^-), G^tv seeded from G^M."""
         k, h = self.k, self.h
         e_eq = self.eps[0]
         E, U = np.linalg.eigh(0.5 * (e_eq + _dag(e_eq)))
@@ -137,6 +145,8 @@ class KBEOracle:
 
     # ---- bootstrap -------------------------------------------------------
     def _boot_mixed(self):
+        """Mixed rows 1..k of the start square together (Eq. KBET with D and
+        I_{0,m,.} of Appendix A), G^tv(0, tau) = i xi G^M(beta - tau)."""
         k, h, No, W = self.k, self.h, self.no, self.W
         g0 = 1j * self.xi * np.einsum("bc,cxy->bxy", self.Rev, self.gm)  # G^tv(0, tau)
         self.GTV[0] = g0
@@ -160,6 +170,8 @@ class KBEOracle:
                 self.GTV[m, i] = X[(m - 1) * No:m * No, i * No:(i + 1) * No]
 
     def _boot_ret(self):
+        """Retarded columns n = 0..k of the start square (Eq. KBER in its first
+        argument, D and I_{n,m,.} of Appendix A), G^R(n, n) = -i."""
         k, h, No, W = self.k, self.h, self.no, self.W
         for n in range(k + 1):
             self.GR[n, n] = -1j * self.I1
@@ -224,6 +236,9 @@ class KBEOracle:
                 self.GLs[m, t] = X[(t - 1) * No:t * No]
 
     def bootstrap(self):
+        """Start square T <= k by global iteration with Sigma (Sec. 3.3,
+        dyson_start): mean-field guess, then mixed, retarded and lesser parts
+        until the change is below boot_tol."""
         k = self.k
         self.hf_guess()
         err = np.inf
@@ -249,6 +264,9 @@ class KBEOracle:
 
     # ---- time step T > k ---------------------------------------------------
     def extrapolate(self, T):
+        """Guess of step T (Sec. 3.4): polynomial extrapolation of degree k with
+        weights e_l = (-1)^l C(k+1, l+1) along lines of constant time
+        difference, and of G^tv(T) in T; G^R(T, T) = -i."""
         k = self.k
         e = self.W.extrap()
         for tp in range(T + 1):
@@ -270,6 +288,8 @@ class KBEOracle:
         self.GTV[T] = sum(e[l] * self.GTV[T - 1 - l] for l in range(k + 1))
 
     def solve_ret(self, T):
+        """Row G^R(T, .) from Eq. KBER in the second argument: start block
+        s = 1..k, then BDF + Gregory (Appendix A) point solves for s > k."""
         k, h, No, W = self.k, self.h, self.no, self.W
         y = np.zeros((T + 1, No, No), complex)
         y[0] = -1j * self.I1
@@ -303,6 +323,8 @@ class KBEOracle:
             self.GR[T, T - s] = y[s]
 
     def solve_mixed(self, T):
+        """G^tv(T, tau_i) from Eq. KBET: BDF + Gregory point solve with the DLR
+        convolution of Sigma^tv with G^M (Sec. 2.5)."""
         k, h, W = self.k, self.h, self.W
         a = W.a
         w = W.rule(T)
@@ -313,6 +335,8 @@ class KBEOracle:
         self.GTV[T] = np.linalg.solve(M[None], rhs)
 
     def lesser_source(self, T):
+        """Source q_t of the lesser column (Eq. KBEL): h sum_l w^(T)_l
+        Sigma^<(t, l) G^A(l, T) - i int Sigma^tv(t, tau) G^vt(tau, T) dtau."""
         h = self.h
         w = self.W.rule(T)
         GA = _dag(self.GR[T, :T + 1])                          # G^A(l, T), l = 0..T
@@ -326,6 +350,9 @@ class KBEOracle:
         return q
 
     def solve_les(self, T):
+        """Column G^<(., T) from Eq. KBEL in the first argument: x_0 =
+        -[G^tv(T, 0+)]^dagger, start block t = 1..k, BDF + Gregory for t > k;
+        the last entry from the density-matrix scheme (Sec. 3.3)."""
         k, h, No, W = self.k, self.h, self.no, self.W
         a = W.a
         q = self.lesser_source(T)
@@ -378,6 +405,8 @@ class KBEOracle:
         return -1j * xi * rho
 
     def step(self, T):
+        """Time step T > k (Sec. 3.4): extrapolate, then Sigma, retarded, mixed
+        and lesser parts until max |G^(i) - G^(i-1)| < tol or max_iter."""
         self.extrapolate(T)
         err = np.inf
         it = 0
@@ -397,6 +426,7 @@ class KBEOracle:
         return it, err
 
     def run(self, nt=None):
+        """Bootstrap and step to nt - 1 (Sec. 3.3, 3.4)."""
         nt = self.nt if nt is None else nt
         self.bootstrap()
         for T in range(self.k + 1, nt):

@@ -81,6 +81,8 @@ class LatticeOracle:
         self.nt = int(nt)
 
     def bootstrap(self):
+        """Start square of every k-point, iterated together with the shared
+        Sigma (Sec. 3.3 applied to the coupled lattice of Sec. 4.2)."""
         k = self.k
         for o in self.orcs:
             o.hf_guess()
@@ -101,6 +103,8 @@ class LatticeOracle:
             lattice_sigma(self.orcs, self.L, self.U, t)
 
     def step(self, T):
+        """Time step T of every k-point, all iterated together until the
+        largest change over k is below tol (Sec. 3.4, Sec. 4.2)."""
         for o in self.orcs:
             o.extrapolate(T)
         for it in range(1, self.max_iter + 1):
@@ -116,6 +120,7 @@ class LatticeOracle:
                 break
 
     def run(self):
+        """Bootstrap and step to nt - 1."""
         self.bootstrap()
         for T in range(self.k + 1, self.nt):
             self.step(T)

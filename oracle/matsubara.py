@@ -31,6 +31,9 @@ from .dlr import DLROracle, kernel
 
 
 def matsubara_nodes(om, beta, n_max):
+    """r fermionic Matsubara frequencies nu_n, |n| <= n_max, picked by
+    column-pivoted QR of [1/(i nu_n - w_l)], where the Dyson equation is
+    imposed (Sec. 2.5)."""
     n = np.arange(-n_max, n_max)
     nu = (2 * n + 1) * np.pi / beta
     A = 1.0 / (1j * nu[:, None] - np.asarray(om)[None, :])
@@ -39,6 +42,8 @@ def matsubara_nodes(om, beta, n_max):
 
 
 class MatsubaraOracle:
+    """Self-consistent equilibrium Dyson equation (Eq. KBEM) on the DLR grid."""
+
     def __init__(self, tau, om, beta, xi=-1, n_max=None):
         self.tau = np.asarray(tau, float)
         self.om = np.asarray(om, float)
@@ -59,6 +64,7 @@ class MatsubaraOracle:
         return (self.Kn @ c).reshape(g.shape)
 
     def to_tau(self, gn):
+        """values at the Matsubara nodes -> values on the tau nodes (inverse of to_freq)."""
         c = np.linalg.solve(self.Kn, gn.reshape(self.r, -1))
         return (-(self.Kt @ c)).reshape(gn.shape).real if np.isrealobj(gn) else (-(self.Kt @ c)).reshape(gn.shape)
 
@@ -77,6 +83,8 @@ class MatsubaraOracle:
         return out
 
     def sigma(self, model, G, params):
+        """Sigma^M(tau) on the nodes for the functionals listed in the module
+        header (Eq. Hybrid, Eq. Sigma2B, Migdal, lattice second Born)."""
         N, r, No, _ = G.shape
         S = np.zeros_like(G)
         if model == "bethe":

@@ -24,10 +24,13 @@ import numpy as np
 
 
 def _fermi(e, beta):
+    """Fermi function 1/(e^{beta e} + 1) (Sec. 2.1), overflow-safe."""
     return 0.5 * (1.0 - np.tanh(0.5 * beta * e))
 
 
 class Model:
+    """Sigma = 0 (free propagation); base of the self-energy functionals that
+    fill Sigma^R(T, .), Sigma^<(., T) and Sigma^tv(T, .) of step T (Sec. 3.4)."""
     name = "none"
     self_consistent = False
 
@@ -41,6 +44,7 @@ class Model:
 
 
 class Bethe(Model):
+    """Bethe-lattice DMFT hybridisation Sigma = v^2 G (Eq. Hybrid, Sec. 3.1)."""
     name = "bethe"
     self_consistent = True
 
@@ -166,4 +170,5 @@ class Nambu(Model):
 
 
 def make_model(name, params=None):
+    """Self-energy functional by name: none, bethe, bath, nambu."""
     return {"none": Model, "bethe": Bethe, "bath": Bath, "nambu": Nambu}[name](params)

@@ -166,12 +166,15 @@ class Weights:
         self._I = {}
 
     def I(self, m: int, n: int) -> np.ndarray:
+        """I_{m,n,l}: weights of int_m^n over the points 0..k (Appendix A)."""
         key = (m, n)
         if key not in self._I:
             self._I[key] = np.array([float(x) for x in integ_I_exact(self.k, m, n)])
         return self._I[key]
 
     def rule(self, n: int) -> np.ndarray:
+        """w^(n)_l of int_0^n (unit spacing): start weights for n <= k, Gregory
+        end corrections beyond (Appendix A)."""
         if n not in self._rule:
             self._rule[n] = np.array([float(x) for x in rule_exact(self.k, n)])
         return self._rule[n]
