@@ -1,0 +1,68 @@
+"""The bench's algorithmic-bytes model (bench.phase_bytes, the numerator of
+its roofline) against a brute-force count on a HODLR partition (Sec. 2.2,
+Fig. 2).  The partition is built here from its definition: leaves
+[j L, (j+1) L); a range of leaves [a, b) splits at m = a + (b - a)/2 into the
+block rows [m L, b L) x columns [a L, m L) and the two halves.  The test first
+checks that the leaf triangles and the blocks tile the lower triangle exactly
+once.  It then checks that the model's uncompressed rows, leaf triangles and
+factor terms equal the stored elements a sweep at step T must read, counted
+one by one."""
+import numpy as np
+
+import bench
+
+
+def _partition(nt, L):
+    nleaf = (nt + L - 1) // L
+    out = {"r0": [], "r1": [], "c0": [], "c1": []}
+    stack = [(0, nleaf)]
+    while stack:
+        a, b = stack.pop()
+        if b - a <= 1:
+            continue
+        m = a + (b - a) // 2
+        for key, v in zip(("r0", "r1", "c0", "c1"), (m * L, min(b * L, nt), a * L, m * L)):
+            out[key].append(v)
+        stack += [(m, b), (a, m)]
+    return {key: np.array(v) for key, v in out.items()}
+
+
+def test_partition_tiles_the_lower_triangle():
+    for nt, L in ((1000, 64), (517, 32), (64, 64)):
+        blk = _partition(nt, L)
+        cover = np.zeros((nt, nt), np.int32)
+        for j in range(0, nt, L):
+            e = min(j + L, nt)
+            cover[j:e, j:e] += np.tril(np.ones((e - j, e - j), np.int32))
+        for r0, r1, c0, c1 in zip(blk["r0"], blk["r1"], blk["c0"], blk["c1"]):
+            cover[r0:r1, c0:c1] += 1
+        assert np.array_equal(cover, np.tril(np.ones((nt, nt), np.int32))), (nt, L)
+
+
+def test_bytes_model_counts_every_stored_element_once():
+    nt, L, k, no, r = 1000, 64, 5, 2, 30
+    n2 = no * no
+    blk = _partition(nt, L)
+    rng = np.random.default_rng(3)
+    ranks = rng.integers(1, 20, size=(len(blk["r0"]), n2))
+    for T, es in ((999, 8), (700, 16), (130, 8)):
+        c = ((T - k) // L) * L                    # compression front after step T (whole leaves <= T - k)
+        direct = leaf = fac = 0
+        for s in range(c, T + 1):                 # uncompressed rows: (s, 0..s)
+            direct += s + 1
+        for s in range(c):                        # below the front: leaf triangle or one block
+            for t in range(s + 1):
+                if s // L == t // L:
+                    leaf += 1
+        for b in range(len(blk["r0"])):           # factors: built rows of U, all columns of V
+            r0, r1, c0, c1 = blk["r0"][b], blk["r1"][b], blk["c0"][b], blk["c1"][b]
+            if r0 < c:
+                fac += (min(r1, c) - r0 + (c1 - c0)) * int(ranks[b].sum())
+        band = c * k * n2 * es
+        row = (T + 1) * n2
+        expect_ret = (direct + leaf) * n2 * es + fac * es + band + row * (32 + es)   # no frozen inverses
+        got = bench.phase_bytes("ret", T, c, 0, no, r, L, k, es, blk, ranks)
+        assert got == expect_ret, (T, got, expect_ret)
+        expect_src = (direct + leaf) * n2 * es + fac * es + band + row * es + (T + 1) * r * n2 * 16 + row * 16
+        assert bench.phase_bytes("src", T, c, 0, no, r, L, k, es, blk, ranks) == expect_src
+        assert bench.phase_bytes("ret", T, c, 3, no, r, L, k, es, blk, ranks) - got == 3 * (32 * no) ** 2 * 16
