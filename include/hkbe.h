@@ -337,6 +337,14 @@ int hkbe_weights(int k, double* a, double* omega, double* D, double* I0);
 /* Integration rule w^(n)_l of int_0^{n h} (unit spacing) into w[max(n,k)+1]. */
 int hkbe_rule(int k, int n, double* w);
 
+/* HODLR partition of an nt x nt lower triangle with leaf size `leaf` (Sec. 2.2,
+ * Fig. 2), as hkbe_create builds it, without a handle or a device: *nblk
+ * blocks, and per block (arrays of length >= *nblk when given, any may be
+ * NULL) rows [r0, r1), columns [c0, c1) and level.  Call with all arrays
+ * NULL to get *nblk.  HKBE_ERR_ARG for nt < 1 or leaf < 1. */
+int hkbe_hodlr_partition(int nt, int leaf, int32_t* nblk, int32_t* r0, int32_t* r1, int32_t* c0,
+                         int32_t* c1, int32_t* level);
+
 /* DLR matrices the library builds from the grid (cardinal functions by LU
  * solves, integrals by tanh-sinh quadrature): e0[r] (evaluation at tau=0), ebeta[r] (at beta), rev[r*r]
  * (values at beta - tau_i), q[r*r] (int l_a l_b), phi[r*r*r] (phi[a][c][i] =

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "hkbe_reset_counters": ([H], C.c_int),
         "hkbe_weights": ([C.c_int, _D, _D, _D, _D], C.c_int),
         "hkbe_rule": ([C.c_int, C.c_int, _D], C.c_int),
+        "hkbe_hodlr_partition": ([C.c_int, C.c_int, _I, _I, _I, _I, _I, _I], C.c_int),
         "hkbe_dlr_matrices": ([C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, _D, _D, _D], C.c_int),
         "hkbe_lesser_column_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]
                                        + [C.c_void_p] * 6 + [C.c_void_p] * 3
@@ -369,6 +370,16 @@ def hkbe_rule(k, n):
     w = np.zeros(max(n, k) + 1)
     _check(load().hkbe_rule(k, n, _dp(w)))
     return w
+
+
+def hkbe_hodlr_partition(nt, leaf):
+    """Blocks of the HODLR partition (host only): dict of r0, r1, c0, c1, level."""
+    nb = np.zeros(1, np.int32)
+    _check(load().hkbe_hodlr_partition(int(nt), int(leaf), _ip(nb), None, None, None, None, None))
+    n = int(nb[0])
+    a = [np.zeros(max(n, 1), np.int32) for _ in range(5)]
+    _check(load().hkbe_hodlr_partition(int(nt), int(leaf), _ip(nb), *[_ip(x) for x in a]))
+    return dict(zip(["r0", "r1", "c0", "c1", "level"], [x[:n] for x in a]))
 
 
 def hkbe_dlr_matrices(tau, omega, beta, xi=-1):

@@ -1256,6 +1256,25 @@ int hkbe_rule(int k, int n, double* w) {
   return HKBE_OK;
 }
 
+int hkbe_hodlr_partition(int nt, int leaf, int32_t* nblk, int32_t* r0, int32_t* r1, int32_t* c0,
+                         int32_t* c1, int32_t* level) {
+  if (nt < 1 || leaf < 1 || !nblk) return HKBE_ERR_ARG;
+  hkbe_s tmp;                    // host-side only: build_geometry makes no device call
+  tmp.p.nt = nt;
+  tmp.p.leaf = leaf;
+  tmp.p.nao = 1;
+  build_geometry(&tmp);
+  *nblk = (int32_t)tmp.g_r0.size();
+  for (size_t b = 0; b < tmp.g_r0.size(); ++b) {
+    if (r0) r0[b] = tmp.g_r0[b];
+    if (r1) r1[b] = tmp.g_r1[b];
+    if (c0) c0[b] = tmp.g_c0[b];
+    if (c1) c1[b] = tmp.g_c1[b];
+    if (level) level[b] = tmp.g_lvl[b];
+  }
+  return HKBE_OK;
+}
+
 int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta, int xi, double* e0,
                       double* ebeta, double* rev, double* q, double* phi) {
   if (r < 1 || r > 128 || !tau || !omega || !(beta > 0) || (xi != -1 && xi != 1)) return HKBE_ERR_ARG;

@@ -8,6 +8,7 @@ once.  It then checks that the model's uncompressed rows, leaf triangles and
 factor terms equal the stored elements a sweep at step T must read, counted
 one by one."""
 import numpy as np
+import pytest
 
 import bench
 
@@ -66,3 +67,19 @@ def test_bytes_model_counts_every_stored_element_once():
         expect_src = (direct + leaf) * n2 * es + fac * es + band + row * es + (T + 1) * r * n2 * 16 + row * 16
         assert bench.phase_bytes("src", T, c, 0, no, r, L, k, es, blk, ranks) == expect_src
         assert bench.phase_bytes("ret", T, c, 3, no, r, L, k, es, blk, ranks) - got == 3 * (32 * no) ** 2 * 16
+
+
+def test_library_partition_matches_the_definition():
+    """The partition hkbe_create builds (exported host-only) is the one the
+    bench model and the test above use, for every leaf size the library
+    accepts, and the library rejects bad sizes."""
+    import paper_2604_05319_gb300 as pk
+    for nt, L in ((4096, 64), (8192, 64), (1000, 32), (64, 64), (65, 32), (1, 32)):
+        lib = pk.hkbe_hodlr_partition(nt, L)
+        ref = _partition(nt, L)
+        blocks = [sorted(zip(*(p[key].tolist() for key in ("r0", "r1", "c0", "c1")))) for p in (lib, ref)]
+        assert blocks[0] == blocks[1], (nt, L)
+        assert len(lib["r0"]) == len(ref["r0"]) == max(0, (nt + L - 1) // L - 1)
+        assert (lib["level"] >= 0).all() and (np.diff(np.sort(np.unique(lib["level"]))) == 1).all()
+    with pytest.raises(pk.HKBEError):
+        pk.hkbe_hodlr_partition(0, 64)
