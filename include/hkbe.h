@@ -139,12 +139,14 @@ int hkbe_set_dlr(hkbe_t* h, int r, const double* tau, const double* omega);
 
 /* Equilibrium Matsubara Green's function on the DLR nodes, G^M(tau_i), for
  * every instance: gm[n_inst][r][N_o][N_o] complex (Table 4, get_mat/set_mat).
- * Also precomputes the convolution tensor of Eq. KBET (initGMConvTensor). */
+ * Also precomputes the convolution tensor of Eq. KBET (initGMConvTensor).
+ * Errors: HKBE_ERR_ARG (null, or before hkbe_set_dlr). */
 int hkbe_set_matsubara(hkbe_t* h, const double* gm);
 
 /* Mean-field Hamiltonian eps(t) = h0(t) + Sigma^MF(t) - mu (Eq. KBEM-KBEL) for
  * t = -1..nt-1 and every instance: eps[n_inst][nt+1][N_o][N_o] complex, index
- * 0 holding the equilibrium branch eps(0_|). */
+ * 0 holding the equilibrium branch eps(0_|).  Errors: HKBE_ERR_ARG (null),
+ * HKBE_ERR_NAN (non-finite value). */
 int hkbe_set_hamiltonian(hkbe_t* h, const double* eps);
 
 /* The same for one time t only: eps_t[n_inst][N_o][N_o] complex replaces
@@ -171,7 +173,10 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
  *       (Eq. Hybrid, Peierls phases diag(e^{iA}, e^{-iA})), the bubble and
  *       exchange diagrams of Eq. Sigma2B with U(t)U(t'), and the Fock term
  *       of Eq. SigmaF added to eps(t) at every evaluation (eps as set by the
- *       caller is kept apart).  A(t), U(t) come from hkbe_set_drive.
+ *       caller is kept apart).  A(t), U(t) come from hkbe_set_drive.  With the
+       Fock term -U rho_12 and the -U/2 shift of Eq. Model absorbed in eps,
+       this is the attractive Hubbard term -U (n_up - 1/2)(n_dn - 1/2) of
+       Eq. Model through order U^2.
  *   HKBE_MODEL_LATTICE2B: N_o = 1, one instance per k-point of an L x L grid,
  *       k = 2 pi (m_x, m_y)/L at instance m_x L + m_y, n_inst = L^2, L <= 16;
  *       params[n][0] = L.  Sigma^≷_k from Sigma^≷_r(T,t) =
@@ -179,7 +184,9 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
  *       transform over k; the mixed part with the imaginary branch latest),
  *       U(t) from hkbe_set_drive (instance 0; the same for every k).  The
  *       dispersion with its Peierls shift eps_{k-A(t)} is the caller's eps.
- *       The k-points iterate together (all or none). */
+ *       The k-points iterate together (all or none).
+ * Errors: HKBE_ERR_ARG (unknown model, wrong N_o or parameter count, L^2 !=
+ * n_inst, w0 <= 0 with g != 0). */
 int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams);
 
 /* Drive of the Nambu model: A[n_inst][nt+1] (vector potential) and
@@ -225,18 +232,23 @@ int hkbe_current_step(const hkbe_t* h, int32_t* T);
 int hkbe_get_ret(hkbe_t* h, int inst, int t, int tp, double* out);
 
 /* G^<(t, t') for any 0 <= t, t' <= T (Table 3 get_les; the upper triangle
- * uses G^<(t,t') = -[G^<(t',t)]^dagger, Eq. GLantiHerm). */
+ * uses G^<(t,t') = -[G^<(t',t)]^dagger, Eq. GLantiHerm).  Errors: HKBE_ERR_ARG
+ * (null, bad instance), HKBE_ERR_RANGE (a time outside 0..current step). */
 int hkbe_get_les(hkbe_t* h, int inst, int t, int tp, double* out);
 
-/* Mixed row G^tv(t, tau_i), i = 0..r-1, into out[r][N_o][N_o] (Table 4 get_tv). */
+/* Mixed row G^tv(t, tau_i), i = 0..r-1, into out[r][N_o][N_o] (Table 4 get_tv).
+ * Errors: HKBE_ERR_ARG (null, bad instance, no DLR grid), HKBE_ERR_RANGE
+ * (t outside 0..current step). */
 int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out);
 
 /* Whole retarded row G^R(T, 0..T) and lesser column G^<(0..T, T) of step T:
- * gr[T+1][N_o][N_o], gl[T+1][N_o][N_o] (either may be NULL). */
+ * gr[T+1][N_o][N_o], gl[T+1][N_o][N_o] (either may be NULL).  Errors:
+ * HKBE_ERR_ARG (bad instance), HKBE_ERR_RANGE (T outside 0..current step). */
 int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl);
 
 /* Density matrix rho(t) = xi i G^<(t,t) (Sec. 3.3) for t = 0..T of every
- * instance: rho[n_inst][T+1][N_o][N_o] complex. */
+ * instance: rho[n_inst][T+1][N_o][N_o] complex.  Errors: HKBE_ERR_ARG (null),
+ * HKBE_ERR_RANGE (before the bootstrap). */
 int hkbe_get_density(hkbe_t* h, double* rho);
 
 /* rho(t) of every instance at one time t <= current step:
