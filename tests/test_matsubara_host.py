@@ -120,3 +120,25 @@ def test_lattice_2x2_matches_exact_diagonalisation():
         return G[:, :, 0, 0]
     r, q = _residual_ratio(lib, lambda U: hubbard_cluster(L, U, beta, [], tau)[2], (0.4, 0.2))
     assert r[0] < 1e-3 and 6 < q < 20, (r, q)
+
+
+@pytest.mark.parametrize("beta,lam,params,U", [(18.0, 100.0, [1.0], 2.0),            # the paper's SC state
+                                               (50.0, 200.0, [1.0, 0.5, 0.6], 0.0)])  # C4's Holstein set
+def test_symmetry_broken_equilibria_match_oracle(beta, lam, params, U):
+    """Symmetry-broken iterations (pairing field 1e-4 for 5 iterations) at
+    the paper's superconducting point and at C4's Holstein parameters.  The
+    latter relaxes back to the normal state: its anomalous part decays, since
+    2 g^2 rho(0) / w0 ~ 0.27 puts the Migdal T_c far below 1/50.  Library and
+    oracle solvers agree either way."""
+    tau, om = wk.dlr_grid(lam, 1e-10, beta)
+    em = np.zeros((1, 2, 2), complex)
+    G, e, it, _ = pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_NAMBU, em, [params], U_eq=U, eta=1e-4, n_eta=5,
+                                          mix=0.5, tol=1e-12, max_iter=5000)
+    pd = {"v": params[0], "U": U}
+    if len(params) == 3:
+        pd.update({"g": params[1], "w0": params[2]})
+    Go, eo, ito, _ = MatsubaraOracle(tau, om, beta).solve("nambu", em, pd, tol=1e-12, mix=0.5, eta=1e-4, n_eta=5,
+                                                           max_iter=5000)
+    assert np.abs(G - Go).max() < 1e-10 and np.abs(e - eo).max() < 1e-10
+    anom = np.abs(G[0, :, 0, 1]).max()
+    assert (anom > 0.1) if U else (anom < 1e-9), anom
