@@ -131,3 +131,31 @@ def test_paper_phases_of_the_attractive_hubbard_example():
             assert anom > 0.1 and abs(e[0, 0, 1]) > 0.1, (anom, e[0, 0, 1])
         else:
             assert anom < 1e-10 and abs(e[0, 0, 1]) < 1e-10, (anom, e[0, 0, 1])
+
+
+def test_superconducting_equilibrium_is_stationary():
+    """Propagating the paper's superconducting equilibrium (U = 2, beta = 18,
+    Bethe lattice, no drive) keeps it stationary: G^R(t + d, t) independent
+    of t and rho constant, anomalous parts included, to the discretisation
+    error (which falls at least 8-fold when h halves).  This fixes every
+    anomalous term of the real-time functionals against the Matsubara ones:
+    a flipped Fock sign, a missing sigma_z on the mixed hybridisation, or a
+    wrong sign or factor of the mixed bubble leave deviations of 0.03 or more."""
+    beta = 18.0
+    tau, om = wk.dlr_grid(100.0, 1e-10, beta)
+    mo = MatsubaraOracle(tau, om, beta)
+    G, _, _, err = mo.solve("nambu", np.zeros((1, 2, 2)), {"v": 1.0, "U": 2.0}, tol=1e-13, mix=0.5, eta=1e-4,
+                            n_eta=5, max_iter=5000)
+    assert err < 1e-12 and np.abs(G[0, :, 0, 1]).max() > 0.1
+    devs = []
+    for nt, h in ((40, 0.05), (80, 0.025)):
+        model = make_model("nambu", {"v": 1.0, "A": np.zeros(nt + 1), "U": np.full(nt + 1, 2.0)})
+        o = KBEOracle(nt, h, 5, beta, np.zeros((nt + 1, 2, 2), complex), G[0], tau, om, model, tol=1e-13).run()
+        dev = 0.0
+        for d in range(1, nt // 2):
+            vals = np.array([o.GR[t + d, t] for t in range(nt - d)])
+            dev = max(dev, float(np.abs(vals - vals[0]).max()))
+        rho = np.array([o.rho(t) for t in range(nt)])
+        assert abs(rho[0][0, 1]) > 0.2                       # the pair amplitude is there
+        devs.append(max(dev, float(np.abs(rho - rho[0]).max())))
+    assert devs[1] < 2e-6 and devs[0] / devs[1] > 8, devs
