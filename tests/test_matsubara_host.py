@@ -142,3 +142,21 @@ def test_symmetry_broken_equilibria_match_oracle(beta, lam, params, U):
     assert np.abs(G - Go).max() < 1e-10 and np.abs(e - eo).max() < 1e-10
     anom = np.abs(G[0, :, 0, 1]).max()
     assert (anom > 0.1) if U else (anom < 1e-9), anom
+
+
+def test_lattice_equilibrium_at_c3_size():
+    """C3's interacting equilibrium at full size (16 x 16 k-points, U = 2,
+    beta = 10, half filling): library and oracle solvers agree, and the mean
+    occupation -1/N_k sum_k G_k(beta^-) is 1/2 (particle-hole symmetry of the
+    half-filled square lattice)."""
+    beta, L, U = 10.0, 16, 2.0
+    tau, om = wk.dlr_grid(100.0, 1e-10, beta)
+    m = np.arange(L) * 2 * np.pi / L
+    ek = (-2 * (np.cos(np.repeat(m, L)) + np.cos(np.tile(m, L))))[:, None, None].astype(complex)
+    G, _, it, _ = pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_LATTICE2B, ek, [[L]] * (L * L), U_eq=U, mix=0.5,
+                                          tol=1e-12, max_iter=2000)
+    mo = MatsubaraOracle(tau, om, beta)
+    Go, _, _, _ = mo.solve("lattice2b", ek, {"L": L, "U": U}, tol=1e-12, mix=0.5, max_iter=2000)
+    assert np.abs(G - Go).max() < 1e-10
+    n_k = -np.einsum("c,kc->k", mo.ebeta, G[:, :, 0, 0]).real
+    assert abs(n_k.mean() - 0.5) < 1e-9 and n_k[0] > 0.9 and n_k[(L // 2) * L + L // 2] < 0.1
