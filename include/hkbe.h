@@ -303,9 +303,13 @@ int hkbe_rewind(hkbe_t* h);
  * file: propagating it continues the saved run bit for bit on the same
  * build and GPU type.  The format is this library's own binary layout
  * (magic "HKBECKP1", version 1), not HDF5, and is read on a machine of the
- * same byte order.  Errors: HKBE_ERR_ARG (null), HKBE_ERR_IO (cannot open,
- * short read or write, bad magic or version, or the file's buffers do not
- * match the sizes the parameters give), HKBE_ERR_NOMEM, HKBE_ERR_CUDA.  After
+ * same byte order.  Its last 8 bytes are a checksum of everything before
+ * them: FNV-1a 64 over the bytes taken as little-endian 64-bit words, the
+ * last word zero-padded (offset basis 14695981039346656037, prime
+ * 1099511628211).  hkbe_load verifies it before any device work.  Errors:
+ * HKBE_ERR_ARG (null), HKBE_ERR_IO (cannot open, short read or write, bad
+ * magic or version, checksum mismatch, or the file's buffers do not match
+ * the sizes the parameters give), HKBE_ERR_NOMEM, HKBE_ERR_CUDA.  After
  * a failed hkbe_load, *out is NULL and hkbe_last_error(NULL) holds the
  * message. */
 int hkbe_save(hkbe_t* h, const char* path);

@@ -1075,6 +1075,42 @@ struct CkpScalars {
   int32_t model, r, cdir, nfrozR, nfrozL, pad;
 };
 
+// Checksum of a checkpoint file: FNV-1a over the file's bytes taken as
+// little-endian 64-bit words (the last word zero-padded), written as an
+// 8-byte trailer after everything it covers.
+constexpr uint64_t kFnvOffset = 14695981039346656037ull, kFnvPrime = 1099511628211ull;
+
+uint64_t fnv_words(uint64_t h, const unsigned char* p, size_t n) {
+  size_t i = 0;
+  for (; i + 8 <= n; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, p + i, 8);
+    h = (h ^ w) * kFnvPrime;
+  }
+  if (i < n) {
+    uint64_t w = 0;
+    std::memcpy(&w, p + i, n - i);
+    h = (h ^ w) * kFnvPrime;
+  }
+  return h;
+}
+
+// Checksum of the first `len` bytes of f, read from the start in chunks of a
+// multiple of 8 bytes (so only the final word can be partial).
+bool file_checksum(FILE* f, uint64_t len, uint64_t* out) {
+  if (std::fseek(f, 0, SEEK_SET) != 0) return false;
+  std::vector<unsigned char> buf((size_t)std::min<uint64_t>(len, kCkpChunk));
+  uint64_t h = kFnvOffset;
+  for (uint64_t done = 0; done < len;) {
+    const size_t c = (size_t)std::min<uint64_t>(kCkpChunk, len - done);
+    if (std::fread(buf.data(), 1, c, f) != c) return false;
+    h = fnv_words(h, buf.data(), c);
+    done += c;
+  }
+  *out = h;
+  return true;
+}
+
 bool wr(FILE* f, const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
 bool rd(FILE* f, void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
 template <typename T>
@@ -1098,7 +1134,7 @@ int hkbe_save(hkbe_t* h, const char* path) {
   if (!h || !path) return fail(h, HKBE_ERR_ARG, "null argument");
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   drain(h);
-  FILE* f = std::fopen(path, "wb");
+  FILE* f = std::fopen(path, "w+b");   // read back for the checksum trailer
   if (!f) return fail(h, HKBE_ERR_IO, std::string("cannot open ") + path + " for writing");
   const Dev& d = h->d;
   const CkpScalars sc{h->cur, h->have_dlr, h->have_gm, h->have_eps, h->have_model, h->self_consistent,
@@ -1124,6 +1160,12 @@ int hkbe_save(hkbe_t* h, const char* path) {
       ok = wr(f, buf.data(), c);
     }
     if (e != cudaSuccess) break;
+  }
+  if (ok && e == cudaSuccess) {
+    uint64_t sum = 0;
+    const long len = (std::fflush(f) == 0) ? std::ftell(f) : -1;
+    ok = len >= 0 && file_checksum(f, (uint64_t)len, &sum) && std::fseek(f, 0, SEEK_END) == 0 &&
+         wr(f, &sum, sizeof sum);
   }
   const bool closed = std::fclose(f) == 0;
   if (e != cudaSuccess) return fail(h, HKBE_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
@@ -1151,6 +1193,17 @@ int hkbe_load(const char* path, void* stream, hkbe_t** out) {
     return bad(HKBE_ERR_IO, "not a checkpoint file (bad magic)");
   if (!rd(f, &ver, sizeof ver) || ver != kCkpVersion || !rd(f, &psz, sizeof psz) || psz != sizeof(hkbe_params))
     return bad(HKBE_ERR_IO, "unsupported checkpoint version");
+  {  // the whole file against its trailer, before any device work
+    uint64_t sum = 0, trailer = 0;
+    if (std::fseek(f, 0, SEEK_END) != 0) return bad(HKBE_ERR_IO, "cannot seek in the checkpoint file");
+    const long len = std::ftell(f);
+    if (len < (long)(sizeof mg + sizeof ver + sizeof psz + sizeof trailer)) return bad(HKBE_ERR_IO, "short checkpoint file");
+    if (!file_checksum(f, (uint64_t)len - sizeof trailer, &sum) || !rd(f, &trailer, sizeof trailer))
+      return bad(HKBE_ERR_IO, "short read (checksum)");
+    if (sum != trailer) return bad(HKBE_ERR_IO, "checksum mismatch: the checkpoint file is damaged");
+    if (std::fseek(f, (long)(sizeof mg + sizeof ver + sizeof psz), SEEK_SET) != 0)
+      return bad(HKBE_ERR_IO, "cannot seek in the checkpoint file");
+  }
   if (!rd(f, &p, sizeof p) || !rd(f, &sc, sizeof sc)) return bad(HKBE_ERR_IO, "short read (header)");
   if (sc.r < 0 || sc.r > 128 || (sc.have_dlr != 0) != (sc.r > 0) || sc.cur < -1 || sc.cur >= p.nt || sc.model < 0 ||
       sc.model > HKBE_MODEL_LATTICE2B || sc.cdir < 0 || sc.cdir > std::max(sc.cur, 0) || sc.nfrozR < 0 ||
@@ -1190,8 +1243,10 @@ int hkbe_load(const char* path, void* stream, hkbe_t** out) {
       if (e != cudaSuccess) return bad(HKBE_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
     }
   }
+  uint64_t trailer = 0;
   char extra;
-  if (std::fread(&extra, 1, 1, f) != 0) return bad(HKBE_ERR_IO, "trailing bytes after the device buffers");
+  if (!rd(f, &trailer, sizeof trailer) || std::fread(&extra, 1, 1, f) != 0)
+    return bad(HKBE_ERR_IO, "trailing bytes after the device buffers");
   std::fclose(f);
   h->have_gm = sc.have_gm != 0;
   h->have_eps = sc.have_eps != 0;

@@ -75,6 +75,17 @@ def test_create_rejects_bad_arguments_without_gpu():
         assert e.value.code == -1
 
 
+def _fnv_words(data):
+    """FNV-1a 64 over little-endian 64-bit words, the last one zero-padded
+    (the checkpoint trailer's definition in include/hkbe.h)."""
+    import struct
+    h = 14695981039346656037
+    data = bytes(data) + b"\0" * (-len(data) % 8)
+    for (w,) in struct.iter_unpack("<Q", data):
+        h = ((h ^ w) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
 def test_checkpoint_load_refuses_bad_files_without_gpu(tmp_path):
     """hkbe_load checks the file's magic, version and header before any
     device call; hkbe_save and hkbe_load reject null arguments."""
@@ -96,10 +107,17 @@ def test_checkpoint_load_refuses_bad_files_without_gpu(tmp_path):
     # scalars cur, have_dlr, have_gm, have_eps, have_model, self_consistent, model, r, cdir,
     # nfrozR, nfrozL, pad: a grid of r = 200 nodes is out of range
     sc = np.array([-1, 1, 0, 0, 0, 1, 1, 200, 0, 0, 0, 0], np.int32).tobytes()
-    (tmp_path / "badhead.ckp").write_bytes(head + sc)
-    with pytest.raises(pk.HKBEError) as e:
+    body = head + sc
+    (tmp_path / "badhead.ckp").write_bytes(body + _fnv_words(body).to_bytes(8, "little"))
+    with pytest.raises(pk.HKBEError) as e:      # the checksum passes; the header is refused
         pk.hkbe_load(str(tmp_path / "badhead.ckp"))
     assert e.value.code == pk.HKBE_ERR_IO and "inconsistent" in str(e.value)
+    flipped = bytearray(body)
+    flipped[40] ^= 0x10                          # one bit of the parameters
+    (tmp_path / "flipped.ckp").write_bytes(bytes(flipped) + _fnv_words(body).to_bytes(8, "little"))
+    with pytest.raises(pk.HKBEError) as e:
+        pk.hkbe_load(str(tmp_path / "flipped.ckp"))
+    assert e.value.code == pk.HKBE_ERR_IO and "checksum" in str(e.value)
     (tmp_path / "v2.ckp").write_bytes(b"HKBECKP1" + (2).to_bytes(4, "little") + head[12:] + sc)
     with pytest.raises(pk.HKBEError) as e:
         pk.hkbe_load(str(tmp_path / "v2.ckp"))
