@@ -196,3 +196,48 @@ def test_pin_catches_wrong_gregory_weight(monkeypatch):
         return w
     e = _patched_error(monkeypatch, lambda m: m.setattr(W.Weights, "rule", bad))
     assert e > 1e-4
+
+
+def _bethe_energy(o, T, W):
+    """n(T) = -i G^<(T,T) and E_kin(T) = -i [Sigma * G]^<(T,T) (Langreth rule
+    for the lesser component of the contour convolution at equal times,
+    Sec. 2.1): h sum_l w_l [Sigma^R(T,l) G^<(l,T) + Sigma^<(T,l) G^A(l,T)]
+    - i int Sigma^tv(T,tau) G^vt(tau,T) dtau, with the Gregory rule of step T
+    and the DLR quadrature (Sec. 2.5)."""
+    h = o.h
+    wt = W.rule(T)
+    GA = np.conj(np.swapaxes(o.GR[T, :T + 1], -1, -2))
+    SLT = np.array([(-np.conj(o.SLs[T, l].T) if l < T else o.SLs[T, T]) for l in range(T + 1)])
+    conv = h * np.einsum("l,lxy,lyz->xz", wt, o.SR[T, :T + 1], o.GLs[T, :T + 1])
+    conv += h * np.einsum("l,lxy,lyz->xz", wt, SLT, GA)
+    v = np.einsum("ab,bxy->axy", o.Q, o.gvt(T))
+    conv += -1j * np.einsum("axy,ayz->xz", o.STV[T], v)
+    return (-1j * o.GLs[T, T])[0, 0].real, (-1j * conv)[0, 0]
+
+
+def test_bethe_energy_conserved_at_order_k():
+    """Undriven Bethe lattice from its equilibrium: the energy per site,
+    E = eps0 n + E_kin with E_kin = -i [Sigma * G]^<(t,t), stays at its
+    closed form int w A(w) f(w) dw (A the semicircle of half-bandwidth 2
+    centred on eps0; eps0 n is then int eps0 A f) at every step, and its
+    drift falls as h^k (k = 5) when h halves."""
+    from oracle.weights import Weights
+    W = Weights(5)
+    drift, dev = [], []
+    for nt, h in [(40, 0.1), (80, 0.05)]:
+        w = wk.c1_workload(seed=0, nt=nt, h=h, k=5, dlr_eps=1e-12)
+        o = from_workload(w, tol=1e-14)
+        o.run()
+        e0 = w["eps"][0, 1, 0, 0].real
+        # closed forms by Gauss-Chebyshev quadrature of the second kind
+        th = np.arange(1, 4001) * np.pi / 4001
+        om = e0 + 2 * np.cos(th)
+        wq = (2 / np.pi) * np.pi / 4001 * np.sin(th) ** 2
+        f = 0.5 * (1 - np.tanh(0.5 * BETA * om))
+        n_cl, ek_cl = np.sum(wq * f), np.sum(wq * f * (om - e0))
+        E = np.array([[e0 * n + ek.real, ek.imag] for n, ek in (_bethe_energy(o, T, W) for T in range(6, nt))])
+        assert np.abs(E[:, 1]).max() < 1e-12                      # E_kin is real
+        drift.append(np.abs(E[:, 0] - E[0, 0]).max())
+        dev.append(np.abs(E[:, 0] - (e0 * n_cl + ek_cl)).max())
+    assert dev[1] < 1e-6
+    assert drift[1] < 1e-6 and drift[0] / drift[1] > 2 ** 4     # order k = 5 (measured 2^4.7)
