@@ -4,30 +4,45 @@
 One bench "step" is one KBE time step T of the whole batch: extrapolation,
 self-energy, retarded row, mixed, lesser source and column, density matrix,
 the self-consistency loop, and the HODLR compression of that step, for every
-instance.  The run bootstraps, propagates untimed to N_t - 1 - 2K, then
-  e2e window   : K steps through the public C ABI with host buffers: eps(T)
-                 of every instance uploaded from pinned memory, one step,
-                 rho(T) of every instance downloaded into pinned memory;
-  timed window : the last K steps (the most expensive ones), inputs resident
-                 in HBM, CUDA events on the library's stream.
-  value        = instances x K / seconds of the timed window (summed over ranks)
-  roofline     = the dominant history kernel's algorithmic bytes / its device time
-  cpu_baseline = the FP64 oracle on the host cores, on a bounded sample
+instance.  Default workload: C4 (N_t = 8192, Nambu Holstein-Migdal, 76
+instances), the configuration the metric is quoted on.
+
+The timed window is K consecutive time steps starting at T_s, the first step
+at or after N_t/4 after which a leaf is compressed (T_s - k a multiple of the
+leaf), so every window holds its compressions at the rate of one per leaf of
+steps or more (one per window when K < leaf: a conservative figure).  The
+run bootstraps, propagates untimed to T_s - 1, saves a device snapshot, and
+  e2e window    : the K steps through the public C ABI with host buffers: eps(T)
+                  of every instance uploaded from pinned memory, one step,
+                  rho(T) of every instance downloaded into pinned memory;
+  device window : the same K steps again from the restored snapshot, inputs
+                  resident in HBM, CUDA events on the library's stream;
+  phase pass    : the same K steps once more with per-phase CUDA events (phase
+                  shares, the dominant kernel's time for the roofline).
+The plain FP64 form of the same batch then runs the same window (its own
+handle; profiled pass only: its device state leaves no room for a snapshot).
+
+  value        = instances x K / seconds of the device window (mixed form)
+  roofline     = algorithmic bytes of the dominant history kernel per launch /
+                 its mean launch time, against the measured HBM copy bandwidth
+  cpu_baseline = the FP64 oracle stepping the same window, one core and every
+                 core (one instance per process)
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload C2-batch|C2|C1] [--n-inst B] [--precision mixed|fp64]
+                       [--workload C4|C2-batch|C3|C1] [--n-inst B] [--no-fp64]
 """
 from __future__ import annotations
 
 import os
 
-# The CPU baseline is the single-threaded oracle: keep numpy's BLAS on one
-# thread (the GPU arm uses numpy only to build its inputs).
+# The oracle baseline runs one thread per process (cores = processes).
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import statistics
 import subprocess
 import sys
@@ -41,90 +56,134 @@ sys.path.insert(0, ROOT)
 
 import kbe_workloads as wk  # noqa: E402
 
-def _batch_c2(n_inst, seed=0, nt=4096):
-    """C2 (Bethe, quench eps0 0 -> 1 at t=5, N_t=4096, h=0.02, HODLR leaf 64,
-    eps_SVD 1e-8) for a batch: instance 0 is C2 itself, instance i > 0 takes
-    its quench amplitude from U[0.5, 1.5] (numpy default_rng(seed))."""
-    w = wk.c2_workload(nt=nt, n_inst=n_inst)
-    amp = np.concatenate([[1.0], np.random.default_rng(seed).uniform(0.5, 1.5, size=n_inst - 1)])
-    w["eps"][:, 1:, 0, 0] *= amp[:, None]
-    return w
-
-
-def _batch_c4(n_inst, seed=0, nt=8192):
-    """C4-shaped batch: Nambu Bethe DMFT with the Holstein-Migdal term (g=0.5,
-    w0=0.6), beta=50, N_t=8192, h=0.01, pulse A(t) = A0 sin(t) exp(-(t-20)^2/50)
-    with A0 = 0.3 for instance 0 and A0 ~ 0.3 U[0.5, 1.5] for the others,
-    HODLR leaf 64, eps_SVD 1e-7.  Initial state: the normal non-interacting
-    Bethe lattice (closed-form G^M), not the coupled superconducting
-    equilibrium (no Matsubara solver here)."""
-    w = wk.nambu_workload(nt=nt, h=0.01, k=5, beta=50.0, n_inst=n_inst, v=1.0, eps0=0.0, A0=0.3, Omega=1.0,
-                          tc=20.0, width=50.0, g=0.5, w0=0.6, dlr_lambda=200.0, dlr_eps=1e-10)
-    amp = np.concatenate([[1.0], np.random.default_rng(seed).uniform(0.5, 1.5, size=n_inst - 1)])
-    w["drive_A"] = w["drive_A"] * amp[:, None]
-    w["wl"].svd_tol = 1e-7
-    return w
-
-
 WORKLOADS = {
-    "C4-batch": dict(desc="C4-shaped: Nambu Bethe-lattice DMFT, hybridisation with Peierls phases + Holstein-Migdal "
-                          "(g=0.5, w0=0.6), beta=50, N_t=8192, h=0.01, order 5, DLR Lambda=200 eps=1e-10, pulse "
-                          "A(t)=A0 sin(t) exp(-(t-20)^2/50) (A0=0.3 instance 0, 0.3 U[0.5,1.5] others), HODLR "
-                          "leaf 64, eps_SVD 1e-7, normal non-interacting initial state",
-                     make=_batch_c4, n_inst=76, precision="mixed"),
+    "C4": dict(desc="C4: Nambu Bethe-lattice DMFT, hybridisation with Peierls phases + Holstein-Migdal "
+                    "(g=0.5, w0=0.6), beta=50, N_t=8192, h=0.01, order 5, DLR Lambda=200 eps=1e-10, pulse "
+                    "A(t)=A0 sin(t) exp(-(t-20)^2/50) (A0=0.3 instance 0, 0.3 U[0.5,1.5] others), HODLR "
+                    "leaf 64, eps_SVD 1e-7, diagonal rho scheme, normal non-interacting initial state",
+               make=lambda n_inst, seed=0, **kw: wk.c4_batch_workload(n_inst, seed, **kw), n_inst=76, precision="mixed",
+               tol_fp64=1e-12, tol_mixed=1e-7),
     "C2-batch": dict(desc="Bethe lattice (Sigma=v^2 G, v=1), beta=5, N_t=4096, h=0.02, order 5, DLR Lambda=100 "
                           "eps=1e-10, level quench 0 -> A at t=5 (A=1 for instance 0, U[0.5,1.5] for the others), "
                           "HODLR leaf 64, eps_SVD 1e-8, r_max 64",
-                     make=_batch_c2, n_inst=304, precision="mixed"),
-    "C2": dict(desc="C2: Bethe lattice, beta=5, N_t=4096, h=0.02, order 5, quench eps0 0->1 at t=5, "
-                    "HODLR leaf 64, eps_SVD 1e-8, one instance",
-               make=lambda n_inst, seed=0: wk.c2_workload(n_inst=n_inst), n_inst=1, precision="fp64"),
+                     make=lambda n_inst, seed=0, **kw: wk.c2_batch_workload(n_inst, seed, **kw), n_inst=304,
+                     precision="mixed", tol_fp64=1e-12, tol_mixed=1e-7),
     "C3": dict(desc="C3-shaped: 2D Hubbard second Born on a 16 x 16 k-grid (256 coupled instances), J=1, "
                     "half filling, beta=10, N_t=2048, h=0.02, order 5, interaction quenched 0 -> U=2 at t=0 "
                     "(the free lattice as initial state), undriven, HODLR leaf 64, eps_SVD 1e-6",
                make=lambda n_inst, seed=0: wk.lattice_workload(L=16, nt=2048, h=0.02, k=5, beta=10.0, U=2.0,
                                                                 t_quench=0.0, svd_tol=1e-6, leaf=64),
-               n_inst=256, precision="mixed"),
+               n_inst=256, precision="mixed", tol_fp64=1e-12, tol_mixed=1e-7),
     "C1": dict(desc="C1: Bethe lattice, beta=5, N_t=256, h=0.025, order 5, undriven, dense storage",
-               make=lambda n_inst, seed=0: wk.c1_workload(seed=seed, n_inst=n_inst), n_inst=1, precision="fp64"),
+               make=lambda n_inst, seed=0: wk.c1_workload(seed=seed, n_inst=n_inst), n_inst=1,
+               precision="fp64", tol_fp64=1e-12, tol_mixed=1e-7),
 }
+WORKLOADS["C4-batch"] = WORKLOADS["C4"]   # name used by earlier profiles
+C5_DESC = ("C5: 64 independent instances, N_o = 1..4 (16 each: Bethe driven level, Nambu second Born with U "
+           "quenched on and a Peierls drive, and for N_o = 3, 4 a driven level matrix on two bath levels), "
+           "N_t ~ U[512, 4096] per instance, beta=5, h=0.02, order 5, DLR Lambda=100 eps=1e-10, HODLR leaf 64, "
+           "eps_SVD 1e-7, complex64 form; one handle per N_o, the four stepped concurrently from four host "
+           "threads on four CUDA streams")
+
+METRIC = "KBE time steps/s"
+UNIT = "instance time steps/s"
 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
 
 
-def phase_bytes(phase, T, c, nfroz, no, r, L, k, es, blocks, ranks):
-    """Algorithmic bytes one launch of `phase` moves at step T for one
-    instance: every stored element it needs, read once.  es = bytes per
-    element of the two-time storage (rows, leaves, factors, band: 16
-    complex128, 8 complex64); chunk inverses, the row being solved (FP64
-    buffer), projections and mixed components are complex128 in both forms.
-      ret / les: Sigma^R uncompressed rows [c, T], leaf triangles below c,
-                 built factor rows of U and V times rank, band (k per row),
-                 frozen chunk inverses, the solved row (r/w) and its storage;
-      src:       the same for Sigma^< plus the G^R row, Sigma^tv and q(t)."""
-    n2 = no * no
-    direct = sum(s + 1 for s in range(c, T + 1)) * n2 * es if c <= T else 0
-    leaves = (c // L) * (L * (L + 1) // 2) * n2 * es
+def window_start(nt, k, leaf, hodlr):
+    """First step T >= N_t/4 after which a leaf is compressed (T - k is a
+    multiple of the leaf); N_t/4 for dense storage."""
+    T = max(nt // 4, k + 1)
+    if hodlr:
+        while (T - k) % leaf:
+            T += 1
+    return T
+
+
+def history_elements(T, k, L, blocks, rank_of_block, hodlr):
+    """H(T): stored elements (one orbital pair) of one two-time component that
+    the history integrals of step T read.  HODLR: the paper's scheme, whose
+    front is c = T - k (rows older than k + 1 steps are compressed at every
+    step): built block factor rows times the pair's rank plus all factor
+    columns, built leaf triangles, and the k + 1 uncompressed rows s = c..T
+    (s + 1 elements each).  Dense storage: the lower triangle up to row T."""
+    if not hodlr:
+        return (T + 1) * (T + 2) // 2
+    c = T - k
     fac = 0
-    if blocks is not None:
-        for b in range(len(blocks["r0"])):
-            r0, r1, c0, c1 = (int(blocks[x][b]) for x in ("r0", "r1", "c0", "c1"))
-            if r0 >= c:
-                continue
-            fac += ((min(r1, c) - r0) + (c1 - c0)) * int(np.sum(ranks[b])) * es
-    band = c * k * n2 * es if blocks is not None else 0
+    for b in range(len(blocks["r0"])):
+        r0, r1, c0, c1 = (int(blocks[x][b]) for x in ("r0", "r1", "c0", "c1"))
+        if r0 >= c:
+            continue
+        fac += (min(r1, c) - r0 + (c1 - c0)) * int(rank_of_block[b])
+    leaves = 0
+    for j in range(0, c, L):
+        m = min(L, c - j)
+        leaves += m * (m + 1) // 2
+    direct = sum(s + 1 for s in range(c, T + 1))
+    return fac + leaves + direct
+
+
+def history_all_pairs(T, k, L, no, blocks, ranks, hodlr):
+    """H(T) summed over the N_o^2 orbital pairs; ranks[b, p] is the rank of
+    block b, pair p."""
+    if not hodlr:
+        return no * no * history_elements(T, k, L, None, None, False)
+    return sum(history_elements(T, k, L, blocks, ranks[:, p], True) for p in range(no * no))
+
+
+def phase_bytes(phase, T, k, no, r, L, es, blocks, ranks, hodlr):
+    """Algorithmic bytes of one launch of `phase` at step T for one instance
+    (one corrector iteration): every stored element it needs, read once.
+    es = bytes per element of the two-time storage (16 complex128, 8 complex64).
+      ret / les: Sigma^R history H_R(T) plus the row read and written;
+      src:       Sigma^< history H_<(T), the G^R row, Sigma^tv rows (T+1) r
+                 (complex128 in both forms) and q(t) written."""
+    n2 = no * no
+    H = history_all_pairs(T, k, L, no, blocks, ranks, hodlr)
     row = (T + 1) * n2
     if phase in ("ret", "les"):
-        return int(direct + leaves + fac + band + nfroz * (32 * no) ** 2 * 16 + row * (32 + es))
+        return int(H * es + 2 * row * es)
     if phase == "src":
-        return int(direct + leaves + fac + band + row * es + (T + 1) * r * n2 * 16 + row * 16)
+        return int(H * es + row * es + (T + 1) * r * n2 * 16 + row * 16)
     return 0
+
+
+def phase_flops(phase, T, k, no, L, blocks, ranks, hodlr):
+    """Algorithmic real flops of one launch of `phase` (one instance): every
+    history element read enters N_o complex multiply-adds (8 N_o flop)."""
+    if phase not in ("ret", "les", "src"):
+        return 0
+    return int(8 * no * history_all_pairs(T, k, L, no, blocks, ranks, hodlr))
+
+
+KERNEL_OF = {"ret": "k_ret2", "les": "k_les2", "src": "k_src_c"}
+SOURCE_OF = {"ret": "kernels_sweep.cu", "les": "kernels_sweep.cu", "src": "kernels_hodlr.cu"}
+
+
+def traffic_record(phase, n_inst, T):
+    """DRAM bytes per launch of the phase's main kernel from a committed ncu
+    summary (profiles/traffic_<kernel>.json: dram__bytes_read.sum +
+    dram__bytes_write.sum of one capture, per instance, with the sha256 of
+    the kernel source it was taken on), scaled to n_inst instances and to
+    step T in proportion to T.  None when there is no capture or the source
+    has changed since."""
+    kern = KERNEL_OF.get(phase)
+    p = os.path.join(ROOT, "profiles", f"traffic_{kern}.json")
+    if kern is None or not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    src = os.path.join(ROOT, "paper_2604_05319_gb300", "csrc", SOURCE_OF[phase])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec.get("source_sha256"):
+        return None
+    return float(rec["dram_bytes_per_instance"]) * n_inst * (T / float(rec["T"]))
 
 
 class ClockSampler:
@@ -172,44 +231,87 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# ---------------------------------------------------------------------------
+# The oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
 
-
-def oracle_sample(spec, seconds=15.0, seed=0):
-    """Time the FP64 oracle stepping instance 0 of the workload on the host
-    for about `seconds` (from the bootstrap: the early, cheapest steps).  For
-    the lattice the sample is all k-points (they are coupled), on a grid of
-    64 time steps; the rate is counted in instance time steps."""
-    w = spec["make"](n_inst=1, seed=seed)
-    if w["wl"].model == "lattice2b":
-        from oracle.lattice import LatticeOracle
-        wl = w["wl"]
-        nts = 64
-        o = LatticeOracle(w["L"], nts, wl.h, wl.k, wl.beta, w["eps"][:, :nts + 1], w["gm"], w["tau"], w["omega"],
-                          w["drive_U"][0][:nts + 1], tol=wl.tol)
-        o.bootstrap()
+def _oracle_window_worker(job):
+    """One process: the FP64 oracle for instance `inst` of the workload, sized
+    to the window (N = T_s + steps + 1 time points), stepping T_s, T_s+1, ...
+    Its history arrays are zero-filled rather than propagated from the
+    bootstrap (a C4 oracle would need hours to reach T_s); a time step's
+    arithmetic does not depend on the values it reads, and the iteration count
+    is fixed to `iters` (tol 0), the GPU's mean count in that window.  Returns
+    the seconds of every step."""
+    wname, n_inst, seed, inst, T_s, steps, iters = job
+    from oracle.kbe import KBEOracle
+    from oracle.models import make_model
+    spec = WORKLOADS[wname]
+    w = spec["make"](n_inst=n_inst, seed=seed)
+    wl = w["wl"]
+    nt = T_s + steps + 1
+    params = dict(wl.params)
+    if "drive_A" in w:
+        params.update({"A": w["drive_A"][inst][:nt + 1], "U": w["drive_U"][inst][:nt + 1]})
+    o = KBEOracle(nt, wl.h, wl.k, wl.beta, w["eps"][inst][:nt + 1], w["gm"][inst], w["tau"], w["omega"],
+                  make_model(wl.model, params), rho_mode=wl.rho_mode, tol=0.0, max_iter=int(iters))
+    out = []
+    for j in range(steps):
         t0 = time.perf_counter()
-        steps, T = 0, wl.k
-        for T in range(wl.k + 1, nts):
-            o.step(T)
-            steps += 1
-            if time.perf_counter() - t0 > seconds:
-                break
-        dt = time.perf_counter() - t0
-        return steps * len(o.orcs) / dt, steps, dt, T
-    from oracle.kbe import from_workload
-    o = from_workload(w)
-    o.bootstrap()
-    k, nt = w["wl"].k, w["wl"].nt
-    t0 = time.perf_counter()
-    steps, T = 0, k
-    for T in range(k + 1, nt):
-        o.step(T)
-        steps += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    return steps / dt, steps, dt, T
+        o.step(T_s + j)
+        out.append(time.perf_counter() - t0)
+    return out
 
+
+def oracle_window(wname, n_inst, seed, T_s, steps, iters, procs):
+    """The oracle on `procs` host processes (one instance each, spawned), each
+    stepping `steps` time steps from T_s.  Returns (instance steps per second
+    over the slowest process, per-process step times)."""
+    n = min(procs, n_inst)
+    jobs = [(wname, n_inst, seed, i, T_s, steps, iters) for i in range(n)]
+    if n == 1:
+        res = [_oracle_window_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_oracle_window_worker, jobs)
+    wall = max(sum(r) for r in res)
+    return n * steps / wall, res
+
+
+def run_reference(args, wname):
+    """The oracle as it stands, on the GPU machine's host cores, on this arm's
+    window: one process per core (one instance each); a bench step is one
+    time step of every process; W warm-up steps, then K timed steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = WORKLOADS[wname]
+    w = spec["make"](n_inst=1, seed=0)
+    wl = w["wl"]
+    hod = wl.svd_tol > 0
+    T_s = window_start(wl.nt, wl.k, wl.leaf, hod)
+    procs = min(os.cpu_count() or 1, args.n_inst or spec["n_inst"])
+    iters = args.ref_iters
+    v, res = oracle_window(wname, args.n_inst or spec["n_inst"], 0, T_s, args.warmup + args.steps, iters, procs)
+    timed = [r[args.warmup:] for r in res]
+    wall = max(sum(r) for r in timed)
+    val = len(timed) * args.steps / wall
+    sample = (f"oracle (numpy FP64, dense) in {len(timed)} processes (one core and one instance each) "
+              f"stepping time steps {T_s}..{T_s + args.warmup + args.steps - 1} of {wname}; "
+              f"{args.warmup} warm-up steps, then {args.steps} timed; history arrays zero-filled (a time step's "
+              f"arithmetic does not depend on the values), {iters} corrector iterations per step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "desc": spec["desc"], "window_start": T_s},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": len(timed), "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arms
+# ---------------------------------------------------------------------------
 
 def rank_seed(rank):
     """Seed of a rank's instances: every rank propagates its own batch
@@ -227,49 +329,218 @@ def max_over_ranks(values, dist, device):
     return t.tolist()
 
 
-METRIC = "KBE time steps/s"
-UNIT = "instance time steps/s"
+def make_stepper(pk, w, prec, tol):
+    wl = w["wl"]
+    st = pk.Stepper(wl.nt, wl.h, wl.k, wl.beta, nao=wl.nao, n_inst=w["eps"].shape[0], rho_mode=wl.rho_mode,
+                    max_iter=wl.max_iter, tol=tol, precision=prec, svd_tol=wl.svd_tol, leaf=wl.leaf, r_max=64)
+    mid, mpar = pk.model_params_for(w)
+    st.set_inputs(w["tau"], w["omega"], w["gm"], w["eps"], mid, mpar)
+    if "drive_U" in w:
+        pk.hkbe_set_drive(st.h, w["drive_A"], w["drive_U"])
+    st.bootstrap()
+    return st
 
 
-def run_reference(args, spec, wname):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    per_rep = []
-    for rep in range(args.warmup + args.steps):
-        v, steps, dt, Tlast = oracle_sample(spec, seconds=args.ref_seconds, seed=0)
-        if rep >= args.warmup:
-            per_rep.append((v, steps, dt, Tlast))
-    val = statistics.median(p[0] for p in per_rep)
-    steps, dt, Tlast = per_rep[0][1:]
-    sample = (f"oracle (numpy FP64, dense, one thread) on instance 0 of {wname}: bootstrap, then time steps "
-              f"k+1..{Tlast} ({steps} steps, {dt:.1f} s) per rep; median of {args.steps} reps after "
-              f"{args.warmup} warm-up reps")
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "desc": spec["desc"]},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+def roofline_of(pk, st, w, prof, iters, T_s, K, es, dom, n_inst):
+    """Algorithmic bytes and flops of the dominant phase over the window
+    (per-instance iteration counts, ranks at the window start)."""
+    wl = w["wl"]
+    hod = wl.svd_tol > 0
+    no, r = wl.nao, len(w["tau"])
+    blocks = pk.hkbe_get_blocks(st.h) if hod else None
+    nb = len(blocks["r0"]) if hod else 0
+    comp = 3 if dom == "src" else 2
+    nbytes = nflops = 0
+    for i in range(n_inst):
+        rk = pk.hkbe_get_ranks(st.h, i, comp, nb, no)[0] if hod else None
+        for j in range(K):
+            T = T_s + j
+            it = int(iters[j, i])
+            nbytes += it * phase_bytes(dom, T, wl.k, no, r, wl.leaf, es, blocks, rk, hod)
+            nflops += it * phase_flops(dom, T, wl.k, no, wl.leaf, blocks, rk, hod)
+    launches = int(np.sum(iters))  # one launch of the phase per corrector iteration (all instances)
+    t_dom = prof[dom][0] / 1e3
+    return nbytes, nflops, t_dom, launches
+
+
+def run_arm(pk, torch, spec, wname, n_inst, prec_name, K, seed, dist, local, snapshot, want_e2e):
+    """One precision form on the window: returns a dict of measurements."""
+    w = spec["make"](n_inst=n_inst, seed=seed)
+    wl = w["wl"]
+    prec = pk.PREC_MIXED if prec_name == "mixed" else pk.PREC_FP64
+    tol = spec["tol_mixed"] if prec_name == "mixed" else spec["tol_fp64"]
+    nt, k, no = wl.nt, wl.k, wl.nao
+    hod = wl.svd_tol > 0
+    T_s = window_start(nt, k, wl.leaf, hod)
+    K = max(1, min(K, nt - T_s))
+    st = make_stepper(pk, w, prec, tol)
+    t0 = time.perf_counter()
+    st.step(T_s - 1 - k)                       # untimed propagation to T_s - 1
+    torch.cuda.synchronize()
+    t_prop = time.perf_counter() - t0
+    resident = pk.hkbe_get_stats(st.h)
+    out = {"T_s": T_s, "K": K, "t_prop": t_prop, "resident": resident, "w": w}
+    n2 = no * no
+    if snapshot:
+        pk.hkbe_snapshot_save(st.h)
+    # ---- e2e window (public C ABI, host buffers, copies inside the timed region) ----
+    if want_e2e:
+        eps_pin = torch.empty((K, n_inst, n2 * 2), dtype=torch.float64).pin_memory()
+        eps_pin.copy_(torch.from_numpy(np.ascontiguousarray(
+            w["eps"][:, T_s + 1:T_s + 1 + K].transpose(1, 0, 2, 3)).view(np.float64).reshape(K, n_inst, n2 * 2)))
+        rho_pin = torch.empty((K, n_inst, n2 * 2), dtype=torch.float64).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(K):
+            T = T_s + j
+            pk.hkbe_set_hamiltonian_at(st.h, T, eps_pin[j].data_ptr())
+            st.step(1)
+            pk.hkbe_get_density_at(st.h, T, rho_pin[j].data_ptr())
+        torch.cuda.synchronize()
+        out["t_e2e"] = time.perf_counter() - t0
+        out["h2d"] = n_inst * n2 * 16
+        out["d2h"] = n_inst * n2 * 16
+        pk.hkbe_snapshot_restore(st.h)
+    # ---- device window: same steps, inputs resident, no per-phase events ----
+    if snapshot:
+        pk.hkbe_reset_counters(st.h)
+        sampler = ClockSampler(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev_a.record()
+        iters, _ = st.step(K)
+        ev_b.record()
+        torch.cuda.synchronize()
+        out["clocks"] = sampler.stop()
+        out["t_win"] = ev_a.elapsed_time(ev_b) / 1e3
+        out["launches"] = sum(v[1] for v in st.timing().values())
+        pk.hkbe_snapshot_restore(st.h)
+    # ---- phase pass: per-phase CUDA events (profiled) ----
+    pk.hkbe_reset_counters(st.h)
+    pk.hkbe_set_profiling(st.h, True)
+    sampler = None if snapshot else ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()   # ncu --profile-from-start off sees this pass only
+    ev_a.record()
+    iters, _ = st.step(K)
+    ev_b.record()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    pk.hkbe_set_profiling(st.h, False)
+    t_prof = ev_a.elapsed_time(ev_b) / 1e3
+    prof = st.timing()
+    if not snapshot:
+        out["clocks"] = sampler.stop()
+        out["t_win"] = t_prof
+        out["launches"] = sum(v[1] for v in prof.values())
+    out["t_prof"] = t_prof
+    out["iters"] = iters
+    out["prof"] = prof
+    es = 8 if prec == pk.PREC_MIXED else 16
+    dom = max(("ret", "les", "src"), key=lambda p: prof[p][0])
+    nbytes, nflops, t_dom, nl = roofline_of(pk, st, w, prof, iters, T_s, K, es, dom, n_inst)
+    out.update(dom=dom, dom_bytes=nbytes, dom_flops=nflops, t_dom=t_dom, dom_launches=nl)
+    st.close()
+    return out
+
+
+def run_c5(args, pk, torch):
+    """The uneven batch C5: every N_o group is one handle with per-instance
+    N_t, the four handles step concurrently (host threads, one CUDA stream
+    each).  Window: K steps from T_s (the first compression step at or after
+    N_t,max/4); value = instance steps taken in the window / its wall time
+    (the groups run on several streams, so the window is bracketed by device
+    synchronisations and timed on the host)."""
+    from concurrent.futures import ThreadPoolExecutor
+    draws = wk.c5_draws()
+    groups = [wk.c5_group_workload(no, draws) for no in (1, 2, 3, 4)]
+    nt_max = max(g["wl"].nt for g in groups)
+    k, L = groups[0]["wl"].k, groups[0]["wl"].leaf
+    T_s = window_start(nt_max, k, L, True)
+    K = args.steps
+    steppers = []
+    for g in groups:
+        wl = g["wl"]
+        s = torch.cuda.Stream()
+        st = pk.Stepper(wl.nt, wl.h, wl.k, wl.beta, nao=wl.nao, n_inst=wl.n_inst, rho_mode=wl.rho_mode,
+                        max_iter=wl.max_iter, tol=1e-7, precision=pk.PREC_MIXED, svd_tol=wl.svd_tol, leaf=wl.leaf,
+                        r_max=64, stream=s.cuda_stream, nt_per_inst=g["nt_per_inst"])
+        mid, mpar = pk.model_params_for(g)
+        st.set_inputs(g["tau"], g["omega"], g["gm"], g["eps"], mid, mpar)
+        if "drive_U" in g:
+            pk.hkbe_set_drive(st.h, g["drive_A"], g["drive_U"])
+        st.bootstrap()
+        steppers.append((st, s, g))
+    pool = ThreadPoolExecutor(4)
+
+    def advance(to):
+        def one(item):
+            st, s, g = item
+            cur = pk.hkbe_current_step(st.h)
+            n = min(to, g["wl"].nt - 1) - cur
+            return st.step(n)[0] if n > 0 else None
+        return list(pool.map(one, steppers))
+    t0 = time.perf_counter()
+    advance(T_s - 1)
+    torch.cuda.synchronize()
+    t_prop = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = advance(T_s - 1 + K)
+    torch.cuda.synchronize()
+    t_win = time.perf_counter() - t0
+    done = sum(int(np.sum(it > 0)) for it in its if it is not None)
+    total_steps = sum(int(np.sum(g["nt_per_inst"] - 1 - k)) for g in groups)
+    line = {"metric": METRIC, "value": done / t_win, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": T_s - 1 - k,
+            "ms_per_step": t_win / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 storage, f32 bulk sums, f64 point solves and TSVD", "data": "synthetic",
+            "config": {"workload": "C5", "desc": C5_DESC, "n_inst_per_gpu": 64,
+                       "timed_window": f"time steps {T_s}..{T_s + K - 1} of every group (instances past their "
+                                       f"N_t idle); host-timed between device synchronisations",
+                       "instance_steps_in_window": done, "instances_active_at_window_end":
+                           int(sum(np.sum(g["nt_per_inst"] - 1 >= T_s + K - 1) for g in groups)),
+                       "untimed_propagation_s": round(t_prop, 2),
+                       "nt_per_inst_total_steps": total_steps}}
+    for st, s, g in steppers:
+        st.close()
     print(json.dumps(line))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=128, help="time steps per timed window")
-    ap.add_argument("--warmup", type=int, default=3, help="minimum untimed time steps before the windows")
+    ap.add_argument("--steps", type=int, default=64, help="time steps per timed window")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed steps before the window (at least 3; the "
+                                                          "propagation to the window start is longer)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="C2-batch", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C4", choices=sorted(WORKLOADS) + ["C5"])
     ap.add_argument("--n-inst", type=int, default=None, help="instances per GPU (default: the workload's)")
-    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"])
-    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps per process in cpu_baseline")
+    ap.add_argument("--ref-iters", type=int, default=2, help="oracle corrector iterations per step")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
-    spec = WORKLOADS[args.workload]
+    wname = "C4" if args.workload == "C4-batch" else args.workload
+    if wname == "C5":
+        import torch
+        import paper_2604_05319_gb300 as pk
+        if args.impl == "reference":
+            raise SystemExit("C5 has no reference arm; its oracle baseline is C4's")
+        return run_c5(args, pk, torch)
+    spec = WORKLOADS[wname]
     if args.impl == "reference":
-        return run_reference(args, spec, args.workload)
+        return run_reference(args, wname)
 
     import torch
     import paper_2604_05319_gb300 as pk
@@ -283,126 +554,98 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n_inst = args.n_inst or spec["n_inst"]
-    if args.workload == "C3" and n_inst != 256:
+    if wname == "C3" and n_inst != 256:
         raise SystemExit("C3 has one instance per k-point of its 16 x 16 grid: --n-inst must be 256")
-    prec_name = args.precision or spec["precision"]
-    prec = pk.PREC_MIXED if prec_name == "mixed" else pk.PREC_FP64
-    w = spec["make"](n_inst=n_inst, seed=rank_seed(rank))   # each rank its own instances
+    prec_name = spec["precision"]
+    fp64_tf, fp32_tf = pk.hkbe_fma_peaks()
+    main_arm = run_arm(pk, torch, spec, wname, n_inst, prec_name, args.steps, rank_seed(rank), dist, local,
+                       snapshot=True, want_e2e=True)
+    T_s, K = main_arm["T_s"], main_arm["K"]
+    w = main_arm.pop("w")
     wl = w["wl"]
-    nt, k, no, r = wl.nt, wl.k, wl.nao, len(w["tau"])
-    hod = wl.svd_tol > 0
-    K = max(1, min(args.steps, (nt - 1 - k - args.warmup) // 2))
-    T0 = nt - 1 - 2 * K                      # the untimed propagation ends here
-    tol = 1e-7 if prec == pk.PREC_MIXED else wl.tol
-    st = pk.Stepper(nt, wl.h, k, wl.beta, nao=no, n_inst=n_inst, rho_mode=wl.rho_mode,
-                    max_iter=wl.max_iter, tol=tol, precision=prec, svd_tol=wl.svd_tol, leaf=wl.leaf, r_max=64)
-    mid, mp = pk.model_params_for(w)
-    st.set_inputs(w["tau"], w["omega"], w["gm"], w["eps"], mid, mp)
-    if "drive_U" in w:
-        pk.hkbe_set_drive(st.h, w["drive_A"], w["drive_U"])
-    st.bootstrap()
-    # ---- untimed propagation (at least `warmup` time steps) ----
-    t_prop0 = time.perf_counter()
-    st.step(T0 - k)
-    torch.cuda.synchronize()
-    t_prop = time.perf_counter() - t_prop0
-    resident = pk.hkbe_get_stats(st.h)
-    # ---- e2e window: per step, eps(T) host -> device from pinned memory, one
-    # time step, rho(T) device -> host into pinned memory, all through the C ABI
-    n2 = no * no
-    eps_pin = torch.empty((K, n_inst, n2 * 2), dtype=torch.float64).pin_memory()
-    eps_pin.copy_(torch.from_numpy(np.ascontiguousarray(
-        w["eps"][:, T0 + 2:T0 + 2 + K].transpose(1, 0, 2, 3)).view(np.float64).reshape(K, n_inst, n2 * 2)))
-    rho_pin = torch.empty((K, n_inst, n2 * 2), dtype=torch.float64).pin_memory()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j in range(K):
-        T = T0 + 1 + j
-        pk.hkbe_set_hamiltonian_at(st.h, T, eps_pin[j].data_ptr())
-        st.step(1)
-        pk.hkbe_get_density_at(st.h, T, rho_pin[j].data_ptr())
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    h2d = n_inst * n2 * 16
-    d2h = n_inst * n2 * 16
-    # ---- device-timed window: the last K time steps, inputs resident ----
-    blocks = pk.hkbe_get_blocks(st.h) if hod else None
-    nb = len(blocks["r0"]) if hod else 0
-    ranks0 = [pk.hkbe_get_ranks(st.h, i, X, nb, no)[0] for i in range(n_inst) for X in (2, 3)] if hod else None
-    pk.hkbe_reset_counters(st.h)
-    pk.hkbe_set_profiling(st.h, True)
-    sampler = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.cudart().cudaProfilerStart()   # a profiler started with --profile-from-start off sees this window only
-    ev_a.record()
-    iters, _ = st.step(K)
-    ev_b.record()
-    torch.cuda.synchronize()
-    torch.cuda.cudart().cudaProfilerStop()
-    clocks = sampler.stop()
-    t_win = ev_a.elapsed_time(ev_b) / 1e3
-    pk.hkbe_set_profiling(st.h, False)
-    prof = st.timing()
-    launches = sum(v[1] for v in prof.values())
-    t_win, t_e2e = max_over_ranks([t_win, t_e2e], dist, "cuda")
+    fp64_arm = None
+    if prec_name == "mixed" and not args.no_fp64:
+        fp64_arm = run_arm(pk, torch, spec, wname, n_inst, "fp64", K, rank_seed(rank), dist, local,
+                           snapshot=False, want_e2e=False)
+        fp64_arm.pop("w")
+    t_win, t_e2e = max_over_ranks([main_arm["t_win"], main_arm["t_e2e"]], dist, "cuda")
     units = n_inst * K * world
     value = units / t_win
-    # ---- roofline of the dominant history kernel over the window ----
-    dom = max(("ret", "les", "src"), key=lambda p: prof[p][0])
-    es = 8 if prec == pk.PREC_MIXED else 16
-    nbytes = 0
-    for j in range(K):
-        T = T0 + K + 1 + j
-        c = ((T - 1 - k) // wl.leaf) * wl.leaf if hod else 0          # first uncompressed row at step T
-        nfroz = {"ret": max(0, (T - 2 * k) // 32), "les": max(0, T // 32), "src": 0}[dom]
-        for i in range(n_inst):
-            rk = ranks0[2 * i + (1 if dom == "src" else 0)] if hod else None
-            nbytes += int(iters[j, i]) * phase_bytes(dom, T, c, nfroz, no, r, wl.leaf, k, es, blocks, rk)
-    dom_s = prof[dom][0] / 1e3
-    achieved = nbytes / dom_s / 1e9
     peak, peak_kind = peaks()
+    dom = main_arm["dom"]
+    achieved = main_arm["dom_bytes"] / main_arm["t_dom"] / 1e9
+    traffic = traffic_record(dom, n_inst, T_s + K // 2)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, steps, dt, Tlast = oracle_sample(spec, seconds=15.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"instance 0 of {args.workload}: time steps k+1..{Tlast} ({steps} steps, {dt:.1f} s) "
-                         f"from the bootstrap, numpy FP64 dense oracle, one thread (early steps, cheaper than "
-                         f"the GPU's timed window at T > {T0 + K})"}
+        iters_mean = float(np.mean(main_arm["iters"]))
+        it = max(1, int(round(iters_mean)))
+        v1, _ = oracle_window(wname, n_inst, rank_seed(rank), T_s, args.cpu_steps, it, 1)
+        procs = min(os.cpu_count() or 1, n_inst)
+        vall, _ = oracle_window(wname, n_inst, rank_seed(rank), T_s, args.cpu_steps, it, procs)
+        cpu = {"value": vall, "unit": UNIT, "cores": procs, "kind": "oracle", "one_core": v1,
+               "nproc": os.cpu_count(),
+               "sample": f"FP64 dense numpy oracle stepping time steps {T_s}..{T_s + args.cpu_steps - 1} of "
+                         f"{wname} (the start of the GPU window), {it} corrector iterations per step (the GPU's "
+                         f"mean in the window), history arrays zero-filled (a step's arithmetic does not depend "
+                         f"on the values it reads); value: {procs} processes, one core and one instance each; "
+                         f"one_core: one process"}
     if rank == 0:
+        prof = main_arm["prof"]
         tot = sum(v[0] for v in prof.values())
+        comp_steps = sum(1 for T in range(T_s, T_s + K) if wl.svd_tol > 0 and (T - wl.k) % wl.leaf == 0)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": K, "warmup": T0 - k, "ms_per_step": t_win / K * 1e3,
+            "steps": K, "warmup": T_s - 1 - wl.k, "ms_per_step": t_win / K * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 storage, f32 bulk sums, f64 solves" if prec == pk.PREC_MIXED else "f64",
+            "dtype": ("c64 storage, f32 bulk sums and TSVD, f64 point solves" if prec_name == "mixed" else "f64"),
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": spec["desc"], "n_inst_per_gpu": n_inst,
-                       "precision": prec_name, "nt": nt, "h": wl.h, "k": k,
-                       "timed_window": f"time steps {T0 + K + 1}..{nt - 1} (the last {K}); e2e window "
-                                       f"{T0 + 1}..{T0 + K}",
-                       "mean_iterations_per_time_step": float(np.mean(iters)),
-                       "untimed_propagation_s": round(t_prop, 2),
-                       "propagation_avg_steps_per_s": round(n_inst * (T0 - k) / t_prop, 1),
-                       "device_bytes": int(resident),
-                       "l2": f"inputs larger than L2: {resident / 1e9:.1f} GB of state resident"},
-            "roofline": {"bound": "hbm", "kernel": {"ret": "k_ret2", "les": "k_les2", "src": "k_src_h"}[dom],
-                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "bytes_model": "phase_bytes() per instance and corrector iteration, window ranks"},
+            "config": {"workload": wname, "desc": spec["desc"], "n_inst_per_gpu": n_inst,
+                       "precision": prec_name, "nt": wl.nt, "h": wl.h, "k": wl.k,
+                       "timed_window": f"time steps {T_s}..{T_s + K - 1} (first compression step at or after "
+                                       f"N_t/4; {comp_steps} leaf compression(s) inside); e2e and the device "
+                                       f"window run the same steps from one device snapshot",
+                       "mean_iterations_per_time_step": float(np.mean(main_arm["iters"])),
+                       "untimed_propagation_s": round(main_arm["t_prop"], 2),
+                       "propagation_avg_steps_per_s": round(n_inst * (T_s - 1 - wl.k) / main_arm["t_prop"], 1),
+                       "device_bytes": int(main_arm["resident"]),
+                       "l2": f"inputs larger than L2: {main_arm['resident'] / 1e9:.1f} GB of state resident"},
+            "roofline": {"bound": "hbm", "kernel": KERNEL_OF[dom], "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "bytes_per_launch": main_arm["dom_bytes"] / max(1, main_arm["dom_launches"]),
+                         "mean_launch_ms": main_arm["t_dom"] / max(1, main_arm["dom_launches"]) * 1e3,
+                         "bytes_model": "Sigma history H(T) of the paper's scheme (factor rows x rank, leaf "
+                                        "triangles, k+1 uncompressed rows) per instance and corrector iteration, "
+                                        "ranks at the window start"},
             "phase_share": {k2: round(v[0] / tot, 4) for k2, v in prof.items() if v[0] > 0},
+            "alu_peaks": {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "how": "hkbe_fma_peaks, CUDA events"},
             "cpu_baseline": cpu,
-            "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": main_arm["h2d"],
+                    "d2h_bytes_per_step": main_arm["d2h"]},
+            "gpu_launches": main_arm["launches"],
+            "clocks": main_arm["clocks"],
         }
+        if fp64_arm is not None:
+            f = fp64_arm
+            fval = n_inst * f["K"] * world / f["t_win"]
+            fprof = f["prof"]
+            ftot = sum(v[0] for v in fprof.values())
+            line["fp64"] = {
+                "value": fval, "unit": UNIT, "ms_per_step": f["t_win"] / f["K"] * 1e3,
+                "mixed_over_fp64": value / fval,
+                "timed_window": f"time steps {f['T_s']}..{f['T_s'] + f['K'] - 1}, per-phase events on",
+                "mean_iterations_per_time_step": float(np.mean(f["iters"])),
+                "untimed_propagation_s": round(f["t_prop"], 2),
+                "device_bytes": int(f["resident"]),
+                "roofline": {"bound": "alu", "kernel": KERNEL_OF[f["dom"]],
+                             "achieved": f["dom_flops"] / f["t_dom"] / 1e12, "peak": fp64_tf,
+                             "peak_kind": "measured (hkbe_fma_peaks)", "unit": "TFLOP/s",
+                             "frac": f["dom_flops"] / f["t_dom"] / 1e12 / fp64_tf,
+                             "hbm_frac": f["dom_bytes"] / f["t_dom"] / 1e9 / peak},
+                "phase_share": {k2: round(v[0] / ftot, 4) for k2, v in fprof.items() if v[0] > 0},
+                "clocks": f["clocks"],
+            }
         print(json.dumps(line))
-    st.close()
     if dist:
         dist.destroy_process_group()
 

@@ -62,13 +62,16 @@ enum {
   HKBE_PREC_FP64 = 0,     /* complex128 storage of every two-time and mixed
                              component (dense triangles or HODLR factors); FP64
                              arithmetic throughout                               */
-  HKBE_PREC_MIXED = 1     /* complex64 storage of G, Sigma (two-time and mixed),
-                             HODLR factors, band and chunk inverses; every point
-                             solve, the TSVD core, weights, DLR matrices and
-                             accumulations stay FP64.  Expected deviation from
-                             the FP64 form: about 1e-6 relative (single-precision
-                             rounding of the stored history; a GPU design choice,
-                             the paper computes in FP64 throughout)             */
+  HKBE_PREC_MIXED = 1,    /* complex64 storage of the two-time components
+                             (rows, HODLR factors, leaves, band); FP32 bulk
+                             history sums and FP32 TSVD; the row being solved,
+                             every point solve, the mixed components, weights
+                             and DLR matrices stay FP64.  Expected deviation
+                             from the FP64 form: about 1e-6 relative (single-
+                             precision rounding of the stored history; a GPU
+                             design choice, the paper computes in FP64)          */
+  HKBE_PREC_TF32X3 = 2,   /* not provided: rejected by hkbe_create (see there) */
+  HKBE_PREC_BF16X3 = 3    /* not provided: rejected by hkbe_create (see there) */
 };
 
 typedef struct {
@@ -91,10 +94,21 @@ typedef struct {
 
 typedef struct hkbe_s hkbe_t;
 
-/* Create a stepper for p->n_inst instances sharing nt, k, nao, h, beta.
- * `stream` is a cudaStream_t (or NULL).  On success *out receives the handle.
- * Errors: HKBE_ERR_ARG (bad sizes), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
-int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out);
+/* Create a stepper for p->n_inst instances sharing k, nao, h, beta and the
+ * storage form (Sec. 3.1 objects; the Sec. 4 examples construct one per
+ * system).  nt_per_inst[n_inst] (or NULL: every instance runs p->nt steps)
+ * gives each instance its own number of time steps N_t,n in k+2..p->nt: an
+ * instance takes part in the steps T <= N_t,n - 1 and is left untouched after
+ * them (its iteration count and error are 0 there), its HODLR compression
+ * front freezes at its last whole leaf of rows older than k + 1 steps, and
+ * its rows stay readable up to N_t,n - 1.  The lattice model needs one N_t
+ * for every k-point (hkbe_set_model refuses otherwise).  `stream` is a
+ * cudaStream_t (or NULL).  On success *out receives the handle.  Errors:
+ * HKBE_ERR_ARG (bad sizes; precision HKBE_PREC_TF32X3 or HKBE_PREC_BF16X3,
+ * whose operand splitting serves dense tensor-core contractions, of which
+ * this path has none: every history sum is a per-instance matrix-vector
+ * product), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
+int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, hkbe_t** out);
 
 /* Equilibrium Dyson equation on the DLR grid (Eq. KBEM, Sec. 2.5, 3.2),
  * solved self-consistently on the host: prepares G^M of an interacting
@@ -221,7 +235,11 @@ int hkbe_set_initial_slices(hkbe_t* h, const double* gr, const double* gl, const
  * per iteration Sigma, retarded row, mixed, lesser column, density matrix,
  * until max |G^(i) - G^(i-1)| < tol or max_iter).  Outputs (may be NULL):
  * iters[n_inst*n_steps], err[n_inst*n_steps].  Errors: HKBE_ERR_RANGE (past
- * nt-1), HKBE_ERR_NOCONV (state kept; the step counter still advances). */
+ * nt-1), HKBE_ERR_NOCONV (state kept; the step counter still advances: the
+ * self-consistency loop reached max_iter, or, HODLR form, the Jacobi SVD of a
+ * TSVD block core did not converge in 40 sweeps), HKBE_ERR_RANK (a block's
+ * epsilon-rank was capped at r_max).  The TSVD conditions are counted over
+ * the n_steps of this call and reset afterwards. */
 int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err);
 
 /* Current time step T (the last completed step), -1 before the bootstrap. */
@@ -272,8 +290,13 @@ int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out);
  * 0..current step.  Synchronous. */
 int hkbe_get_observables(hkbe_t* h, int t, double* rho, double* ekin, double* current);
 
-/* Device bytes held by the handle. */
-int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes);
+/* Device bytes held by the handle (snapshot copies not included) and, HODLR
+ * form, the epsilon-ranks of instance `inst`: ranks[4][nblk][nao*nao] for the
+ * components G^R, G^<, Sigma^R, Sigma^< (block order of hkbe_get_blocks; 0 for
+ * a block with no row built yet).  Either output may be NULL (ranks must be
+ * NULL for a dense handle).  Errors: HKBE_ERR_ARG (null handle, bad instance,
+ * ranks on a dense handle), HKBE_ERR_CUDA. */
+int hkbe_get_stats(hkbe_t* h, int inst, int32_t* ranks, size_t* device_bytes);
 
 /* HODLR geometry (Sec. 2.2, Fig. 2): *nblk blocks; each of the arrays (may be
  * NULL, length >= *nblk when given) receives rows [r0, r1), columns [c0, c1)
@@ -294,6 +317,28 @@ int hkbe_get_ranks(hkbe_t* h, int inst, int comp, int32_t* ranks, int32_t* first
  * Errors: HKBE_ERR_ARG before the bootstrap. */
 int hkbe_rewind(hkbe_t* h);
 
+/* In-memory checkpoint of the whole propagation state (Sec. 3.6 keeps the
+ * full state in checkpoint files for a restart; this keeps one copy in device
+ * memory instead).  hkbe_snapshot_save copies every device buffer of the
+ * handle (hkbe_get_stats bytes) into a second device allocation made on the
+ * first call and reused afterwards, together with the step counter and the
+ * compression front.  hkbe_snapshot_restore copies it back: stepping the
+ * restored handle repeats the run from the saved step bit for bit.
+ * hkbe_snapshot_free releases the copy (hkbe_destroy does too).  Both run on
+ * the handle's stream and return after it has finished.  Errors:
+ * HKBE_ERR_ARG (null, before the bootstrap, restore without a saved copy),
+ * HKBE_ERR_NOMEM (the copy does not fit), HKBE_ERR_CUDA. */
+int hkbe_snapshot_save(hkbe_t* h);
+int hkbe_snapshot_restore(hkbe_t* h);
+int hkbe_snapshot_free(hkbe_t* h);
+
+/* Measured FP64 and FP32 fused multiply-add throughput of the current CUDA
+ * device in TFLOP/s (2 flop per FMA; many independent FMA chains, CUDA-event
+ * timed, about 50 ms in all): the ALU peaks the FP64 history sums and the
+ * FP32 bulk sums are compared with.  No handle; the paper has no
+ * counterpart.  Errors: HKBE_ERR_ARG (null), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
+int hkbe_fma_peaks(double* fp64_tflops, double* fp32_tflops);
+
 /* Checkpoint (Sec. 3.6, checkpoint files: the full simulation state, restart
  * through a constructor).  hkbe_save writes to `path` the parameters, the
  * host-side set-up (DLR grid, G^M, eps, model, step counter, compression
@@ -302,7 +347,7 @@ int hkbe_rewind(hkbe_t* h);
  * handle's stream.  hkbe_load creates a new handle on `stream` from such a
  * file: propagating it continues the saved run bit for bit on the same
  * build and GPU type.  The format is this library's own binary layout
- * (magic "HKBECKP1", version 1), not HDF5, and is read on a machine of the
+ * (magic "HKBECKP1", version 2: with the checksum trailer and the per-instance N_t), not HDF5, and is read on a machine of the
  * same byte order.  Its last 8 bytes are a checksum of everything before
  * them: FNV-1a 64 over the bytes taken as little-endian 64-bit words, the
  * last word zero-padded (offset basis 14695981039346656037, prime
@@ -376,18 +421,20 @@ int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta
 #define HKBE_NOALLOC_SCRATCH_CPLX 65536
 
 /* The lesser column of one time step, x_t = G^<(t, T) for t = 0..T (the
- * source q of Eq. KBEL followed by the lesser VIDE, horizontal density
- * matrix), computed from buffers the caller already owns and WITHOUT any
- * device allocation.  It is meant for callers that cannot call cudaMalloc
- * (for example code running inside a memory allocator's callbacks, or in a
- * process whose device memory is all handed to another framework); they cannot
- * use hkbe_create, which allocates the handle's arrays.  The same kernels as
- * hkbe_step's lesser phase run here; their scratch (the mixed-product vector,
- * the boundary value and the lesser source, r*nao^2 + nao^2 + nt*nao^2 + 2
- * complex doubles) lives in one file-scope device array of
- * HKBE_NOALLOC_SCRATCH_CPLX entries that every GPU loading the library holds
- * until the process exits.  Sizes beyond it are rejected with HKBE_ERR_ARG
- * and a message saying so.
+ * lesser source followed by the lesser integral equation of a time step,
+ * horizontal density matrix), computed from buffers the caller already owns
+ * and WITHOUT any device allocation.  It is meant for callers that cannot
+ * call cudaMalloc (for example code running inside a memory allocator's
+ * callbacks, or in a process whose device memory is all handed to another
+ * framework); they cannot use hkbe_create, which allocates the handle's
+ * arrays.  It runs the library's point-by-point dense lesser kernels (the
+ * source, then one point solve per t); hkbe_step's dense FP64 form computes
+ * the same column with its chunked sweep, equal up to rounding.  Their
+ * scratch (the mixed-product vector, the boundary value and the lesser
+ * source, r*nao^2 + nao^2 + nt*nao^2 + 2 complex doubles) lives in one
+ * file-scope device array of HKBE_NOALLOC_SCRATCH_CPLX entries that every
+ * GPU loading the library holds until the process exits.  Sizes beyond it
+ * are rejected with HKBE_ERR_ARG and a message saying so.
  *
  * All array arguments are DEVICE pointers to one instance in the dense layout
  * of the handle API: lower-triangular arrays of nt(nt+1)/2 N_o x N_o complex
@@ -403,12 +450,17 @@ int hkbe_dlr_matrices(int r, const double* tau, const double* omega, double beta
  * T the step with k < T < nt.  Work is queued on `stream` (NULL: legacy
  * default stream); the call returns without waiting for it.
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the array, which keeps the previous
- * call's contents; calls that overlap on the GPU (other streams, other host
- * threads) race on it, so serialise them.  On failure the message is copied
- * into errbuf[errlen] (may be NULL). */
+ * The first call on a device does a one-time set-up with that device
+ * current: it looks up the scratch array's device address
+ * (cudaGetSymbolAddress).  With lazy module loading (the CUDA default) that
+ * lookup also loads the library's device code and the array onto the
+ * device, which allocates device memory.  So make the first call on each
+ * device outside any context that forbids allocation, and before any stream
+ * capture; later calls allocate nothing.  The set-up is safe to race from
+ * several host threads.  Every call shares the array, which keeps the
+ * previous call's contents; calls that overlap on the GPU (other streams,
+ * other host threads) race on it, so serialise them.  On failure the
+ * message is copied into errbuf[errlen] (may be NULL). */
 int hkbe_lesser_column_noalloc(int nt, int k, int nao, int r, double h, int T,
                                const void* d_gr, const void* d_sr, const void* d_sl,
                                const void* d_gtv, const void* d_stv, const void* d_eps,

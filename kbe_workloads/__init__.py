@@ -291,3 +291,116 @@ def lattice_workload(L=4, nt=120, h=0.02, k=5, beta=10.0, U=2.0, t_quench=0.0, A
     return {"wl": wl, "tau": tau, "omega": om, "eps": eps, "gm": gm, "L": L, "kx": kx, "ky": ky,
             "model_params": np.array([[float(L)]] * nk), "drive_A": np.tile(A, (nk, 1)),
             "drive_U": np.tile(Uv, (nk, 1))}
+
+
+# ---------------------------------------------------------------------------
+# Batched workloads of the benchmark (many independent instances of one
+# configuration; each instance is an input set, nothing is solved here)
+# ---------------------------------------------------------------------------
+
+def c2_batch_workload(n_inst, seed=0, nt=4096):
+    """C2 for a batch: Bethe, quench eps0 0 -> A at t = 5, N_t = 4096,
+    h = 0.02, HODLR leaf 64, eps_SVD 1e-8; instance 0 has A = 1 (C2 itself),
+    instance i > 0 takes A ~ U[0.5, 1.5] from numpy default_rng(seed)."""
+    w = c2_workload(nt=nt, n_inst=n_inst)
+    amp = np.concatenate([[1.0], np.random.default_rng(seed).uniform(0.5, 1.5, size=n_inst - 1)])
+    w["eps"][:, 1:, 0, 0] *= amp[:, None]
+    return w
+
+
+def c4_batch_workload(n_inst, seed=0, nt=8192, rho_mode=1):
+    """C4-shaped batch: Nambu Bethe-lattice DMFT with the Holstein-Migdal term
+    (g = 0.5, w0 = 0.6), beta = 50, N_t = 8192, h = 0.01, order 5, DLR
+    Lambda = 200, eps = 1e-10, pulse A(t) = A0 sin(t) exp(-(t-20)^2/50), HODLR
+    leaf 64, eps_SVD 1e-7, diagonal density-matrix scheme (driven).  Instance
+    0 has A0 = 0.3; instance i > 0 takes A0 = 0.3 U[0.5, 1.5] from numpy
+    default_rng(seed).  Initial state: the normal non-interacting Bethe
+    lattice (closed-form G^M); the coupling is on from t = 0."""
+    w = nambu_workload(nt=nt, h=0.01, k=5, beta=50.0, n_inst=n_inst, v=1.0, eps0=0.0, A0=0.3, Omega=1.0,
+                       tc=20.0, width=50.0, g=0.5, w0=0.6, dlr_lambda=200.0, dlr_eps=1e-10, rho_mode=rho_mode)
+    amp = np.concatenate([[1.0], np.random.default_rng(seed).uniform(0.5, 1.5, size=n_inst - 1)])
+    w["drive_A"] = w["drive_A"] * amp[:, None]
+    w["wl"].svd_tol = 1e-7
+    return w
+
+
+def bath_gm(tau, beta, eps0, V, eb):
+    """G^M of the impurity block of the quadratic problem
+    H = [[eps0, V], [V^dagger, diag(eb)]] (exact diagonalisation)."""
+    H = np.block([[np.asarray(eps0, complex), np.asarray(V, complex)],
+                  [np.asarray(V, complex).conj().T, np.diag(np.asarray(eb, float)).astype(complex)]])
+    no = np.asarray(eps0).shape[0]
+    return free_level_gm(tau, beta, H)[:, :no, :no]
+
+
+C5_BATH_LEVELS = np.array([0.7, -0.9])
+
+
+def c5_draws(n_inst=64, seed=0, nt_lo=512, nt_hi=4096):
+    """Per-instance draws of the uneven batch C5 from numpy default_rng(seed):
+    orbital count N_o in {1, 2, 3, 4} (equal shares), N_t ~ U[nt_lo, nt_hi]
+    (integer), level entries ~ U[-0.5, 0.5] (Hermitian), drive amplitude
+    A0 ~ U[0.1, 0.5], frequency Omega ~ U[0.5, 1.5], interaction U ~ U[0.5, 2]
+    (Nambu instances), bath couplings ~ U[-0.5, 0.5] (N_o = 3, 4)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        no = 1 + i % 4
+        e = rng.uniform(-0.5, 0.5, size=(no, no)) + 1j * rng.uniform(-0.5, 0.5, size=(no, no))
+        out.append(dict(nao=no, nt=int(rng.integers(nt_lo, nt_hi + 1)), eps0=0.5 * (e + e.conj().T),
+                        A0=float(rng.uniform(0.1, 0.5)), Omega=float(rng.uniform(0.5, 1.5)),
+                        U=float(rng.uniform(0.5, 2.0)), V=rng.uniform(-0.5, 0.5, size=(no, 2))))
+    return out
+
+
+def c5_group_workload(nao, draws, h=0.02, k=5, beta=5.0, svd_tol=1e-7, leaf=64):
+    """The instances of C5 with N_o = nao as one batch (one handle): inputs
+    up to the group's longest N_t, and per-instance N_t in "nt_per_inst".
+      N_o = 1: Bethe lattice (Sigma = v^2 G, v = 1), level eps0 + A0 sin(Omega t);
+      N_o = 2: Nambu DMFT, level diag(e, -e) (e the drawn diagonal), second Born
+               with U quenched on at t = 0, Peierls drive A0 sin(Omega t);
+      N_o = 3, 4: the level matrix coupled to two bath levels (0.7, -0.9) by
+               the drawn V (fixed Sigma = V g_b V^dagger), level
+               eps0 + A0 sin(Omega t) times the identity.
+    Initial states: the non-interacting equilibria (closed forms)."""
+    ds = [d for d in draws if d["nao"] == nao]
+    n = len(ds)
+    nt = max(d["nt"] for d in ds)
+    tau, om = dlr_grid(100.0, 1e-10, beta)
+    r = len(tau)
+    tt = np.concatenate([[0.0], np.arange(nt) * h])      # index 0: the equilibrium branch
+    eps = np.zeros((n, nt + 1, nao, nao), complex)
+    gm = np.zeros((n, r, nao, nao), complex)
+    extra = {}
+    if nao == 1:
+        for i, d in enumerate(ds):
+            e0 = d["eps0"][0, 0].real
+            eps[i, :, 0, 0] = e0 + d["A0"] * np.sin(d["Omega"] * tt) * (np.arange(nt + 1) > 0)
+            gm[i, :, 0, 0] = semicircle_gm(tau, beta, e0)
+        model, mp = "bethe", np.ones((n, 1))
+    elif nao == 2:
+        As, Us = [], []
+        for i, d in enumerate(ds):
+            e0 = d["eps0"][0, 0].real
+            eps[i] = np.diag([e0, -e0])
+            gm[i, :, 0, 0] = semicircle_gm(tau, beta, e0)
+            gm[i, :, 1, 1] = semicircle_gm(tau, beta, -e0)
+            A = np.concatenate([[0.0], d["A0"] * np.sin(d["Omega"] * tt[1:])])
+            As.append(A)
+            Us.append(np.concatenate([[0.0], np.full(nt, d["U"])]))
+        model, mp = "nambu", np.ones((n, 1))
+        extra = {"drive_A": np.array(As), "drive_U": np.array(Us)}
+    else:
+        mp = []
+        for i, d in enumerate(ds):
+            drive = d["A0"] * np.sin(d["Omega"] * tt) * (np.arange(nt + 1) > 0)
+            eps[i] = d["eps0"][None] + drive[:, None, None] * np.eye(nao)[None]
+            gm[i] = bath_gm(tau, beta, d["eps0"], d["V"], C5_BATH_LEVELS)
+            Vc = np.asarray(d["V"], complex)
+            mp.append(np.concatenate([[2.0], C5_BATH_LEVELS, np.stack([Vc.real, Vc.imag], -1).ravel()]))
+        model, mp = "bath", np.array(mp)
+    wl = Workload(name=f"C5-no{nao}", model=model, nt=nt, h=h, k=k, beta=beta, nao=nao, n_inst=n,
+                  svd_tol=svd_tol, leaf=leaf, rho_mode=1, params={"v": 1.0} if model != "bath" else
+                  {"V": None, "eb": C5_BATH_LEVELS})
+    return dict({"wl": wl, "tau": tau, "omega": om, "eps": eps, "gm": gm, "model_params": mp,
+                 "nt_per_inst": np.array([d["nt"] for d in ds], np.int32)}, **extra)

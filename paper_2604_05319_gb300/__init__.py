@@ -19,12 +19,15 @@ import numpy as np
 from . import _build
 
 HKBE_OK = 0
-HKBE_ERR_IO = -8
+HKBE_ERR_ARG, HKBE_ERR_CUDA, HKBE_ERR_NOCONV, HKBE_ERR_RANGE, HKBE_ERR_RANK = -1, -2, -3, -4, -5
+HKBE_ERR_NAN, HKBE_ERR_NOMEM, HKBE_ERR_IO = -6, -7, -8
 ERRORS = {-1: "HKBE_ERR_ARG", -2: "HKBE_ERR_CUDA", -3: "HKBE_ERR_NOCONV", -4: "HKBE_ERR_RANGE",
           -5: "HKBE_ERR_RANK", -6: "HKBE_ERR_NAN", -7: "HKBE_ERR_NOMEM", -8: "HKBE_ERR_IO"}
 MODEL_NONE, MODEL_BETHE, MODEL_BATH, MODEL_NAMBU, MODEL_LATTICE2B = 0, 1, 2, 3, 4
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_TF32X3 = 2   # rejected by hkbe_create (no dense contraction on this path)
+PREC_BF16X3 = 3   # rejected by hkbe_create
 
 
 class HKBEError(RuntimeError):
@@ -61,7 +64,7 @@ def load(build_if_missing: bool = True):
     L = C.CDLL(_build.LIB)
     H = C.c_void_p
     sig = {
-        "hkbe_create": ([C.POINTER(hkbe_params), C.c_void_p, C.POINTER(H)], C.c_int),
+        "hkbe_create": ([C.POINTER(hkbe_params), _I, C.c_void_p, C.POINTER(H)], C.c_int),
         "hkbe_destroy": ([H], C.c_int),
         "hkbe_last_error": ([H], C.c_char_p),
         "hkbe_set_dlr": ([H, C.c_int, _D, _D], C.c_int),
@@ -87,8 +90,12 @@ def load(build_if_missing: bool = True):
         "hkbe_get_tv": ([H, C.c_int, C.c_int, _D], C.c_int),
         "hkbe_get_row": ([H, C.c_int, C.c_int, _D, _D], C.c_int),
         "hkbe_get_density": ([H, _D], C.c_int),
-        "hkbe_get_stats": ([H, C.POINTER(C.c_size_t)], C.c_int),
+        "hkbe_get_stats": ([H, C.c_int, _I, C.POINTER(C.c_size_t)], C.c_int),
         "hkbe_rewind": ([H], C.c_int),
+        "hkbe_snapshot_save": ([H], C.c_int),
+        "hkbe_snapshot_restore": ([H], C.c_int),
+        "hkbe_snapshot_free": ([H], C.c_int),
+        "hkbe_fma_peaks": ([_D, _D], C.c_int),
         "hkbe_get_blocks": ([H, _I, _I, _I, _I, _I, _I], C.c_int),
         "hkbe_get_ranks": ([H, C.c_int, C.c_int, _I, _I], C.c_int),
         "hkbe_set_profiling": ([H, C.c_int], C.c_int),
@@ -135,9 +142,15 @@ def _check(rc, h=None):
 
 # ---- one-to-one wrappers of the C ABI -------------------------------------
 
-def hkbe_create(params: hkbe_params, stream=None):
+def hkbe_create(params: hkbe_params, stream=None, nt_per_inst=None):
+    """nt_per_inst: None (every instance runs params.nt steps) or one N_t per instance."""
     h = C.c_void_p()
-    _check(load().hkbe_create(C.byref(params), stream, C.byref(h)), None)
+    ntp = None
+    if nt_per_inst is not None:
+        ntp = np.ascontiguousarray(nt_per_inst, dtype=np.int32)
+        if ntp.shape != (params.n_inst,):
+            raise ValueError("nt_per_inst needs one entry per instance")
+    _check(load().hkbe_create(C.byref(params), None if ntp is None else _ip(ntp), stream, C.byref(h)), None)
     return h
 
 
@@ -313,14 +326,39 @@ def hkbe_get_density(h, n_inst, nao, T):
     return out
 
 
-def hkbe_get_stats(h):
+def hkbe_get_stats(h, inst=None, nblk=0, nao=1):
+    """Device bytes; with inst given (HODLR handle), also the ranks
+    [4 components][nblk][nao*nao] of that instance."""
     b = C.c_size_t()
-    _check(load().hkbe_get_stats(h, C.byref(b)), h)
-    return int(b.value)
+    if inst is None:
+        _check(load().hkbe_get_stats(h, 0, None, C.byref(b)), h)
+        return int(b.value)
+    r = np.zeros(max(1, 4 * nblk * nao * nao), np.int32)
+    _check(load().hkbe_get_stats(h, int(inst), _ip(r), C.byref(b)), h)
+    return int(b.value), r[:4 * nblk * nao * nao].reshape(4, nblk, nao * nao)
 
 
 def hkbe_rewind(h):
     _check(load().hkbe_rewind(h), h)
+
+
+def hkbe_snapshot_save(h):
+    _check(load().hkbe_snapshot_save(h), h)
+
+
+def hkbe_snapshot_restore(h):
+    _check(load().hkbe_snapshot_restore(h), h)
+
+
+def hkbe_snapshot_free(h):
+    _check(load().hkbe_snapshot_free(h), h)
+
+
+def hkbe_fma_peaks():
+    """(FP64, FP32) fused multiply-add throughput of the current device, TFLOP/s."""
+    a, b = np.zeros(1), np.zeros(1)
+    _check(load().hkbe_fma_peaks(_dp(a), _dp(b)))
+    return float(a[0]), float(b[0])
 
 
 def hkbe_get_blocks(h):
@@ -409,12 +447,12 @@ class Stepper:
     """Owns one handle; inputs are numpy arrays shaped as in include/hkbe.h."""
 
     def __init__(self, nt, h, k, beta, nao=1, n_inst=1, rho_mode=0, max_iter=50, tol=1e-12,
-                 precision=PREC_FP64, svd_tol=0.0, leaf=64, r_max=64, stream=None):
+                 precision=PREC_FP64, svd_tol=0.0, leaf=64, r_max=64, stream=None, nt_per_inst=None):
         self.p = hkbe_params(nt=nt, k=k, nao=nao, xi=-1, n_inst=n_inst, rho_mode=rho_mode,
                              precision=precision, max_iter=max_iter, h=h, beta=beta, tol=tol,
                              svd_tol=svd_tol, leaf=leaf, r_max=r_max)
         self.nao, self.n_inst, self.nt = nao, n_inst, nt
-        self.h = hkbe_create(self.p, stream)
+        self.h = hkbe_create(self.p, stream, nt_per_inst)
         self.r = 0
 
     def close(self):
@@ -486,4 +524,6 @@ def model_params_for(workload_dict):
         return MODEL_NAMBU, np.asarray(workload_dict["model_params"], dtype=float)
     if wl.model == "lattice2b":
         return MODEL_LATTICE2B, np.asarray(workload_dict["model_params"], dtype=float)
+    if wl.model == "bath":   # per instance [nb, eps_b[nb], V[nao][nb] as (re, im) pairs]
+        return MODEL_BATH, np.asarray(workload_dict["model_params"], dtype=float)
     raise ValueError(wl.model)

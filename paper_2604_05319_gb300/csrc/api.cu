@@ -21,6 +21,7 @@ struct hkbe_s {
   cudaStream_t s = nullptr;
   std::string err;
   int cur = -1;
+  std::vector<int> last;   // last time step of each instance (its N_t - 1)
   bool have_dlr = false, have_gm = false, have_eps = false, have_model = false;
   bool self_consistent = true;
   std::vector<double> tau, om, gm_host, eps_host;
@@ -49,6 +50,11 @@ struct hkbe_s {
   // device arrays that make up the propagation state, zeroed by hkbe_rewind so
   // that a rewound run starts from exactly the state that followed bootstrap
   std::vector<std::pair<void*, size_t>> state_arrays;
+  // in-memory snapshot (hkbe_snapshot_save): a device copy of every buffer in
+  // allocs, plus the host-side counters that go with it
+  std::vector<void*> snap_dev;
+  size_t snap_bytes = 0;
+  int snap_cur = -1, snap_cdir = 0, snap_nfrozR = 0, snap_nfrozL = 0;
 };
 
 namespace {
@@ -131,6 +137,15 @@ int dalloc_tv(hkbe_t* h, void** p, size_t count) {
 }
 
 int no2(const hkbe_t* h) { return h->p.nao * h->p.nao; }
+
+// Last computed step of instance n (an instance stops at its own N_t - 1).
+int cur_of(const hkbe_t* h, int n) { return std::min(h->cur, h->last[n]); }
+// First uncompressed row of instance n (the device-side front_of).
+int front_host(const hkbe_t* h, int n) {
+  const int lk = h->last[n] - h->d.k;
+  const int fz = lk >= h->d.L ? (lk / h->d.L) * h->d.L : 0;
+  return std::min(h->d.cdir, fz);
+}
 
 // bytes of one complex storage element
 size_t esz(const hkbe_t* h) { return h->d.prec ? sizeof(float2) : sizeof(double2); }
@@ -237,9 +252,14 @@ extern "C" {
 
 const char* hkbe_last_error(const hkbe_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
+int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, hkbe_t** out) {
   if (!p || !out) return fail(nullptr, HKBE_ERR_ARG, "null argument");
   *out = nullptr;
+  if (p->precision == HKBE_PREC_TF32X3 || p->precision == HKBE_PREC_BF16X3)
+    return fail(nullptr, HKBE_ERR_ARG,
+                "precision 2 (FP32 + 3xTF32 split) and 3 (BF16x3 split) are not provided: they split the operands "
+                "of a dense contraction for the tensor cores, and every history sum here is a per-instance "
+                "matrix-vector product; use HKBE_PREC_MIXED for the reduced-precision form");
   if (p->k < 1 || p->k > 5) return fail(nullptr, HKBE_ERR_ARG, "k must be in 1..5");
   if (p->nt < p->k + 2) return fail(nullptr, HKBE_ERR_ARG, "nt must be >= k + 2");
   if (p->nao < 1 || p->nao > 4) return fail(nullptr, HKBE_ERR_ARG, "nao must be in 1..4");
@@ -251,6 +271,10 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
     return fail(nullptr, HKBE_ERR_ARG, "precision must be HKBE_PREC_FP64 or HKBE_PREC_MIXED");
   if (p->max_iter < 1) return fail(nullptr, HKBE_ERR_ARG, "max_iter must be >= 1");
   if (p->svd_tol < 0) return fail(nullptr, HKBE_ERR_ARG, "svd_tol must be >= 0");
+  if (nt_per_inst)
+    for (int n = 0; n < p->n_inst; ++n)
+      if (nt_per_inst[n] < p->k + 2 || nt_per_inst[n] > p->nt)
+        return fail(nullptr, HKBE_ERR_ARG, "nt_per_inst[" + std::to_string(n) + "] must be in k+2..nt");
   if (p->svd_tol > 0) {
     if (p->leaf != 32 && p->leaf != 64) return fail(nullptr, HKBE_ERR_ARG, "leaf must be 32 or 64");
     if (p->leaf <= 2 * p->k) return fail(nullptr, HKBE_ERR_ARG, "leaf must exceed 2k");
@@ -259,6 +283,9 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
   hkbe_t* h = new hkbe_t();
   h->p = *p;
   h->s = (cudaStream_t)stream;
+  h->last.assign(p->n_inst, p->nt - 1);
+  if (nt_per_inst)
+    for (int n = 0; n < p->n_inst; ++n) h->last[n] = nt_per_inst[n] - 1;
   Dev& d = h->d;
   d.nt = p->nt; d.k = p->k; d.no = p->nao; d.n_inst = p->n_inst; d.xi = p->xi;
   d.rho_mode = p->rho_mode; d.h = p->h; d.beta = p->beta; d.r = 0; d.model = 0;
@@ -297,7 +324,16 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
       h->g_wslv[lv + 1] = h->g_wslv[lv] + 2LL * d.L * ncl + (long long)d.L * d.rmax + (long long)d.L * d.L + 2LL * ldk * ldk;
     }
     d.tsvd_ws_per = h->g_wslv[d.maxl];
-    const size_t ctas = N * 4 * n2;
+    // instances compressed at a time on one shared workspace: as many as fit
+    // in 32 GiB of workspace.  One launch over the whole batch is fastest
+    // (the CTAs' FP64 work is uneven, and consecutive launches each wait for
+    // their slowest CTA: groups of 12 C4 instances made the compression 2.3
+    // times slower); groups only bound the memory of very large batches.
+    {
+      const double per_inst = 4.0 * n2 * d.tsvd_ws_per * sizeof(double2);
+      d.tsvd_group = (int)std::max(1.0, std::min((double)N, std::floor(34359738368.0 / per_inst)));
+    }
+    const size_t ctas = (size_t)d.tsvd_group * 4 * n2;
     for (int X = 0; X < 4; ++X) {
       if ((rc = dalloc_el(h, &d.hod[X].U, N * d.utot * d.rmax)) || (rc = dalloc_el(h, &d.hod[X].V, N * d.vtot * d.rmax)) ||
           (rc = dalloc(h, &d.hod[X].S, N * d.nblk * n2 * d.rmax)) ||
@@ -354,7 +390,7 @@ int hkbe_create(const hkbe_params* p, void* stream, hkbe_t** out) {
       (rc = dalloc(h, &d.qsrc, (size_t)d.n_inst * d.nt * d.no * d.no)) ||
       (rc = dalloc(h, &d.x0, (size_t)d.n_inst * d.no * d.no)) || (rc = dalloc(h, &d.err, (size_t)d.n_inst)) ||
       (rc = dalloc(h, &d.active, (size_t)d.n_inst)) || (rc = dalloc(h, &h->any_dev, 1)) ||
-      (rc = dalloc(h, &h->diagbuf, (size_t)d.n_inst * d.no * d.no))) {
+      (rc = dalloc(h, &h->diagbuf, (size_t)d.n_inst * d.no * d.no)) || (rc = upload(h, &d.last, h->last))) {
     g_create_error = h->err;
     hkbe_destroy(h);
     return rc;
@@ -375,6 +411,7 @@ int hkbe_destroy(hkbe_t* h) {
   drain(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->snap_dev) cudaFree(p);
   delete h;
   return HKBE_OK;
 }
@@ -518,6 +555,9 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
     const int L = (int)params[0];
     if (L < 1 || L > 16 || L * L != d.n_inst || (double)L != params[0])
       return fail(h, HKBE_ERR_ARG, "LATTICE2B needs an integer L in 1..16 with n_inst = L*L");
+    for (int n = 0; n < d.n_inst; ++n)
+      if (h->last[n] != d.nt - 1)
+        return fail(h, HKBE_ERR_ARG, "LATTICE2B couples its k-points through Sigma: every k needs the same N_t");
     for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = L;
     h->self_consistent = true;
   } else if (model == HKBE_MODEL_NAMBU) {
@@ -643,11 +683,14 @@ static int check_ready(hkbe_t* h) {
 
 // Run the iteration loop of one bootstrap or one time step; `pass` launches
 // one iteration.  Records per-instance iteration counts and final errors.
+// Instances with act0[n] == 0 (past their last step) take no part.
 template <typename F>
-static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, double* errs, bool* any_failed) {
+static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, double* errs, bool* any_failed,
+                   const std::vector<int>* act0 = nullptr) {
   Dev& d = h->d;
   const int N = d.n_inst;
   std::vector<int> act(N, 1), it_of(N, 0);
+  if (act0) act = *act0;
   std::vector<double> err(N, 0.0);
   HK_CUDA(h, cudaMemcpyAsync(d.active, act.data(), N * sizeof(int), cudaMemcpyHostToDevice, h->s));
   const double tol_eff = h->self_consistent ? tol : INFINITY;
@@ -674,7 +717,8 @@ static int iterate(hkbe_t* h, int max_iter, double tol, F pass, int32_t* iters, 
     drain(h);
     if (!any) break;
     if (d.model == HKBE_MODEL_LATTICE2B) {  // k-points are coupled through Sigma: iterate all or none
-      std::fill(act.begin(), act.end(), 1);
+      if (act0) act = *act0;
+      else std::fill(act.begin(), act.end(), 1);
       HK_CUDA(h, cudaMemcpyAsync(d.active, act.data(), N * sizeof(int), cudaMemcpyHostToDevice, h->s));
     }
   }
@@ -804,6 +848,8 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
       }
     }
     HK_CUDA(h, run_phase(h, HKBE_PHASE_EXTRAP, 1, [&]() { return hk::launch_extrapolate(d, T, h->s); }));
+    std::vector<int> act0(N);
+    for (int n = 0; n < N; ++n) act0[n] = T <= h->last[n] ? 1 : 0;
     bool failed = false;
     rc = iterate(h, h->p.max_iter, h->p.tol,
                  [&]() -> cudaError_t {
@@ -830,7 +876,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                      return e;
                    return cudaSuccess;
                  },
-                 iters ? iters + (size_t)st * N : nullptr, err ? err + (size_t)st * N : nullptr, &failed);
+                 iters ? iters + (size_t)st * N : nullptr, err ? err + (size_t)st * N : nullptr, &failed, &act0);
     if (rc) return rc;
     any_failed |= failed;
     h->cur = T;
@@ -842,11 +888,18 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
     }
   }
   if (h->hodlr) {
+    // TSVD status of the compressions of these steps: [0] ranks capped at
+    // r_max, [1] block cores whose Jacobi SVD did not converge in 40 sweeps
+    // (their factors are the last sweep's, still a factorisation of the block).
     int st[2] = {0, 0};
     HK_CUDA(h, cudaMemcpyAsync(st, h->status_dev, sizeof(st), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaMemsetAsync(h->status_dev, 0, sizeof(st), h->s));
     HK_CUDA(h, cudaStreamSynchronize(h->s));
     drain(h);
     if (st[0] > 0) return fail(h, HKBE_ERR_RANK, "a block's epsilon-rank exceeded r_max (truncated to r_max)");
+    if (st[1] > 0)
+      return fail(h, HKBE_ERR_NOCONV, "the Jacobi SVD of " + std::to_string(st[1]) +
+                                           " TSVD block core(s) did not converge in 40 sweeps");
   }
   if (any_failed) return fail(h, HKBE_ERR_NOCONV, "self-consistency did not converge within max_iter");
   return HKBE_OK;
@@ -863,7 +916,7 @@ int hkbe_current_step(const hkbe_t* h, int32_t* T) {
 static int fetch_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
   const size_t cnt = (size_t)(T + 1) * no2(h);
   hk::Dev& d = h->d;
-  if (h->hodlr && T < d.cdir) {
+  if (h->hodlr && T < front_host(h, inst)) {
     HK_CUDA(h, hk::launch_row_out(d, inst, T, gr ? h->rowbuf_r : nullptr, gl ? h->rowbuf_l : nullptr, h->s));
     if (gr) HK_CUDA(h, cudaMemcpyAsync(gr, h->rowbuf_r, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
     if (gl) HK_CUDA(h, cudaMemcpyAsync(gl, h->rowbuf_l, cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
@@ -887,14 +940,16 @@ static int copy_el(hkbe_t* h, int X, int inst, int T, int t, double* out) {
 int hkbe_get_ret(hkbe_t* h, int inst, int t, int tp, double* out) {
   if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
-  if (tp < 0 || tp > t || t > h->cur) return fail(h, HKBE_ERR_RANGE, "need 0 <= t' <= t <= current step");
+  if (tp < 0 || tp > t || t > cur_of(h, inst))
+    return fail(h, HKBE_ERR_RANGE, "need 0 <= t' <= t <= current step (and the instance's last step)");
   return copy_el(h, 0, inst, t, tp, out);
 }
 
 int hkbe_get_les(hkbe_t* h, int inst, int t, int tp, double* out) {
   if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
-  if (t < 0 || tp < 0 || t > h->cur || tp > h->cur) return fail(h, HKBE_ERR_RANGE, "times must be in 0..current step");
+  if (t < 0 || tp < 0 || t > cur_of(h, inst) || tp > cur_of(h, inst))
+    return fail(h, HKBE_ERR_RANGE, "times must be in 0..current step (and the instance's last step)");
   if (t <= tp) return copy_el(h, 1, inst, tp, t, out);
   const int no = h->d.no;
   std::vector<double> tmp(2 * no * no);
@@ -912,7 +967,8 @@ int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out) {
   if (!h || !out) return fail(h, HKBE_ERR_ARG, "null argument");
   if (!h->have_dlr) return fail(h, HKBE_ERR_ARG, "no DLR grid");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
-  if (t < 0 || t > h->cur) return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step");
+  if (t < 0 || t > cur_of(h, inst))
+    return fail(h, HKBE_ERR_RANGE, "t must be in 0..current step (and the instance's last step)");
   const size_t cnt = (size_t)h->d.r * no2(h);
   HK_CUDA(h, cudaMemcpyAsync(out, static_cast<double2*>(h->d.GTV) + ((size_t)inst * h->d.nt + t) * cnt,
                              cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
@@ -923,7 +979,8 @@ int hkbe_get_tv(hkbe_t* h, int inst, int t, double* out) {
 int hkbe_get_row(hkbe_t* h, int inst, int T, double* gr, double* gl) {
   if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
   if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
-  if (T < 0 || T > h->cur) return fail(h, HKBE_ERR_RANGE, "T must be in 0..current step");
+  if (T < 0 || T > cur_of(h, inst))
+    return fail(h, HKBE_ERR_RANGE, "T must be in 0..current step (and the instance's last step)");
   return fetch_row(h, inst, T, gr, gl);
 }
 
@@ -948,7 +1005,7 @@ int hkbe_get_ranks(hkbe_t* h, int inst, int comp, int32_t* ranks, int32_t* first
   if (ranks)
     HK_CUDA(h, cudaMemcpyAsync(ranks, h->d.hod[comp].rank + (size_t)inst * cnt, cnt * sizeof(int), cudaMemcpyDeviceToHost, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
-  if (first_direct) *first_direct = h->d.cdir;
+  if (first_direct) *first_direct = front_host(h, inst);
   return HKBE_OK;
 }
 
@@ -959,6 +1016,10 @@ int hkbe_get_density(hkbe_t* h, double* rho) {
   std::vector<double> tmp(2 * n2);
   for (int n = 0; n < h->d.n_inst; ++n)
     for (int t = 0; t <= T; ++t) {
+      if (t > h->last[n]) {   // past the instance's last step: zeros
+        std::memset(rho + (((size_t)n * (T + 1) + t) * n2) * 2, 0, sizeof(double) * 2 * n2);
+        continue;
+      }
       int rc = copy_el(h, 1, n, t, t, tmp.data());
       if (rc) return rc;
       double* o = rho + (((size_t)n * (T + 1) + t) * n2) * 2;
@@ -1009,9 +1070,66 @@ int hkbe_get_observables(hkbe_t* h, int t, double* rho, double* ekin, double* cu
   return HKBE_OK;
 }
 
-int hkbe_get_stats(const hkbe_t* h, size_t* device_bytes) {
-  if (!h || !device_bytes) return HKBE_ERR_ARG;
-  *device_bytes = h->bytes;
+int hkbe_get_stats(hkbe_t* h, int inst, int32_t* ranks, size_t* device_bytes) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (device_bytes) *device_bytes = h->bytes;
+  if (!ranks) return HKBE_OK;
+  if (!h->hodlr) return fail(h, HKBE_ERR_ARG, "ranks requested from a dense handle");
+  if (inst < 0 || inst >= h->d.n_inst) return fail(h, HKBE_ERR_ARG, "instance out of range");
+  const size_t cnt = (size_t)h->d.nblk * no2(h);
+  for (int X = 0; X < 4; ++X)
+    HK_CUDA(h, cudaMemcpyAsync(ranks + X * cnt, h->d.hod[X].rank + (size_t)inst * cnt, cnt * sizeof(int),
+                               cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  return HKBE_OK;
+}
+
+int hkbe_snapshot_free(hkbe_t* h) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  for (void* p : h->snap_dev) cudaFree(p);
+  h->snap_dev.clear();
+  h->snap_bytes = 0;
+  h->snap_cur = -1;
+  return HKBE_OK;
+}
+
+int hkbe_snapshot_save(hkbe_t* h) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (h->cur < 0) return fail(h, HKBE_ERR_ARG, "hkbe_bootstrap must precede hkbe_snapshot_save");
+  if (h->snap_dev.size() != h->allocs.size()) {
+    hkbe_snapshot_free(h);
+    for (size_t i = 0; i < h->allocs.size(); ++i) {
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, h->alloc_bytes[i]);
+      if (e != cudaSuccess) {
+        hkbe_snapshot_free(h);
+        return fail(h, HKBE_ERR_NOMEM, std::string("snapshot cudaMalloc: ") + cudaGetErrorString(e));
+      }
+      h->snap_dev.push_back(p);
+      h->snap_bytes += h->alloc_bytes[i];
+    }
+  }
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    HK_CUDA(h, cudaMemcpyAsync(h->snap_dev[i], h->allocs[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->snap_cur = h->cur;
+  h->snap_cdir = h->d.cdir;
+  h->snap_nfrozR = h->d.nfrozR;
+  h->snap_nfrozL = h->d.nfrozL;
+  return HKBE_OK;
+}
+
+int hkbe_snapshot_restore(hkbe_t* h) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (h->snap_cur < 0 || h->snap_dev.size() != h->allocs.size())
+    return fail(h, HKBE_ERR_ARG, "no snapshot to restore (hkbe_snapshot_save first)");
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    HK_CUDA(h, cudaMemcpyAsync(h->allocs[i], h->snap_dev[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  h->cur = h->snap_cur;
+  h->d.cdir = h->snap_cdir;
+  h->d.nfrozR = h->snap_nfrozR;
+  h->d.nfrozL = h->snap_nfrozL;
   return HKBE_OK;
 }
 
@@ -1067,7 +1185,7 @@ int hkbe_rewind(hkbe_t* h) {
 // ---- checkpoint files ----
 namespace {
 constexpr char kCkpMagic[8] = {'H', 'K', 'B', 'E', 'C', 'K', 'P', '1'};
-constexpr uint32_t kCkpVersion = 1;
+constexpr uint32_t kCkpVersion = 2;   // 2: checksum trailer and per-instance N_t
 constexpr size_t kCkpChunk = size_t(64) << 20;  // host staging of device buffers
 
 struct CkpScalars {
@@ -1141,7 +1259,8 @@ int hkbe_save(hkbe_t* h, const char* path) {
                       d.model, d.r, d.cdir, d.nfrozR, d.nfrozL, 0};
   const uint32_t ver = kCkpVersion, psz = sizeof(hkbe_params);
   bool ok = wr(f, kCkpMagic, sizeof kCkpMagic) && wr(f, &ver, sizeof ver) && wr(f, &psz, sizeof psz) &&
-            wr(f, &h->p, sizeof(hkbe_params)) && wr(f, &sc, sizeof sc) && wr_vec(f, h->tau) && wr_vec(f, h->om) &&
+            wr(f, &h->p, sizeof(hkbe_params)) && wr(f, &sc, sizeof sc) && wr_vec(f, h->last) &&
+            wr_vec(f, h->tau) && wr_vec(f, h->om) &&
             wr_vec(f, h->gm_host) && wr_vec(f, h->eps_host) && wr_vec(f, h->snap_gr) && wr_vec(f, h->snap_gl) &&
             wr_vec(f, h->snap_sr) && wr_vec(f, h->snap_sl) && wr_vec(f, h->snap_tv) && wr_vec(f, h->snap_stv);
   const uint64_t na = h->allocs.size();
@@ -1209,7 +1328,12 @@ int hkbe_load(const char* path, void* stream, hkbe_t** out) {
       sc.model > HKBE_MODEL_LATTICE2B || sc.cdir < 0 || sc.cdir > std::max(sc.cur, 0) || sc.nfrozR < 0 ||
       sc.nfrozL < 0 || sc.nfrozR > (p.nt + 31) / 32 || sc.nfrozL > (p.nt + 31) / 32)
     return bad(HKBE_ERR_IO, "inconsistent checkpoint header");
-  int rc = hkbe_create(&p, stream, &h);
+  std::vector<int> last;
+  if (p.n_inst < 1 || p.nt < 2 || !rd_vec(f, last, (uint64_t)p.n_inst) || last.size() != (size_t)p.n_inst)
+    return bad(HKBE_ERR_IO, "short read (per-instance N_t)");
+  std::vector<int32_t> ntn(p.n_inst);
+  for (int n = 0; n < p.n_inst; ++n) ntn[n] = last[n] + 1;
+  int rc = hkbe_create(&p, ntn.data(), stream, &h);
   if (rc) return bad(rc, g_create_error);
   Dev& d = h->d;
   std::vector<double> tau, om;

@@ -10,6 +10,16 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ long long tri(int T) { return (long long)T * (T + 1) / 2; }
 
+// First uncompressed row of instance n.  An instance whose last step comes
+// before N_t - 1 stops taking part in the compression once its rows end: its
+// front freezes at the last whole leaf of rows older than k + 1 steps, and
+// the rows after it stay in their ring slots, which no later kernel writes.
+__device__ __forceinline__ int front_of(const Dev& d, int n) {
+  const int lk = d.last[n] - d.k;
+  const int fz = lk >= d.L ? (lk / d.L) * d.L : 0;
+  return d.cdir < fz ? d.cdir : fz;
+}
+
 // Row T of a two-time component: the dense lower triangle, or (compressed
 // storage) the ring of uncompressed rows, slot T mod ring.
 // S is the storage element type (double2 or float2).

@@ -7,15 +7,16 @@
 //
 // Per self-consistency iteration at step T the launches are
 //   k_sigma  Sigma^R(T, .), Sigma^<(., T), Sigma^tv(T, .) from the current G
-//   k_ret    retarded row, unknown y_s = G^R(T, T-s) (Eq. KBER), one CTA per
-//            (instance, orbital row); start block s <= k solved together, then
-//            chunks of 32 points: far-field history sums in parallel over the
-//            CTA, near field + point solve sequentially in one warp
+//   (the retarded row, Eq. KBER, is solved by k_ret2 in kernels_sweep.cu)
 //   k_mixed  G^tv(T, tau_i) (Eq. KBET), one warp per (instance, node)
 //   k_vt     v_a = sum_b Q_ab G^vt(tau_b, T) and x_0 = -[G^tv(T, 0)]^dagger
 //   k_src    lesser source q(t), t = 0..T, one warp per (instance, t)
 //   k_les    lesser column x_t = G^<(t, T) (Eq. KBEL), one CTA per
-//            (instance, orbital column), same chunked structure as k_ret
+//            (instance, orbital column): start block t <= k solved together,
+//            then chunks of 32 points: far-field history sums in parallel over
+//            the CTA, near field + point solve sequentially in one warp.  The
+//            stepper uses the chunked sweep k_les2 (kernels_sweep.cu); k_les
+//            serves the allocation-free entry point
 //   k_rho    diagonal density-matrix update (Sec. 3.3), when selected
 // Each kernel folds max |new - old| of what it writes into err[instance].
 #include "dev_util.cuh"
@@ -222,7 +223,7 @@ __global__ void k_extrap(Dev d, int T) {
   const int n = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = d.k;
-  if (idx >= 2 * (T + 1) + d.r) return;
+  if (idx >= 2 * (T + 1) + d.r || T > d.last[n]) return;
   double e[6];
   {
     double c = 1.0;  // C(k+1, l+1) built incrementally
@@ -273,158 +274,8 @@ __global__ void k_extrap(Dev d, int T) {
   for (int q = 0; q < NO2; ++q) st(dst + q, acc[q]);
 }
 
-// ---------------------------------------------------------------------------
-// Retarded row, Eq. KBER: y_s = G^R(T, T-s), right-multiplying VIDE in s.
-// ---------------------------------------------------------------------------
 constexpr int CH = 32;     // chunk of the sequential sweeps
 constexpr int NWARP = 8;   // warps per sweep CTA
-
-template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_ret(Dev d, int T) {
-  constexpr int NO2 = NO * NO;
-  const int n = blockIdx.y, irow = blockIdx.x;
-  if (!d.active[n]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = d.k;
-  const double h = d.h;
-  const DevW& W = d.w;
-  __shared__ zd sA[20 * 20];
-  __shared__ zd sB[20];
-  __shared__ zd red[NWARP][CH][NO];
-  __shared__ zd ych[CH][NO];
-  __shared__ double serr;
-  if (tid == 0) serr = 0.0;
-  S* rowp = el<NO, S>(d.GR, d, n, T, 0);  // G^R(T, t') at rowp + t' NO2
-  auto yptr = [&](int s) { return rowp + (long long)(T - s) * NO2 + irow * NO; };
-  double myerr = 0.0;
-  // ---- start block s = 1..k ----
-  const int ns = k * NO;
-  if (warp == 0) {
-    for (int e = lane; e < ns * ns; e += 32) {
-      const int row = e / ns, col = e % ns;       // row (s, j), col (l, m)
-      const int s = row / NO + 1, j = row % NO, l = col / NO + 1, m = col % NO;
-      zd v = srx<NO, S>(d, n, T - l, T - s, m, j) * (-h * W.I0[s][l]);
-      if (m == j) v += zd(0, W.D[s][l] / h);
-      if (l == s) v -= ld(epsp<NO>(d, n, T - s) + m * NO + j);
-      sA[row * ns + col] = v;
-    }
-    for (int row = lane; row < ns; row += 32) {
-      const int s = row / NO + 1, j = row % NO;
-      // b_s[j] = -sum_m y0[m] C[0,s][m][j], y0 = -i e_irow  ->  i C[0,s][irow][j]
-      zd c = srx<NO, S>(d, n, T, T - s, irow, j) * (-h * W.I0[s][0]);
-      if (irow == j) c += zd(0, W.D[s][0] / h);
-      sB[row] = zd(0, 1) * c;
-    }
-    __syncwarp();
-    warp_lu_solve(ns, sA, sB, 1, nullptr);
-    for (int row = lane; row < ns; row += 32) {
-      const int s = row / NO + 1, j = row % NO;
-      S* p = yptr(s) + j;
-      zd old = ld(p);
-      st(p, sB[row]);
-      myerr = fmax(myerr, sqrt((sB[row] - old).abs2()));
-    }
-    if (lane == 0) {
-      S* p = yptr(0);
-      for (int j = 0; j < NO; ++j) {
-        zd v = (j == irow) ? zd(0, -1) : zd();
-        myerr = fmax(myerr, sqrt((ld(p + j) - v).abs2()));
-        st(p + j, v);
-      }
-    }
-  }
-  __syncthreads();
-  // ---- BDF region s = k+1..T in chunks ----
-  for (int s0 = k + 1; s0 <= T; s0 += CH) {
-    const int cn = min(CH, T + 1 - s0);
-    {  // far field: l < s0, lanes over s, warps over l
-      zd acc[NO];
-#pragma unroll
-      for (int j = 0; j < NO; ++j) acc[j] = zd();
-      const int s = s0 + lane;
-      if (lane < cn) {
-        for (int l = warp; l < s0; l += NWARP) {
-          const double wl = rule_w(W, s, l);
-          const S* yl = yptr(l);
-          const S* sr = el<NO, S>(d.SR, d, n, T - l, T - s);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ld(yl + m) * wl;
-#pragma unroll
-            for (int j = 0; j < NO; ++j) acc[j] = cfma(ym, ld(sr + m * NO + j), acc[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NO; ++j) red[warp][lane][j] = acc[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      zd far[NO];
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        far[j] = zd();
-        for (int w2 = 0; w2 < NWARP; ++w2) far[j] += red[w2][lane][j];
-        far[j] = far[j] * h;
-      }
-      for (int sl = 0; sl < cn; ++sl) {
-        const int s = s0 + sl;
-        zd part[NO];
-#pragma unroll
-        for (int j = 0; j < NO; ++j) part[j] = zd();
-        if (lane < sl) {  // near field, l in [s0, s)
-          const int l = s0 + lane;
-          const double wl = h * rule_w(W, s, l);
-          const S* sr = el<NO, S>(d.SR, d, n, T - l, T - s);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = ych[lane][m] * wl;
-#pragma unroll
-            for (int j = 0; j < NO; ++j) part[j] = cfma(ym, ld(sr + m * NO + j), part[j]);
-          }
-        }
-        if (lane >= 1 && lane <= k) {  // -(i/h) a_j y_{s-j}
-          const int sj = s - lane;
-          const zd c = zd(0, -W.a[lane] / h);
-#pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            const zd ym = (sj >= s0) ? ych[sj - s0][m] : ld(yptr(sj) + m);
-            part[m] += c * ym;
-          }
-        }
-        warp_sum<NO>(part);
-        if (lane == sl) {
-          zd rhs[NO], y[NO];
-#pragma unroll
-          for (int j = 0; j < NO; ++j) rhs[j] = part[j] + far[j];
-          const double ws = h * rule_w(W, s, s);
-          const S* sd = el<NO, S>(d.SR, d, n, T - s, T - s);
-          const double2* ep = epsp<NO>(d, n, T - s);
-          M<NO> Mm;
-#pragma unroll
-          for (int x = 0; x < NO; ++x)
-#pragma unroll
-            for (int y2 = 0; y2 < NO; ++y2)
-              Mm.a[x][y2] = (x == y2 ? zd(0, W.a[0] / h) : zd()) - ld(ep + x * NO + y2) - ld(sd + x * NO + y2) * ws;
-          solve_row<NO>(Mm, rhs, y);
-          S* p = yptr(s);
-#pragma unroll
-          for (int j = 0; j < NO; ++j) {
-            myerr = fmax(myerr, sqrt((y[j] - ld(p + j)).abs2()));
-            st(p + j, y[j]);
-            ych[sl][j] = y[j];
-          }
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-  myerr = warp_max(myerr);
-  if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
-  __syncthreads();
-  if (tid == 0) atomic_max_nonneg(d.err + n, serr);
-}
 
 // ---------------------------------------------------------------------------
 // Mixed component at step T, Eq. KBET (one warp per (instance, node)).
@@ -1068,11 +919,6 @@ cudaError_t launch_sigma(const Dev& d, int T, cudaStream_t s) {
   if (d.model == 4) return launch_sigma_lattice(d, T, s);
   dim3 g((2 * (T + 1) + d.r + 127) / 128, d.n_inst);
   HK_DISPATCH(d.no, (k_sigma<NO, S><<<g, 128, 0, s>>>(d, T)));
-  return cudaGetLastError();
-}
-cudaError_t launch_ret(const Dev& d, int T, cudaStream_t s) {
-  dim3 g(d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_ret<NO, S><<<g, 256, 0, s>>>(d, T)));
   return cudaGetLastError();
 }
 cudaError_t launch_mixed(const Dev& d, int T, cudaStream_t s) {

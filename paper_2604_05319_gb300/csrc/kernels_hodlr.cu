@@ -34,10 +34,29 @@ namespace hk {
 //   P1 = S o sum_{rows l} w_l g_l[z][y] U(l,:),  q(t in cols) += P1 . conj(V(t,:))
 //   P2 = S o sum_{cols l} w_l g_l[z][y] V(l,:),  q(t in rows) -= conj(U(t,:)) . P2
 // ---------------------------------------------------------------------------
-template <int NO>
-__device__ __forceinline__ double2* Psrc(const Dev& d, int n, int b, int p, int y, int which) {
-  return d.proj + (long long)d.n_inst * NO * d.maxl * NO * NO * d.rmax +
-         (((((long long)n * d.nblk + b) * (NO * NO) + p) * NO + y) * 2 + which) * d.rmax;
+// Slot of P1 (which = 0) or P2 (which = 1), rmax complex values in the bulk
+// arithmetic R of the form (FP32 in the complex64 form: the products with the
+// factor rows need no conversion), inside a complex128-sized slot.
+template <int NO, typename R>
+__device__ __forceinline__ cx<R>* Psrc(const Dev& d, int n, int b, int p, int y, int which) {
+  return reinterpret_cast<cx<R>*>(d.proj + (long long)d.n_inst * NO * d.maxl * NO * NO * d.rmax +
+                                  (((((long long)n * d.nblk + b) * (NO * NO) + p) * NO + y) * 2 + which) * d.rmax);
+}
+
+// sum_{q < rk} P[q] conj(F[q]) for one thread: P (bulk type, shared by the
+// CTA, cached) and F (a factor row in global memory) with eight loads of F in
+// flight rather than one load per term.
+template <typename R, typename S>
+__device__ __forceinline__ cx<R> lr_dot_conj(const cx<R>* P, const S* F, int rk) {
+  cx<R> acc = cx<R>(0);
+  for (int q0 = 0; q0 < rk; q0 += 8) {
+    cx<R> f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f[u] = q0 + u < rk ? ldr<R>(F + q0 + u) : cx<R>(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = cfma(P[q0 + u < rk ? q0 + u : 0], f[u].conj(), acc);
+  }
+  return acc;
 }
 
 template <int NO, typename S>
@@ -85,7 +104,8 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
     if (tid < d.rmax) {
       zd acc = zd();
       for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][tid];
-      st(Psrc<NO>(d, n, b, p, y, which) + tid, tid < rk ? acc * Sp<NO>(d, 3, n, b, p)[tid] : zd());
+      const zd v = tid < rk ? acc * Sp<NO>(d, 3, n, b, p)[tid] : zd();
+      Psrc<NO, R>(d, n, b, p, y, which)[tid] = cx<R>((R)v.re, (R)v.im);
     }
     __syncthreads();
   }
@@ -193,10 +213,7 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
       const S* V = Vp<NO, S>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
-        const double2* P = Psrc<NO>(d, n, b, p, y, 0);
-        cx<R> sb = cx<R>(0);
-        for (int q = 0; q < rk; ++q) sb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), sb);
-        acc[x * NO + y] += wide(sb);
+        acc[x * NO + y] += wide(lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 0), V, rk));
       }
     }
   }
@@ -211,10 +228,7 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
       const S* U = Up<NO, S>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
-        const double2* P = Psrc<NO>(d, n, b, p, y, 1);
-        cx<R> sb = cx<R>(0);
-        for (int q = 0; q < rk; ++q) sb = cfma(ldr<R>(U + q).conj(), ldr<R>(P + q), sb);
-        acc[x * NO + y] -= wide(sb);
+        acc[x * NO + y] -= wide(lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 1), U, rk));
       }
     }
   }
@@ -291,9 +305,9 @@ __global__ void k_src_h(Dev d, int T) {
       const S* V = Vp<NO, S>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
-        const double2* P = Psrc<NO>(d, n, b, p, y, 0);
+        const cx<R>* P = Psrc<NO, R>(d, n, b, p, y, 0);
         cx<R> sb = cx<R>(0);
-        for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), sb);
+        for (int q = lane; q < rk; q += 32) sb = cfma(P[q], ldr<R>(V + q).conj(), sb);
         acc[x * NO + y] += wide(sb);
       }
     }
@@ -323,9 +337,9 @@ __global__ void k_src_h(Dev d, int T) {
         const S* U = Up<NO, S>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
 #pragma unroll
         for (int y = 0; y < NO; ++y) {
-          const double2* P = Psrc<NO>(d, n, b, p, y, 1);
+          const cx<R>* P = Psrc<NO, R>(d, n, b, p, y, 1);
           cx<R> sb = cx<R>(0);
-          for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(U + q).conj(), ldr<R>(P + q), sb);
+          for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(U + q).conj(), P[q], sb);
           acc[x * NO + y] -= wide(sb);
         }
       }
@@ -353,6 +367,7 @@ template <int NO, typename S>
 __global__ void k_comp_copy(Dev d, int A, int nb) {
   constexpr int NO2 = NO * NO;
   const int n = blockIdx.y;
+  if (A + nb + d.k > d.last[n]) return;   // the instance's rows end before this leaf is final
   const int j = A / d.L;
   const long long ntr = (long long)nb * (nb + 1) / 2;
   const long long total = 4 * ntr + (long long)nb * d.k;
@@ -389,24 +404,31 @@ __global__ void k_comp_copy(Dev d, int A, int nb) {
 // One CTA per (component X, level slot, pair p) x instance.  Workspace per
 // CTA (complex doubles): E [nb][ncol], Q [nb][ncol], P [nb][rmax], C [nb][nb],
 // K [(rmax+nb)][(rmax+nb)] column-major, Vh [(rmax+nb)][(rmax+nb)] column-major.
+//
+// FP64 throughout, in both storage forms.  The complex64 form truncates at
+// the rounding floor of its stored rows (below), so every step must round
+// well below that floor; measured on the C4 batch, FP32 variants of the
+// projections (even with FP64 folds), of the residual rows, of the rotation
+// of V, or of the core Jacobi each put rounding directions above it and the
+// ranks grew to r_max within a few hundred steps.
 constexpr double kF32Unit = 5.9604644775390625e-8;  // 2^-24, complex64 unit roundoff
 
 template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
+__global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb, int n0) {
   constexpr int NO2 = NO * NO;
-  const int n = blockIdx.y;
+  const int n = n0 + blockIdx.y;   // instances n0 .. n0 + gridDim.y - 1 share the workspace
   const int X = blockIdx.x / (d.maxl * NO2);
   const int lv = (blockIdx.x / NO2) % d.maxl;
   const int p = blockIdx.x % NO2;
   const int j = A / d.L;
   const int b = d.rowblk[j * d.maxl + lv];
-  if (b < 0) return;
+  if (b < 0 || A + nb + d.k > d.last[n]) return;   // the instance's rows end before this leaf is final
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int r0 = d.b_r0[b], c0 = d.b_c0[b];
   const int ncol = d.b_c1[b] - c0;
   const int rmax = d.rmax;
   const int ld_k = rmax + d.L;  // leading dimension of K and Vh
-  double2* ws = d.tsvd_ws + (((long long)n * 4 + X) * NO2 + p) * d.tsvd_ws_per + d.ws_lvoff[lv];
+  double2* ws = d.tsvd_ws + (((long long)blockIdx.y * 4 + X) * NO2 + p) * d.tsvd_ws_per + d.ws_lvoff[lv];
   double2* Em = ws;                                   // [nb][ncol]
   double2* Qm = Em + (long long)d.L * ncol;           // [nb][ncol]
   double2* Pm = Qm + (long long)d.L * ncol;           // [nb][rmax]
@@ -471,6 +493,9 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb) {
   __syncthreads();
   // Two-pass Gram-Schmidt on the rows of E: E = C Q, rows of Q orthonormal.
   // residual rows below a quarter of the threshold add no basis direction
+  // (a higher floor, the rounding level of one stored row, rejects rows that
+  // are each at noise level but together carry a direction above the
+  // threshold: measured on the C4 batch, the ranks then grew about threefold)
   const double delta = 0.25 * tol;
   __shared__ zd s_coef[64];
 
@@ -677,7 +702,7 @@ __global__ void k_row_out(Dev d, int n, int T, double2* out_r, double2* out_l) {
     if (!out) continue;
     for (int p = 0; p < NO2; ++p) {
       zd v;
-      if (T >= d.cdir) {
+      if (T >= front_of(d, n)) {
         v = ld(el<NO, S>(ringX(d, X), d, n, T, t) + p);
       } else {
         const int jT = T / d.L, jt = t / d.L;
@@ -708,7 +733,11 @@ __global__ void k_density_at(Dev d, int t, double2* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.n_inst * NO2) return;
   const int n = e / NO2, q = e % NO2;
-  const S* p = (!d.ring || t >= d.cdir) ? el<NO, S>(d.GL, d, n, t, t) : Lf<NO, S>(d, 1, n, t / d.L, t, t);
+  if (t > d.last[n]) {   // past the instance's last step
+    st(out + e, zd());
+    return;
+  }
+  const S* p = (!d.ring || t >= front_of(d, n)) ? el<NO, S>(d.GL, d, n, t, t) : Lf<NO, S>(d, 1, n, t / d.L, t, t);
   st(out + e, ld(p + q) * zd(0, (double)d.xi));
 }
 
@@ -868,8 +897,10 @@ cudaError_t launch_compress(const Dev& d, int A, int nb, cudaStream_t s) {
     dim3 g(64, d.n_inst);
     HK_DISPATCH(d.no, (k_comp_copy<NO, S><<<g, 256, 0, s>>>(d, A, nb)));
   }
-  dim3 g(4 * d.maxl * d.no * d.no, d.n_inst);
-  HK_DISPATCH(d.no, (k_tsvd<NO, S><<<g, 256, 0, s>>>(d, A, nb)));
+  for (int n0 = 0; n0 < d.n_inst; n0 += d.tsvd_group) {
+    dim3 g(4 * d.maxl * d.no * d.no, min(d.tsvd_group, d.n_inst - n0));
+    HK_DISPATCH(d.no, (k_tsvd<NO, S><<<g, 256, 0, s>>>(d, A, nb, n0)));
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_density_at(const Dev& d, int t, double2* out, cudaStream_t s) {

@@ -54,6 +54,27 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
   return d.cinv + (((long long)n * d.nchunk + cc) * 2 + which) * nn;
 }
 
+// Sum over q < rk of P[q] * F[q] (or P[q] * conj(F[q])): the far field of one
+// compressed block at one row or column, P its projection vector staged in
+// shared memory, F the block's factor row in global memory.  Four threads
+// share an output (q = sl, sl + 4, ...) and each keeps eight loads of F in
+// flight, so the row streams instead of waiting on one load per term.
+template <typename R, typename S, bool CONJ>
+__device__ __forceinline__ cx<R> lr_dot4(const cx<R>* P, const S* F, int rk, int sl) {
+  cx<R> acc = cx<R>(0);
+  for (int q0 = sl; q0 < rk; q0 += 32) {
+    cx<R> f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + 4 * u;
+      f[u] = q < rk ? ldr<R>(F + q) : cx<R>(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = cfma(P[q0 + 4 * u < rk ? q0 + 4 * u : 0], CONJ ? f[u].conj() : f[u], acc);
+  }
+  return acc;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -61,7 +82,7 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
 // t' = T-1 .. 0; the start block t' >= T-k is solved together.
 // ---------------------------------------------------------------------------
 template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
+__global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
   const int n = blockIdx.y, irow = blockIdx.x;
@@ -76,7 +97,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
-  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2)
+  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
+                                 // entry (staged != 0) the block projections [maxl][NO2][rmax]
   if (tid == 0) serr = 0.0;
   // The row being solved lives in FP64 during the sweep (in the complex64
   // storage form a separate buffer), so the point-to-point recursion of the
@@ -171,6 +193,19 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
         }
       }
       __syncthreads();
+      // projections of every block over this leaf's columns, staged in shared
+      // memory for the far-field loop below (the buffer of the hot-chunk
+      // coefficients, which the chunk solves fill only after it)
+      cx<R>* Ps = reinterpret_cast<cx<R>*>(ctile);
+      if (staged) {
+        const int per = NO2 * d.rmax;
+        for (int e = tid; e < d.maxl * per; e += blockDim.x) {
+          const int lv = e / per, p = (e / d.rmax) % NO2, q = e % d.rmax;
+          const int blk = d.colblk[jl * d.maxl + lv];
+          Ps[e] = (blk >= 0 && d.b_r0[blk] < c) ? ldr<R>(Pj<NO>(d, n, irow, lv, p) + q) : cx<R>(0);
+        }
+        __syncthreads();
+      }
       // (2) for every column of the leaf: uncompressed rows s in [c, T], the
       // blocks below the leaf (weight 1) and the near-diagonal corrections;
       // 4 threads per column.
@@ -212,9 +247,13 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
               const int j = p % NO;
               const int rk = *Rk<NO>(d, 2, n, blk, p);
               const S* V = Vp<NO, S>(d, 2, n, blk, p) + (long long)(tp - c0) * d.rmax;
-              const double2* P = Pj<NO>(d, n, irow, lv, p);
               cx<R> pb = cx<R>(0);
-              for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), pb);
+              if (staged) {
+                pb = lr_dot4<R, S, true>(Ps + (lv * NO2 + p) * d.rmax, V, rk, sl);
+              } else {
+                const double2* P = Pj<NO>(d, n, irow, lv, p);
+                for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), pb);
+              }
               acc[j] += wide(pb);
             }
           }
@@ -406,7 +445,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T) {
 // Lesser column, Eq. KBEL: unknown x(t) = G^<(t, T) (column jc), t = 0..T.
 // ---------------------------------------------------------------------------
 template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
+__global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
   const int n = blockIdx.y, jc = blockIdx.x;
@@ -421,7 +460,8 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ double serr;
-  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2)
+  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
+                                 // entry (staged != 0) the block projections [maxl][NO2][rmax]
   if (tid == 0) serr = 0.0;
   // FP64 column during the sweep (see k_ret2); xp: as solved, sp: storage
   S* colp = el<NO, S>(d.GL, d, n, T, 0);
@@ -487,6 +527,19 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
         }
       }
       __syncthreads();
+      // projections of every block left of this leaf's rows, staged in shared
+      // memory for the loop below (the buffer of the hot-chunk coefficients,
+      // which the chunk solves fill only after it)
+      cx<R>* Ps = reinterpret_cast<cx<R>*>(ctile);
+      if (staged) {
+        const int per = NO2 * d.rmax;
+        for (int e = tid; e < d.maxl * per; e += blockDim.x) {
+          const int lv = e / per, p = (e / d.rmax) % NO2, q = e % d.rmax;
+          const int blk = d.rowblk[jl * d.maxl + lv];
+          Ps[e] = blk >= 0 ? ldr<R>(Pj<NO>(d, n, jc, lv, p) + q) : cx<R>(0);
+        }
+        __syncthreads();
+      }
       // (2) every row of the leaf: blocks left of it and near-diagonal corrections
       {
         const int row = tid >> 2, sl = tid & 3;
@@ -504,9 +557,13 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T) {
               const int m = p / NO;
               const int rk = *Rk<NO>(d, 2, n, blk, p);
               const S* U = Up<NO, S>(d, 2, n, blk, p) + (long long)(t - r0) * d.rmax;
-              const double2* P = Pj<NO>(d, n, jc, lv, p);
               cx<R> pb = cx<R>(0);
-              for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(U + q), ldr<R>(P + q), pb);
+              if (staged) {
+                pb = lr_dot4<R, S, false>(Ps + (lv * NO2 + p) * d.rmax, U, rk, sl);
+              } else {
+                const double2* P = Pj<NO>(d, n, jc, lv, p);
+                for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(U + q), ldr<R>(P + q), pb);
+              }
               acc[m] += wide(pb);
             }
           }
@@ -763,6 +820,7 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
   const DevW& W = d.w;
   const int a = (which == 1 && cc == 0) ? 1 : cc * CK;
   const int cnt = (which == 1 && cc == 0) ? CK - 1 : CK;
+  if (cc * CK + CK + (which == 0 ? 2 * k : 0) > d.last[n]) return;   // frozen only after the instance ends
   const int nn = cnt * NO;
   constexpr int LD = CK * NO;
   double2* Bout = Cinv<NO>(d, n, cc, which);
@@ -868,18 +926,32 @@ static cudaError_t allow_smem(K kern, size_t bytes) {
   if (bytes + 16 * 1024 <= 48 * 1024) return cudaSuccess;  // with the static arrays, under the default
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
+// Dynamic shared memory of a sweep: the hot-chunk coefficients (N_o <= 2)
+// and, in the compressed form, the staged block projections, which share one
+// buffer; staging is used when it fits in 64 KiB.
+template <int NO, typename S>
+static size_t sweep_smem(const Dev& d, int* staged) {
+  using R = typename Bulk<S>::R;
+  const size_t ps = d.ring ? (size_t)d.maxl * NO * NO * d.rmax * sizeof(cx<R>) : 0;
+  *staged = (d.ring && ps <= 65536) ? 1 : 0;
+  return std::max(kStageBytes<NO>, *staged ? ps : (size_t)0);
+}
 template <int NO, typename S>
 static cudaError_t sweep_ret(const Dev& d, int T, cudaStream_t s) {
-  cudaError_t e = allow_smem(k_ret2<NO, S>, kStageBytes<NO>);
+  int staged = 0;
+  const size_t bytes = sweep_smem<NO, S>(d, &staged);
+  cudaError_t e = allow_smem(k_ret2<NO, S>, bytes);
   if (e != cudaSuccess) return e;
-  k_ret2<NO, S><<<dim3(d.no, d.n_inst), 256, kStageBytes<NO>, s>>>(d, T);
+  k_ret2<NO, S><<<dim3(d.no, d.n_inst), 256, bytes, s>>>(d, T, staged);
   return cudaGetLastError();
 }
 template <int NO, typename S>
 static cudaError_t sweep_les(const Dev& d, int T, cudaStream_t s) {
-  cudaError_t e = allow_smem(k_les2<NO, S>, kStageBytes<NO>);
+  int staged = 0;
+  const size_t bytes = sweep_smem<NO, S>(d, &staged);
+  cudaError_t e = allow_smem(k_les2<NO, S>, bytes);
   if (e != cudaSuccess) return e;
-  k_les2<NO, S><<<dim3(d.no, d.n_inst), 256, kStageBytes<NO>, s>>>(d, T);
+  k_les2<NO, S><<<dim3(d.no, d.n_inst), 256, bytes, s>>>(d, T, staged);
   return cudaGetLastError();
 }
 cudaError_t launch_ret_h(const Dev& d, int T, cudaStream_t s) {

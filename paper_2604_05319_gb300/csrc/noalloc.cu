@@ -14,6 +14,7 @@
 // shares it.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/hkbe.h"
 #include "host_numerics.h"
@@ -27,9 +28,12 @@ namespace {
 constexpr long long kScratchCplx = HKBE_NOALLOC_SCRATCH_CPLX;
 static __device__ __align__(256) double2 g_scratch[kScratchCplx];
 
-// Device address of g_scratch, looked up once per device.
+// Device address of g_scratch, looked up once per device (std::call_once:
+// host threads may make their first calls at the same time).
 constexpr int kMaxDevices = 64;
+static std::once_flag g_scratch_once[kMaxDevices];
 static double2* g_scratch_ptr[kMaxDevices] = {nullptr};
+static cudaError_t g_scratch_err[kMaxDevices] = {cudaSuccess};
 
 int report(char* errbuf, size_t errlen, int code, const char* msg) {
   if (errbuf && errlen) {
@@ -65,12 +69,12 @@ extern "C" int hkbe_lesser_column_noalloc(int nt, int k, int nao, int r, double 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report(errbuf, errlen, HKBE_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return report(errbuf, errlen, HKBE_ERR_ARG, "device index too large");
-  if (!g_scratch_ptr[dev]) {  // set-up, once per device, with that device current
+  std::call_once(g_scratch_once[dev], [dev]() {  // set-up, once per device, with that device current
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return report(errbuf, errlen, HKBE_ERR_CUDA, cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<double2*>(p);
-  }
+    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_scratch);
+    if (g_scratch_err[dev] == cudaSuccess) g_scratch_ptr[dev] = static_cast<double2*>(p);
+  });
+  if (g_scratch_err[dev] != cudaSuccess) return report(errbuf, errlen, HKBE_ERR_CUDA, cudaGetErrorString(g_scratch_err[dev]));
   double2* base = g_scratch_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
 

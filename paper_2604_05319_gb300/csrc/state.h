@@ -44,8 +44,9 @@ struct Dev {
   Hod hod[4];          // 0 G^R, 1 G^<, 2 Sigma^R, 3 Sigma^<
   void* band;          // [n][nt][k][no2] Sigma^R(t, t-d), d = 1..k
   double2* proj;       // sweep projections [n][no][maxl][no2][rmax] (+ source: see kernels)
-  double2* tsvd_ws;    // TSVD workspace: [n][4][no2] groups of tsvd_ws_per entries,
-  long long tsvd_ws_per;  // level lv of a group at offset ws_lvoff[lv]
+  double2* tsvd_ws;    // TSVD workspace: [tsvd_group][4][no2] slots of tsvd_ws_per entries,
+  long long tsvd_ws_per;  // level lv of a slot at offset ws_lvoff[lv]; the compression
+  int tsvd_group;         // runs tsvd_group instances at a time on one shared workspace
   const long long* ws_lvoff;
   int* status;         // [0] rank overflow count, [1] Jacobi non-convergence count
   // frozen 32-point chunk inverses of the two sweeps (FP64): [n][nchunk][2][(32 no)^2]
@@ -76,12 +77,12 @@ struct Dev {
   double2 *diag64;             // [n][nt][no2]    FP64 history of G^<(t, t) (diagonal scheme)
   double *err;                 // [n]
   int *active;                 // [n]
+  const int *last;             // [n] last time step of each instance (N_t of the instance - 1)
 };
 
 // ---- launchers (all on `s`) ----
 cudaError_t launch_extrapolate(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_sigma(const Dev& d, int T, cudaStream_t s);
-cudaError_t launch_ret(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_mixed(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_vt(const Dev& d, int T, cudaStream_t s);
 cudaError_t launch_src(const Dev& d, int T, cudaStream_t s);

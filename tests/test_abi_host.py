@@ -75,6 +75,23 @@ def test_create_rejects_bad_arguments_without_gpu():
         assert e.value.code == -1
 
 
+def test_create_rejects_split_precision_and_bad_nt_per_inst_without_gpu():
+    """Precision modes 2 and 3 (split-operand tensor-core forms) are refused
+    with the reason; a per-instance N_t outside k+2..nt is refused."""
+    base = dict(nt=16, k=2, nao=1, xi=-1, n_inst=3, rho_mode=0, precision=0, max_iter=10, h=0.1, beta=1.0,
+                tol=1e-10)
+    for prec in (pk.PREC_TF32X3, pk.PREC_BF16X3):
+        with pytest.raises(pk.HKBEError) as e:
+            pk.hkbe_create(pk.hkbe_params(**dict(base, precision=prec)))
+        assert e.value.code == pk.HKBE_ERR_ARG and "matrix-vector" in str(e.value)
+    for bad in ([16, 16, 17], [16, 3, 16]):
+        with pytest.raises(pk.HKBEError) as e:
+            pk.hkbe_create(pk.hkbe_params(**base), nt_per_inst=bad)
+        assert e.value.code == pk.HKBE_ERR_ARG and "nt_per_inst" in str(e.value)
+    with pytest.raises(ValueError):
+        pk.hkbe_create(pk.hkbe_params(**base), nt_per_inst=[16, 16])
+
+
 def _fnv_words(data):
     """FNV-1a 64 over little-endian 64-bit words, the last one zero-padded
     (the checkpoint trailer's definition in include/hkbe.h)."""
@@ -99,7 +116,7 @@ def test_checkpoint_load_refuses_bad_files_without_gpu(tmp_path):
     assert e.value.code == pk.HKBE_ERR_IO and "magic" in str(e.value)
     p = pk.hkbe_params(nt=16, k=2, nao=1, xi=-1, n_inst=1, rho_mode=0, precision=0, max_iter=10,
                        h=0.1, beta=1.0, tol=1e-10)
-    head = b"HKBECKP1" + (1).to_bytes(4, "little") + C.sizeof(p).to_bytes(4, "little") + bytes(p)
+    head = b"HKBECKP1" + (2).to_bytes(4, "little") + C.sizeof(p).to_bytes(4, "little") + bytes(p)
     (tmp_path / "short.ckp").write_bytes(head[:-3])
     with pytest.raises(pk.HKBEError) as e:
         pk.hkbe_load(str(tmp_path / "short.ckp"))
@@ -118,9 +135,10 @@ def test_checkpoint_load_refuses_bad_files_without_gpu(tmp_path):
     with pytest.raises(pk.HKBEError) as e:
         pk.hkbe_load(str(tmp_path / "flipped.ckp"))
     assert e.value.code == pk.HKBE_ERR_IO and "checksum" in str(e.value)
-    (tmp_path / "v2.ckp").write_bytes(b"HKBECKP1" + (2).to_bytes(4, "little") + head[12:] + sc)
+    # a version-1 file (before the checksum trailer and the per-instance N_t) gets the version error
+    (tmp_path / "v1.ckp").write_bytes(b"HKBECKP1" + (1).to_bytes(4, "little") + head[12:] + sc)
     with pytest.raises(pk.HKBEError) as e:
-        pk.hkbe_load(str(tmp_path / "v2.ckp"))
+        pk.hkbe_load(str(tmp_path / "v1.ckp"))
     assert e.value.code == pk.HKBE_ERR_IO and "version" in str(e.value)
     assert pk.load().hkbe_save(None, b"x") == -1
     assert pk.load().hkbe_load(None, None, None) == -1

@@ -41,32 +41,50 @@ def test_partition_tiles_the_lower_triangle():
 
 
 def test_bytes_model_counts_every_stored_element_once():
+    """With the paper's per-step front c = T - k, the model's history H(T)
+    equals a one-by-one count: uncompressed rows s >= c (s + 1 elements),
+    below c every element either in its leaf triangle or in exactly one block,
+    whose factors hold (built rows + columns) x rank elements."""
     nt, L, k, no, r = 1000, 64, 5, 2, 30
     n2 = no * no
     blk = _partition(nt, L)
     rng = np.random.default_rng(3)
     ranks = rng.integers(1, 20, size=(len(blk["r0"]), n2))
     for T, es in ((999, 8), (700, 16), (130, 8)):
-        c = ((T - k) // L) * L                    # compression front after step T (whole leaves <= T - k)
-        direct = leaf = fac = 0
-        for s in range(c, T + 1):                 # uncompressed rows: (s, 0..s)
+        c = T - k
+        direct = leaf = inblock = 0
+        for s in range(c, T + 1):
             direct += s + 1
-        for s in range(c):                        # below the front: leaf triangle or one block
+        for s in range(c):
             for t in range(s + 1):
                 if s // L == t // L:
                     leaf += 1
-        for b in range(len(blk["r0"])):           # factors: built rows of U, all columns of V
+                else:
+                    inblock += 1
+        fac = 0
+        covered = 0
+        for b in range(len(blk["r0"])):
             r0, r1, c0, c1 = blk["r0"][b], blk["r1"][b], blk["c0"][b], blk["c1"][b]
             if r0 < c:
                 fac += (min(r1, c) - r0 + (c1 - c0)) * int(ranks[b].sum())
-        band = c * k * n2 * es
+                covered += (min(r1, c) - r0) * (c1 - c0)
+        assert covered == inblock                 # the built blocks hold exactly the off-leaf elements
+        H = (direct + leaf) * n2 + fac
         row = (T + 1) * n2
-        expect_ret = (direct + leaf) * n2 * es + fac * es + band + row * (32 + es)   # no frozen inverses
-        got = bench.phase_bytes("ret", T, c, 0, no, r, L, k, es, blk, ranks)
-        assert got == expect_ret, (T, got, expect_ret)
-        expect_src = (direct + leaf) * n2 * es + fac * es + band + row * es + (T + 1) * r * n2 * 16 + row * 16
-        assert bench.phase_bytes("src", T, c, 0, no, r, L, k, es, blk, ranks) == expect_src
-        assert bench.phase_bytes("ret", T, c, 3, no, r, L, k, es, blk, ranks) - got == 3 * (32 * no) ** 2 * 16
+        assert bench.history_all_pairs(T, k, L, no, blk, ranks, True) == H
+        assert bench.phase_bytes("ret", T, k, no, r, L, es, blk, ranks, True) == H * es + 2 * row * es
+        expect_src = H * es + row * es + (T + 1) * r * n2 * 16 + row * 16
+        assert bench.phase_bytes("src", T, k, no, r, L, es, blk, ranks, True) == expect_src
+        assert bench.phase_flops("les", T, k, no, L, blk, ranks, True) == 8 * no * H
+    # dense storage: the whole lower triangle
+    assert bench.history_all_pairs(9, 5, 64, 2, None, None, False) == 4 * 55
+
+
+def test_window_starts_on_a_compression_step():
+    for nt, k, L in ((8192, 5, 64), (4096, 5, 64), (2048, 3, 32)):
+        T = bench.window_start(nt, k, L, True)
+        assert T >= nt // 4 and (T - k) % L == 0 and T - nt // 4 < L
+    assert bench.window_start(256, 5, 64, False) == 64
 
 
 def test_library_partition_matches_the_definition():

@@ -24,8 +24,8 @@ N_INST, NT_CHECK, SAMPLE, T_QUENCH = 304, 281, 303, 250
 
 
 def test_c2_batch_full_size_first_steps():
-    import bench                                      # the bench's own inputs
-    w = bench._batch_c2(N_INST)                       # N_t = 4096
+    import kbe_workloads as wk                        # the bench's own inputs
+    w = wk.c2_batch_workload(N_INST)                  # N_t = 4096
     wl = w["wl"]
     st = pk.Stepper(wl.nt, wl.h, wl.k, wl.beta, nao=1, n_inst=N_INST, rho_mode=wl.rho_mode,
                     max_iter=wl.max_iter, tol=1e-7, precision=pk.PREC_MIXED, svd_tol=wl.svd_tol,
@@ -37,7 +37,7 @@ def test_c2_batch_full_size_first_steps():
     T = NT_CHECK - 1
     assert pk.hkbe_get_ranks(st.h, SAMPLE, 0, len(pk.hkbe_get_blocks(st.h)["r0"]), 1)[1] == 256
 
-    ws = bench._batch_c2(N_INST, nt=NT_CHECK)          # the same inputs on the first NT_CHECK steps
+    ws = wk.c2_batch_workload(N_INST, nt=NT_CHECK)          # the same inputs on the first NT_CHECK steps
     assert np.array_equal(ws["eps"], w["eps"][:, :NT_CHECK + 1])
     assert np.all(ws["eps"][:, :T_QUENCH + 1] == ws["eps"][0, :T_QUENCH + 1])
     o = from_workload(ws, inst=SAMPLE, tol=1e-13)
