@@ -361,14 +361,24 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
     d.status = h->status_dev;
   }
   if (d.prec) {
-    if ((rc = dalloc(h, &d.row64, (size_t)d.n_inst * 2 * d.nt * d.no * d.no)) ||
+    const size_t rowsz = (size_t)d.n_inst * 2 * d.nt * d.no * d.no, ringsz = (size_t)d.n_inst * d.ring * d.nt * d.no * d.no;
+    if ((!h->hodlr && (rc = dalloc(h, &d.row64, rowsz))) ||
         (rc = dalloc(h, &d.diag64, (size_t)d.n_inst * d.nt * d.no * d.no))) {
       g_create_error = h->err;
       hkbe_destroy(h);
       return rc;
     }
-    h->state_arrays.push_back({d.row64, (size_t)d.n_inst * 2 * d.nt * d.no * d.no * sizeof(double2)});
+    if (!h->hodlr) h->state_arrays.push_back({d.row64, rowsz * sizeof(double2)});
     h->state_arrays.push_back({d.diag64, (size_t)d.n_inst * d.nt * d.no * d.no * sizeof(double2)});
+    // FP64 copies of the ring rows of the four two-time components (compressed form)
+    for (int X = 0; h->hodlr && X < 4; ++X) {
+      if ((rc = dalloc(h, &d.ring64[X], ringsz))) {
+        g_create_error = h->err;
+        hkbe_destroy(h);
+        return rc;
+      }
+      h->state_arrays.push_back({d.ring64[X], ringsz * sizeof(double2)});
+    }
   }
   d.nchunk = (d.nt + 31) / 32;
   d.nfrozR = d.nfrozL = 0;
@@ -775,7 +785,8 @@ static int finish_start(hkbe_t* h) {
     HK_CUDA(h, grab_tv(h->snap_tv, d.GTV));
     HK_CUDA(h, grab_tv(h->snap_stv, d.STV));
   }
-  HK_CUDA(h, hk::launch_diag_seed(d, h->s));
+  HK_CUDA(h, hk::launch_diag_seed(d, h->s));   // also seeds the FP64 row copies of the start square
+  d.use64 = d.ring64[0] ? 1 : 0;
   h->cur = d.k;
   return HKBE_OK;
 }
@@ -1377,6 +1388,7 @@ int hkbe_load(const char* path, void* stream, hkbe_t** out) {
   h->have_model = sc.have_model != 0;
   h->self_consistent = sc.self_consistent != 0;
   h->cur = sc.cur;
+  d.use64 = (h->cur >= 0 && d.ring64[0]) ? 1 : 0;
   d.model = sc.model;
   d.cdir = sc.cdir;
   d.nfrozR = sc.nfrozR;

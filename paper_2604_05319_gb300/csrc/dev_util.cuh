@@ -20,6 +20,10 @@ __device__ __forceinline__ int front_of(const Dev& d, int n) {
   return d.cdir < fz ? d.cdir : fz;
 }
 
+__device__ __forceinline__ void* ringX(const Dev& d, int X) {
+  return X == 0 ? d.GR : X == 1 ? d.GL : X == 2 ? d.SR : d.SL;
+}
+
 // Row T of a two-time component: the dense lower triangle, or (compressed
 // storage) the ring of uncompressed rows, slot T mod ring.
 // S is the storage element type (double2 or float2).
@@ -29,6 +33,26 @@ __device__ __forceinline__ S* el(void* base, const Dev& d, int n, int T, int t) 
   if (d.ring) return b + (((long long)n * d.ring + (T % d.ring)) * d.nt + t) * (NO * NO);
   return b + ((long long)n * d.ntri + tri(T) + t) * (NO * NO);
 }
+// FP64 copy of element (T, t) of component X (complex64 compressed form).
+template <int NO>
+__device__ __forceinline__ double2* el64(const Dev& d, int X, int n, int T, int t) {
+  return d.ring64[X] + (((long long)n * d.ring + (T % d.ring)) * d.nt + t) * (NO * NO);
+}
+// Entry q of element (T, t) of component X in FP64: from the FP64 copy when
+// there is one (and it is seeded), else from the storage.
+template <int NO, typename S>
+__device__ __forceinline__ zd ldx(const Dev& d, int X, int n, int T, int t, int q) {
+  if (d.ring64[X] && d.use64) return ld(el64<NO>(d, X, n, T, t) + q);
+  return ld(el<NO, S>(ringX(d, X), d, n, T, t) + q);
+}
+// Write entry q of element (T, t) of component X: the storage (rounded in the
+// complex64 form) and the FP64 copy.
+template <int NO, typename S>
+__device__ __forceinline__ void stx(const Dev& d, int X, int n, int T, int t, int q, const zd& v) {
+  st(el<NO, S>(ringX(d, X), d, n, T, t) + q, v);
+  if (d.ring64[X]) st(el64<NO>(d, X, n, T, t) + q, v);
+}
+
 // Mixed components G^tv, Sigma^tv: complex128 in both precision forms (their
 // DLR convolution is ill-conditioned; they are r/T times smaller than a row set).
 template <int NO>

@@ -9,9 +9,6 @@ namespace hk {
 constexpr int CHH = 32;     // sweep sub-chunk (the leaf size is a multiple)
 constexpr int NWH = 8;      // warps per sweep CTA
 
-__device__ __forceinline__ void* ringX(const Dev& d, int X) {
-  return X == 0 ? d.GR : X == 1 ? d.GL : X == 2 ? d.SR : d.SL;
-}
 template <int NO, typename S>
 __device__ __forceinline__ S* Up(const Dev& d, int X, int n, int b, int p) {
   const long long rows = d.b_r1[b] - d.b_r0[b];

@@ -81,10 +81,8 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
   if (idx <= T) {
     const int t = idx;
     zd GR[4], GLc[4], GLr[4], GGr[4], GGc[4], Sg[4], Sl[4];
-    const S* pr = el<2, S>(d.GR, d, n, T, t);
-    const S* pl = el<2, S>(d.GL, d, n, T, t);            // G^<(t, T)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { GR[q] = ld(pr + q); GLc[q] = ld(pl + q); }
+    for (int q = 0; q < 4; ++q) { GR[q] = ldx<2, S>(d, 0, n, T, t, q); GLc[q] = ldx<2, S>(d, 1, n, T, t, q); }  // GLc: G^<(t, T)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -109,7 +107,6 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
       dg = zd(0, -1) * (zd(cx, -sx) * (nb + 1.0) + zd(cx, sx) * nb) * zd(0, g * g);
       dl = zd(0, -1) * (zd(cx, sx) * (nb + 1.0) + zd(cx, -sx) * nb) * zd(0, g * g);
     }
-    S* sr = el<2, S>(d.SR, d, n, T, t);
     zd slr[4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -118,14 +115,13 @@ __device__ void nambu_sigma(const Dev& d, int n, int T, int idx) {
         const double w = v2 * s[i] * s[j] * cos(s[i] * A[T + 1] - s[j] * A[t + 1]);
         const double ssij = s[i] * s[j];
         const zd mg = dg * GGr[i * 2 + j] * ssij, ml = dl * GLr[i * 2 + j] * ssij;
-        st(sr + i * 2 + j, Sg[i * 2 + j] - Sl[i * 2 + j] + GR[i * 2 + j] * w + mg - ml);
+        stx<2, S>(d, 2, n, T, t, i * 2 + j, Sg[i * 2 + j] - Sl[i * 2 + j] + GR[i * 2 + j] * w + mg - ml);
         slr[i * 2 + j] = Sl[i * 2 + j] + GLr[i * 2 + j] * w + ml;               // Sigma^<(T, t)
       }
-    S* sl = el<2, S>(d.SL, d, n, T, t);                                         // stores Sigma^<(t, T)
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i)                                                  // stores Sigma^<(t, T)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) st(sl + i * 2 + j, -slr[j * 2 + i].conj());
+      for (int j = 0; j < 2; ++j) stx<2, S>(d, 3, n, T, t, i * 2 + j, -slr[j * 2 + i].conj());
     if (t == T) {  // Fock term of Eq. SigmaF, Sigma^F_ij = -U(T) rho_ij [i = bar j], rho = xi i G^<(T,T)
       const zd rxi(0, (double)d.xi);
       const double2* ee = d.eps_ext + ((long long)n * (d.nt + 1) + T + 1) * 4;
@@ -202,11 +198,21 @@ __global__ void k_sigma(Dev d, int T) {
       for (int e = 0; e < NO2; ++e) st(dst + e, zd());
     }
   };
-  if (idx <= T) {
-    apply(el<NO, S>(d.GR, d, n, T, idx), el<NO, S>(d.SR, d, n, T, idx), 0, (T - idx) * d.h, 0.0);
-  } else if (idx <= 2 * T + 1) {
-    const int t = idx - (T + 1);
-    apply(el<NO, S>(d.GL, d, n, T, t), el<NO, S>(d.SL, d, n, T, t), 1, (t - T) * d.h, 0.0);
+  if (idx <= 2 * T + 1) {   // two-time rows: read G and write Sigma in FP64 where the form keeps FP64 copies
+    const int X = idx <= T ? 0 : 1, t = idx <= T ? idx : idx - (T + 1);
+    zd out[NO2];
+    if (d.model == 1) {  // Bethe: Sigma = v^2 G
+      const double v2 = mp[0] * mp[0];
+#pragma unroll
+      for (int e = 0; e < NO2; ++e) out[e] = ldx<NO, S>(d, X, n, T, t, e) * v2;
+    } else if (d.model == 2) {
+      bath_sigma<NO>(mp, zd(), 0.0, X, d, X == 0 ? (T - t) * d.h : (t - T) * d.h, 0.0, out);
+    } else {
+#pragma unroll
+      for (int e = 0; e < NO2; ++e) out[e] = zd();
+    }
+#pragma unroll
+    for (int e = 0; e < NO2; ++e) stx<NO, S>(d, X + 2, n, T, t, e, out[e]);
   } else {
     const int i = idx - 2 * (T + 1);
     apply(tv<NO>(d.GTV, d, n, T, i), tv<NO>(d.STV, d, n, T, i), 2, T * d.h, d.tau[i]);
@@ -234,33 +240,20 @@ __global__ void k_extrap(Dev d, int T) {
   }
   zd acc[NO2];
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
-  S* dst = nullptr;
-  if (idx <= T) {
-    const int tp = idx;
-    dst = el<NO, S>(d.GR, d, n, T, tp);
-    if (tp == T) {
+  if (idx <= 2 * T + 1) {   // G^R row (X = 0) or G^< column (X = 1), from the FP64 copies where kept
+    const int X = idx <= T ? 0 : 1, tp = idx <= T ? idx : idx - (T + 1);
+    if (X == 0 && tp == T) {
       for (int x = 0; x < NO; ++x) acc[x * NO + x] = zd(0, -1);
     } else if (tp >= k + 1 || tp == 0) {
       for (int l = 0; l <= k; ++l) {
-        const S* s = (tp == 0) ? el<NO, S>(d.GR, d, n, T - 1 - l, 0) : el<NO, S>(d.GR, d, n, T - 1 - l, tp - 1 - l);
-        for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
+        const int c = (tp == 0) ? 0 : tp - 1 - l;
+        for (int q = 0; q < NO2; ++q) acc[q] += ldx<NO, S>(d, X, n, T - 1 - l, c, q) * e[l];
       }
     } else {
-      const S* s = el<NO, S>(d.GR, d, n, T - 1, tp - 1);
-      for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
+      for (int q = 0; q < NO2; ++q) acc[q] = ldx<NO, S>(d, X, n, T - 1, tp - 1, q);
     }
-  } else if (idx <= 2 * T + 1) {
-    const int t = idx - (T + 1);
-    dst = el<NO, S>(d.GL, d, n, T, t);
-    if (t >= k + 1 || t == 0) {
-      for (int l = 0; l <= k; ++l) {
-        const S* s = (t == 0) ? el<NO, S>(d.GL, d, n, T - 1 - l, 0) : el<NO, S>(d.GL, d, n, T - 1 - l, t - 1 - l);
-        for (int q = 0; q < NO2; ++q) acc[q] += ld(s + q) * e[l];
-      }
-    } else {
-      const S* s = el<NO, S>(d.GL, d, n, T - 1, t - 1);
-      for (int q = 0; q < NO2; ++q) acc[q] = ld(s + q);
-    }
+    for (int q = 0; q < NO2; ++q) stx<NO, S>(d, X, n, T, tp, q, acc[q]);
+    return;
   } else {
     const int i = idx - 2 * (T + 1);
     for (int l = 0; l <= k; ++l) {
@@ -269,9 +262,7 @@ __global__ void k_extrap(Dev d, int T) {
     }
     double2* dtv = tv<NO>(d.GTV, d, n, T, i);
     for (int q = 0; q < NO2; ++q) st(dtv + q, acc[q]);
-    return;
   }
-  for (int q = 0; q < NO2; ++q) st(dst + q, acc[q]);
 }
 
 constexpr int CH = 32;     // chunk of the sequential sweeps
@@ -657,6 +648,7 @@ __global__ void k_rho(Dev d, int T) {
     zd x = b[q] * zd(0, -xi);  // G^<(T,T) = -i xi rho
     e = fmax(e, sqrt((x - ld(p + q)).abs2()));
     st(p + q, x);
+    if (d.ring64[1]) st(el64<NO>(d, 1, n, T, T) + q, x);
     if (!f64) st(d.diag64 + ((long long)n * d.nt + T) * NO2 + q, x);
   }
   atomic_max_nonneg(d.err + n, e);
@@ -669,6 +661,18 @@ __global__ void k_diag_seed(Dev d) {
   for (int e = threadIdx.x; e < (d.k + 1) * NO2; e += blockDim.x) {
     const int t = e / NO2, q = e % NO2;
     st(d.diag64 + ((long long)n * d.nt + t) * NO2 + q, ld(el<NO, S>(d.GL, d, n, t, t) + q));
+  }
+  // FP64 copies of the start square's G^R and G^< rows (complex64 compressed form)
+  const int sq = (d.k + 1) * (d.k + 2) / 2;
+  for (int X = 0; X < 2; ++X) {
+    if (!d.ring64[X]) continue;
+    for (int e = threadIdx.x; e < sq * NO2; e += blockDim.x) {
+      const int el_ = e / NO2, q = e % NO2;
+      int T = 0;
+      while ((T + 1) * (T + 2) / 2 <= el_) ++T;
+      const int t = el_ - T * (T + 1) / 2;
+      st(el64<NO>(d, X, n, T, t) + q, ld(el<NO, S>(ringX(d, X), d, n, T, t) + q));
+    }
   }
 }
 

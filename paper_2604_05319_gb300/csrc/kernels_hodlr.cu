@@ -445,11 +445,13 @@ __global__ void __launch_bounds__(256) k_tsvd(Dev d, int A, int nb, int n0) {
   S* V = Vp<NO, S>(d, X, n, b, p);
   double* Sv = Sp<NO>(d, X, n, b, p);
   void* ring = ringX(d, X);
-  // E <- new rows (and max |E| for the complex64 rounding floor below)
+  // E <- new rows (and max |E| for the complex64 rounding floor below).  The
+  // complex64 form reads them from its FP64 copies: rows free of storage
+  // rounding, whose residuals against V hold real directions only.
   double emax = 0.0;
   for (long long e = tid; e < (long long)nb * ncol; e += blockDim.x) {
     const int i = (int)(e / ncol), l = (int)(e % ncol);
-    const zd v = ld(el<NO, S>(ring, d, n, A + i, c0 + l) + p);
+    const zd v = d.ring64[X] ? ld(el64<NO>(d, X, n, A + i, c0 + l) + p) : ld(el<NO, S>(ring, d, n, A + i, c0 + l) + p);
     emax = fmax(emax, v.abs2());
     st(Em + (long long)i * ncol + l, v);
   }
@@ -796,8 +798,8 @@ __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
   if (b <= T) {
     const int t = b;
     if (q < N) {
-      const zd gr = ld(el<1, S>(d.GR, d, q, T, t));
-      const zd glc = ld(el<1, S>(d.GL, d, q, T, t));     // G^<(t, T)
+      const zd gr = ldx<1, S>(d, 0, q, T, t, 0);
+      const zd glc = ldx<1, S>(d, 1, q, T, t, 0);         // G^<(t, T)
       const zd glr = -glc.conj();                         // G^<(T, t)
       const zd ggr = gr + glr;                            // G^>(T, t)
       X1[q] = ggr; X2[q] = glr; Y1[q] = glc; Y2[q] = -ggr.conj();
@@ -816,8 +818,8 @@ __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
     lat_dft2(X1, tmp, tw, L, -1, 1.0);
     lat_dft2(X2, tmp, tw, L, -1, 1.0);
     if (q < N) {
-      st(el<1, S>(d.SR, d, q, T, t), X1[q] - X2[q]);
-      st(el<1, S>(d.SL, d, q, T, t), -X2[q].conj());
+      stx<1, S>(d, 2, q, T, t, 0, X1[q] - X2[q]);
+      stx<1, S>(d, 3, q, T, t, 0, -X2[q].conj());
     }
   } else {
     const int i = b - (T + 1), r = d.r;

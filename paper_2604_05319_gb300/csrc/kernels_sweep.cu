@@ -29,19 +29,22 @@ using Y = double2;       // element type of the row / column being solved
 template <int NO> constexpr bool kStage = NO <= 2;   // hot-chunk coefficients staged in shared memory
 template <int NO> constexpr size_t kStageBytes = kStage<NO> ? sizeof(zd) * CK * CK * NO * NO : 0;
 
-// Where a sweep keeps the row it solves: in place (FP64 storage) or in the
-// FP64 buffer row64[n][which] (complex64 storage).
+// Where a sweep keeps the row it solves: in place (FP64 storage), or in FP64
+// next to the complex64 storage: the row's slot of the FP64 ring copies of the
+// compressed form (which the TSVD later compresses), else the buffer
+// row64[n][which] of the dense form.
 template <int NO, typename S>
 struct Row64 {
   static constexpr bool separate = true;
-  __device__ static Y* get(const Dev& d, int n, int which, S*) {
+  __device__ static Y* get(const Dev& d, int n, int which, int T, S*) {
+    if (d.ring64[which]) return el64<NO>(d, which, n, T, 0);
     return d.row64 + ((long long)n * 2 + which) * d.nt * (NO * NO);
   }
 };
 template <int NO>
 struct Row64<NO, double2> {
   static constexpr bool separate = false;
-  __device__ static Y* get(const Dev&, int, int, double2* p) { return p; }
+  __device__ static Y* get(const Dev&, int, int, int, double2* p) { return p; }
 };
 
 // Inverse of frozen chunk cc of sweep `which`: complex128 in both storage
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
   // the complex64 form), which the FP32 bulk sums read; it holds the previous
   // iterate until an element is overwritten (the convergence measure).
   S* rowp = el<NO, S>(d.GR, d, n, T, 0);
-  Y* rowy = Row64<NO, S>::get(d, n, 0, rowp);
+  Y* rowy = Row64<NO, S>::get(d, n, 0, T, rowp);
   auto yp = [&](int tp) { return rowy + (long long)tp * NO2 + irow * NO; };
   auto sp = [&](int tp) { return rowp + (long long)tp * NO2 + irow * NO; };
   double myerr = 0.0;
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
   if (tid == 0) serr = 0.0;
   // FP64 column during the sweep (see k_ret2); xp: as solved, sp: storage
   S* colp = el<NO, S>(d.GL, d, n, T, 0);
-  Y* coly = Row64<NO, S>::get(d, n, 1, colp);
+  Y* coly = Row64<NO, S>::get(d, n, 1, T, colp);
   auto xp = [&](int t) { return coly + (long long)t * NO2; };  // element [m*NO + jc]
   auto sp = [&](int t) { return colp + (long long)t * NO2; };
   const double2* qs = d.qsrc + (long long)n * d.nt * NO2;

@@ -74,6 +74,14 @@ struct Dev {
   long long scratch_per_inst;
   // complex64 storage form only (null otherwise):
   double2 *row64;              // [n][2][nt][no2] FP64 row of G^R / column of G^< being solved
+                               // (dense storage; the compressed form solves in ring64)
+  // complex64 compressed form only: FP64 copies of the ring rows of G^R, G^<,
+  // Sigma^R, Sigma^< ([n][ring][nt][no2], the storage ring's slots).  The
+  // sweeps solve into them, the self-energy and the extrapolation read them,
+  // and the TSVD compresses from them, so appended rows carry no complex64
+  // rounding noise (null otherwise).
+  double2 *ring64[4];
+  int use64;                   // 1 once the start square's copies are seeded
   double2 *diag64;             // [n][nt][no2]    FP64 history of G^<(t, t) (diagonal scheme)
   double *err;                 // [n]
   int *active;                 // [n]

@@ -70,3 +70,35 @@ def test_lattice_2b_mixed():
     w, o = _case()
     st = _run(w, tol=1e-7, precision=pk.PREC_MIXED)
     assert _err(st, o)[1] < 1e-6
+
+
+def test_lattice_16x16_c3_parameters():
+    """C3's own grid and parameters (16 x 16 k, J = 1, U = 2 quenched on at
+    t = 0, beta = 10, h = 0.02, undriven) on a short propagation: the L = 16
+    path of the real-space self-energy (256 threads, one per k-point and
+    real-space point) against stored oracle rows of eight k-points and the
+    lattice observables at every t (tests/golden/late_rows_c3.npz, written by
+    tests/golden/make_late_rows.py from the oracle alone); dense FP64 within
+    1e-10, complex64 within 1e-6."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "late_rows_c3.npz"))
+    w = wk.lattice_workload(L=16, nt=40, h=0.02, k=5, beta=10.0, U=2.0, t_quench=0.0)
+    nt = w["wl"].nt
+    idx = np.tril_indices(nt)
+    for prec, tol, bound in ((pk.PREC_FP64, 1e-13, 1e-10), (pk.PREC_MIXED, 1e-7, 1e-6)):
+        st = _run(w, tol=tol, precision=prec)
+        ref = max(np.abs(g[f"gr_{q}"]).max() for q in g["k_sample"])
+        err = 0.0
+        for q in g["k_sample"]:
+            GR, GL, GTV = st.dense(int(q))
+            err = max(err, np.abs(GR[idx] - g[f"gr_{q}"]).max(), np.abs(GL[idx] - g[f"gl_{q}"]).max(),
+                      np.abs(GTV - g[f"gtv_{q}"]).max())
+        assert err < bound * ref, (prec, err)
+        oerr = np.zeros(3)
+        for t in range(nt):
+            ob = pk.hkbe_get_lattice_observables(st.h, t)
+            oerr = np.maximum(oerr, np.abs(np.asarray(ob) - [g["n"][t], g["ekin"][t], g["j"][t]]))
+        print("16 x 16", "FP64" if prec == pk.PREC_FP64 else "complex64", "max error: G", err,
+              "n, E_kin, j", oerr.tolist())
+        assert (oerr < bound * np.maximum(1.0, np.abs([g["n"], g["ekin"], g["j"]]).max(axis=1))).all(), oerr
+        st.close()
