@@ -320,9 +320,9 @@ int hkbe_rewind(hkbe_t* h);
 /* In-memory checkpoint of the whole propagation state (Sec. 3.6 keeps the
  * full state in checkpoint files for a restart; this keeps one copy in device
  * memory instead).  hkbe_snapshot_save copies every device buffer of the
- * handle (hkbe_get_stats bytes) into a second device allocation made on the
- * first call and reused afterwards, together with the step counter and the
- * compression front.  hkbe_snapshot_restore copies it back: stepping the
+ * handle that holds state (all but its scratch workspaces) into a second
+ * device allocation made on the first call and reused afterwards, together
+ * with the step counter and the compression front.  hkbe_snapshot_restore copies it back: stepping the
  * restored handle repeats the run from the saved step bit for bit.
  * hkbe_snapshot_free releases the copy (hkbe_destroy does too).  Both run on
  * the handle's stream and return after it has finished.  Errors:

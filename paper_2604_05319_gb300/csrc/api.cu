@@ -52,7 +52,8 @@ struct hkbe_s {
   std::vector<std::pair<void*, size_t>> state_arrays;
   // in-memory snapshot (hkbe_snapshot_save): a device copy of every buffer in
   // allocs, plus the host-side counters that go with it
-  std::vector<void*> snap_dev;
+  std::vector<void*> snap_dev;     // nullptr for scratch buffers (not part of the state)
+  std::vector<const void*> scratch;  // buffers whose contents do not outlive a kernel phase
   size_t snap_bytes = 0;
   int snap_cur = -1, snap_cdir = 0, snap_nfrozR = 0, snap_nfrozL = 0;
 };
@@ -359,6 +360,7 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
       return rc;
     }
     d.status = h->status_dev;
+    h->scratch.insert(h->scratch.end(), {d.tsvd_ws, h->rowbuf_r, h->rowbuf_l});
   }
   if (d.prec) {
     const size_t rowsz = (size_t)d.n_inst * 2 * d.nt * d.no * d.no, ringsz = (size_t)d.n_inst * d.ring * d.nt * d.no * d.no;
@@ -405,6 +407,7 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
     hkbe_destroy(h);
     return rc;
   }
+  h->scratch.insert(h->scratch.end(), {d.cinv_ws, h->diagbuf});
   cudaError_t e = cudaStreamSynchronize(h->s);
   if (e != cudaSuccess) {
     g_create_error = std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e);
@@ -421,7 +424,8 @@ int hkbe_destroy(hkbe_t* h) {
   drain(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
-  for (void* p : h->snap_dev) cudaFree(p);
+  for (void* p : h->snap_dev)
+    if (p) cudaFree(p);
   delete h;
   return HKBE_OK;
 }
@@ -1097,7 +1101,8 @@ int hkbe_get_stats(hkbe_t* h, int inst, int32_t* ranks, size_t* device_bytes) {
 
 int hkbe_snapshot_free(hkbe_t* h) {
   if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
-  for (void* p : h->snap_dev) cudaFree(p);
+  for (void* p : h->snap_dev)
+    if (p) cudaFree(p);
   h->snap_dev.clear();
   h->snap_bytes = 0;
   h->snap_cur = -1;
@@ -1111,6 +1116,10 @@ int hkbe_snapshot_save(hkbe_t* h) {
     hkbe_snapshot_free(h);
     for (size_t i = 0; i < h->allocs.size(); ++i) {
       void* p = nullptr;
+      if (std::find(h->scratch.begin(), h->scratch.end(), h->allocs[i]) != h->scratch.end()) {
+        h->snap_dev.push_back(nullptr);   // scratch: nothing to keep
+        continue;
+      }
       cudaError_t e = cudaMalloc(&p, h->alloc_bytes[i]);
       if (e != cudaSuccess) {
         hkbe_snapshot_free(h);
@@ -1121,7 +1130,8 @@ int hkbe_snapshot_save(hkbe_t* h) {
     }
   }
   for (size_t i = 0; i < h->allocs.size(); ++i)
-    HK_CUDA(h, cudaMemcpyAsync(h->snap_dev[i], h->allocs[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
+    if (h->snap_dev[i])
+      HK_CUDA(h, cudaMemcpyAsync(h->snap_dev[i], h->allocs[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->snap_cur = h->cur;
   h->snap_cdir = h->d.cdir;
@@ -1135,7 +1145,8 @@ int hkbe_snapshot_restore(hkbe_t* h) {
   if (h->snap_cur < 0 || h->snap_dev.size() != h->allocs.size())
     return fail(h, HKBE_ERR_ARG, "no snapshot to restore (hkbe_snapshot_save first)");
   for (size_t i = 0; i < h->allocs.size(); ++i)
-    HK_CUDA(h, cudaMemcpyAsync(h->allocs[i], h->snap_dev[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
+    if (h->snap_dev[i])
+      HK_CUDA(h, cudaMemcpyAsync(h->allocs[i], h->snap_dev[i], h->alloc_bytes[i], cudaMemcpyDeviceToDevice, h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->cur = h->snap_cur;
   h->d.cdir = h->snap_cdir;
