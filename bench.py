@@ -4,7 +4,7 @@
 One bench "step" is one KBE time step T of the whole batch: extrapolation,
 self-energy, retarded row, mixed, lesser source and column, density matrix,
 the self-consistency loop, and the HODLR compression of that step, for every
-instance.  Default workload: C4 (N_t = 8192, Nambu Holstein-Migdal, 76
+instance.  Default workload: C4 (N_t = 8192, Nambu Holstein-Migdal, 128
 instances), the configuration the metric is quoted on.
 
 The timed window is K consecutive time steps starting at T_s, the first step
@@ -61,7 +61,7 @@ WORKLOADS = {
                     "(g=0.5, w0=0.6), beta=50, N_t=8192, h=0.01, order 5, DLR Lambda=200 eps=1e-10, pulse "
                     "A(t)=A0 sin(t) exp(-(t-20)^2/50) (A0=0.3 instance 0, 0.3 U[0.5,1.5] others), HODLR "
                     "leaf 64, eps_SVD 1e-7, diagonal rho scheme, normal non-interacting initial state",
-               make=lambda n_inst, seed=0, **kw: wk.c4_batch_workload(n_inst, seed, **kw), n_inst=76, precision="mixed",
+               make=lambda n_inst, seed=0, **kw: wk.c4_batch_workload(n_inst, seed, **kw), n_inst=128, precision="mixed",
                tol_fp64=1e-12, tol_mixed=1e-7),
     "C2-batch": dict(desc="Bethe lattice (Sigma=v^2 G, v=1), beta=5, N_t=4096, h=0.02, order 5, DLR Lambda=100 "
                           "eps=1e-10, level quench 0 -> A at t=5 (A=1 for instance 0, U[0.5,1.5] for the others), "
@@ -74,6 +74,12 @@ WORKLOADS = {
                make=lambda n_inst, seed=0: wk.lattice_workload(L=16, nt=2048, h=0.02, k=5, beta=10.0, U=2.0,
                                                                 t_quench=0.0, svd_tol=1e-6, leaf=64),
                n_inst=256, precision="mixed", tol_fp64=1e-12, tol_mixed=1e-7),
+    "C3-ysymm": dict(desc="C3 on the reflection-reduced k-set: the 16 x 9 k-points with m_y <= 8 (144 instances; "
+                          "the mirror points enter the real-space sums through their instance), otherwise as C3",
+                     make=lambda n_inst, seed=0: wk.lattice_workload(L=16, nt=2048, h=0.02, k=5, beta=10.0, U=2.0,
+                                                                      t_quench=0.0, svd_tol=1e-6, leaf=64,
+                                                                      ysymm=True),
+                     n_inst=144, grid_points=256, precision="mixed", tol_fp64=1e-12, tol_mixed=1e-7),
     "C1": dict(desc="C1: Bethe lattice, beta=5, N_t=256, h=0.025, order 5, undriven, dense storage",
                make=lambda n_inst, seed=0: wk.c1_workload(seed=seed, n_inst=n_inst), n_inst=1,
                precision="fp64", tol_fp64=1e-12, tol_mixed=1e-7),
@@ -516,6 +522,67 @@ def run_c5(args, pk, torch):
     print(json.dumps(line))
 
 
+def run_scaling(args, pk, torch):
+    """Scaling study (the paper's "Timing results"): one propagation of a
+    small batch of the workload to N_t - 1; every `every` steps the per-step
+    device time (CUDA events over 16 steps), the epsilon-ranks against block
+    size (max over instances and orbital pairs, per component), and the stored
+    elements of the compressed form against the dense lower triangle.  Fits
+    the per-step time to T^p (the whole propagation then grows as N_t^(p+1);
+    the paper's Dyson solver: T^(2+alpha) in total) and the rank to block
+    size^q.  Prints one JSON record."""
+    wname = "C4" if args.workload in ("C4", "C4-batch") else args.workload
+    spec = WORKLOADS[wname]
+    n_inst = args.n_inst or 4
+    w = spec["make"](n_inst=n_inst, seed=0)
+    wl = w["wl"]
+    st = make_stepper(pk, w, pk.PREC_MIXED, spec["tol_mixed"])
+    blocks = pk.hkbe_get_blocks(st.h)
+    nb, no, k, L = len(blocks["r0"]), wl.nao, wl.k, wl.leaf
+    size = (blocks["r1"] - blocks["r0"]).astype(int)
+    every, probe = 512, 16
+    rec = {"T": [], "ms_per_step": [], "ranks_by_size": [], "compressed_over_dense": []}
+    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_all0 = time.perf_counter()
+    for Tm in range(every, wl.nt - probe, every):
+        st.step(Tm - pk.hkbe_current_step(st.h))
+        ev_a.record()
+        st.step(probe)
+        ev_b.record()
+        torch.cuda.synchronize()
+        T = pk.hkbe_current_step(st.h)
+        rk = np.array([pk.hkbe_get_stats(st.h, i, nb, no)[1] for i in range(n_inst)])  # [inst, 4, nblk, no2]
+        front = pk.hkbe_get_ranks(st.h, 0, 0, nb, no)[1]
+        by = {}
+        for sz in sorted(set(size.tolist())):
+            sel = size == sz
+            by[int(sz)] = [int(rk[:, X][:, sel].max()) for X in range(4)]
+        stored = 0
+        for b in range(nb):
+            if blocks["r0"][b] < front:
+                stored += ((min(int(blocks["r1"][b]), front) - int(blocks["r0"][b])) +
+                           int(blocks["c1"][b] - blocks["c0"][b])) * int(rk[0, 2, b].max())
+        stored += (front // L) * L * (L + 1) // 2 + sum(s2 + 1 for s2 in range(front, T + 1))
+        rec["T"].append(int(T))
+        rec["ms_per_step"].append(ev_a.elapsed_time(ev_b) / probe)
+        rec["ranks_by_size"].append(by)
+        rec["compressed_over_dense"].append(stored / ((T + 1) * (T + 2) / 2))
+    t_all = time.perf_counter() - t_all0
+    Ts, ms = np.array(rec["T"], float), np.array(rec["ms_per_step"])
+    half = Ts >= Ts.max() / 4
+    p_fit = float(np.polyfit(np.log(Ts[half]), np.log(ms[half]), 1)[0])
+    last = rec["ranks_by_size"][-1]
+    szs = np.array([s2 for s2 in last if max(last[s2]) > 0], float)
+    rks = np.array([max(last[int(s2)]) for s2 in szs], float)
+    q_fit = float(np.polyfit(np.log(szs), np.log(rks), 1)[0]) if len(szs) > 1 else None
+    out = {"study": "scaling", "workload": wname, "desc": spec["desc"], "n_inst": n_inst,
+           "precision": "mixed", "every": every, "probe_steps": probe, "propagation_s": round(t_all, 1),
+           "per_step_time_exponent": p_fit, "whole_run_exponent": p_fit + 1.0,
+           "rank_vs_block_size_exponent": q_fit, **rec}
+    st.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,9 +596,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps per process in cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle corrector iterations per step")
+    ap.add_argument("--study", default=None, choices=["scaling"], help="the scaling study instead of the bench line")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     wname = "C4" if args.workload == "C4-batch" else args.workload
+    if args.study == "scaling":
+        import torch
+        import paper_2604_05319_gb300 as pk
+        return run_scaling(args, pk, torch)
     if wname == "C5":
         import torch
         import paper_2604_05319_gb300 as pk
@@ -554,8 +626,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n_inst = args.n_inst or spec["n_inst"]
-    if wname == "C3" and n_inst != 256:
-        raise SystemExit("C3 has one instance per k-point of its 16 x 16 grid: --n-inst must be 256")
+    if wname.startswith("C3") and n_inst != spec["n_inst"]:
+        raise SystemExit(f"{wname} has one instance per k-point of its set: --n-inst must be {spec['n_inst']}")
     prec_name = spec["precision"]
     fp64_tf, fp32_tf = pk.hkbe_fma_peaks()
     main_arm = run_arm(pk, torch, spec, wname, n_inst, prec_name, args.steps, rank_seed(rank), dist, local,
@@ -625,6 +697,8 @@ def main():
             "gpu_launches": main_arm["launches"],
             "clocks": main_arm["clocks"],
         }
+        if spec.get("grid_points"):   # reduced k-set: each step advances every point of the full grid
+            line["config"]["grid_point_steps_per_s"] = spec["grid_points"] * K * world / t_win
         if fp64_arm is not None:
             f = fp64_arm
             fval = n_inst * f["K"] * world / f["t_win"]

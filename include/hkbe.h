@@ -115,7 +115,8 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
  * initial state for hkbe_set_matsubara.  No handle and no GPU needed.
  *   r, tau[r], omega[r], beta: the DLR grid (as for hkbe_set_dlr);
  *   model, params[n_inst][nparams]: as for hkbe_set_model (HKBE_MODEL_NONE,
- *     BETHE, NAMBU with optional [v, g, w0], LATTICE2B with params[0] = L);
+ *     BETHE, NAMBU with optional [v, g, w0], LATTICE2B with [L] or
+ *     [L, ysymm], the reduced k-set of hkbe_set_model);
  *   eps[n_inst][nao][nao] complex: the equilibrium-branch level eps(0_|);
  *   U_eq: interaction on the equilibrium branch (second Born and Fock);
  *   eta, n_eta: pairing field eta added to eps_01 and eps_10 for the first
@@ -193,14 +194,19 @@ int hkbe_set_hamiltonian_at(hkbe_t* h, int t, const double* eps_t);
        Eq. Model through order U^2.
  *   HKBE_MODEL_LATTICE2B: N_o = 1, one instance per k-point of an L x L grid,
  *       k = 2 pi (m_x, m_y)/L at instance m_x L + m_y, n_inst = L^2, L <= 16;
- *       params[n][0] = L.  Sigma^≷_k from Sigma^≷_r(T,t) =
+ *       params[n] = [L] or [L, ysymm].  ysymm = 1 (L even) keeps only the
+ *       k-points with m_y <= L/2, instance m_x (L/2+1) + m_y, n_inst =
+ *       L(L/2+1) (Sec. 4.2: the reflection k_y -> -k_y of a drive along x);
+ *       the grid point (m_x, L - m_y) is taken equal to (m_x, m_y) in every
+ *       lattice sum, which is exact when eps_k(t) and the initial state have
+ *       that symmetry (the caller's responsibility).  Sigma^≷_k from Sigma^≷_r(T,t) =
  *       U(T)U(t) G^≷_r(T,t)^2 G^≶_{-r}(t,T) (G_r the lattice Fourier
  *       transform over k; the mixed part with the imaginary branch latest),
  *       U(t) from hkbe_set_drive (instance 0; the same for every k).  The
  *       dispersion with its Peierls shift eps_{k-A(t)} is the caller's eps.
  *       The k-points iterate together (all or none).
- * Errors: HKBE_ERR_ARG (unknown model, wrong N_o or parameter count, L^2 !=
- * n_inst, w0 <= 0 with g != 0). */
+ * Errors: HKBE_ERR_ARG (unknown model, wrong N_o or parameter count, n_inst
+ * not L^2 (L(L/2+1) with ysymm), odd L with ysymm, w0 <= 0 with g != 0). */
 int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams);
 
 /* Drive of the Nambu model: A[n_inst][nt+1] (vector potential) and
@@ -278,7 +284,8 @@ int hkbe_get_density_at(hkbe_t* h, int t, double* rho_t);
  * spin summed where the paper does): out[0] = n = -(i/N_k) sum_k G^<_k(t,t)
  * (per spin), out[1] = E_kin = -(2i/N_k) sum_k eps_k G^<_k(t,t) with
  * eps_k = -2(cos k_x + cos k_y), out[2] = j = -(2i/N_k) sum_k
- * 2 sin(k_x - A(t)) G^<_k(t,t).  Reduced on the device.  HKBE_ERR_ARG for
+ * 2 sin(k_x - A(t)) G^<_k(t,t), the sums over the whole L x L grid (with
+ * ysymm a mirror point counts its instance).  Reduced on the device.  HKBE_ERR_ARG for
  * another model, HKBE_ERR_RANGE for t outside 0..current step. */
 int hkbe_get_lattice_observables(hkbe_t* h, int t, double* out);
 

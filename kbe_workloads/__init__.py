@@ -264,22 +264,27 @@ def nambu_workload(nt=200, h=0.02, k=5, beta=5.0, n_inst=1, v=1.0, eps0=0.0, pai
 
 def lattice_workload(L=4, nt=120, h=0.02, k=5, beta=10.0, U=2.0, t_quench=0.0, A0=0.0, Omega=1.0,
                      tc=1.0, width=0.5, A_step=0.0, dlr_lambda=100.0, dlr_eps=1e-10, tol=1e-12,
-                     max_iter=50, rho_mode=0, svd_tol=0.0, leaf=64):
+                     max_iter=50, rho_mode=0, svd_tol=0.0, leaf=64, ysymm=False):
     """2D Hubbard model on an L x L k-grid (Sec. 4.2), J = 1, half filling
     (Hartree absorbed, mu~ = 0), one instance per k = 2 pi (m_x, m_y)/L
     (instance m_x L + m_y).  Peierls drive along x: eps_k(t) =
     -2 (cos(k_x - A(t)) + cos k_y), with A(t) = A_step for t > 0 plus a
     pulse A0 sin(Omega t) exp(-(t-tc)^2/width); A = 0 on the equilibrium
     branch.  The interaction is quenched 0 -> U at t_quench, so the initial
-    state is the free lattice, G^M_k known in closed form."""
+    state is the free lattice, G^M_k known in closed form.  ysymm: only the
+    k-points with m_y <= L/2 (instance m_x (L/2+1) + m_y), the reflection-
+    reduced set of L(L/2+1) points (the drive along x keeps k_y -> -k_y)."""
+    if ysymm and L % 2:
+        raise ValueError("the reflection-reduced k-set needs an even L")
     tau, om = dlr_grid(dlr_lambda, dlr_eps, beta)
     m = np.arange(L) * 2 * np.pi / L
-    kx = np.repeat(m, L)
-    ky = np.tile(m, L)
+    ny = L // 2 + 1 if ysymm else L
+    kx = np.repeat(m, ny)
+    ky = np.tile(m[:ny], L)
     t = np.arange(nt) * h
     A = np.concatenate([[0.0], A_step * (t > 0) + A0 * np.sin(Omega * t) * np.exp(-(t - tc) ** 2 / width)])
     Uv = np.concatenate([[0.0], np.where(t >= t_quench - 1e-12, U, 0.0)])
-    nk = L * L
+    nk = L * ny
     eps = np.zeros((nk, nt + 1, 1, 1), complex)
     gm = np.zeros((nk, len(tau), 1, 1), complex)
     for q in range(nk):
@@ -287,9 +292,10 @@ def lattice_workload(L=4, nt=120, h=0.02, k=5, beta=10.0, U=2.0, t_quench=0.0, A
         gm[q] = free_level_gm(tau, beta, np.array([[eps[q, 0, 0, 0].real]]))
     wl = Workload(name="lattice", model="lattice2b", nt=nt, h=h, k=k, beta=beta, nao=1, n_inst=nk,
                   dlr_lambda=dlr_lambda, dlr_eps=dlr_eps, svd_tol=svd_tol, leaf=leaf, tol=tol,
-                  max_iter=max_iter, rho_mode=rho_mode, params={"L": L})
+                  max_iter=max_iter, rho_mode=rho_mode, params={"L": L, "ysymm": bool(ysymm)})
+    mpar = [float(L), 1.0] if ysymm else [float(L)]
     return {"wl": wl, "tau": tau, "omega": om, "eps": eps, "gm": gm, "L": L, "kx": kx, "ky": ky,
-            "model_params": np.array([[float(L)]] * nk), "drive_A": np.tile(A, (nk, 1)),
+            "model_params": np.array([mpar] * nk), "drive_A": np.tile(A, (nk, 1)),
             "drive_U": np.tile(Uv, (nk, 1))}
 
 

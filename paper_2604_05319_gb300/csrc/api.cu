@@ -565,14 +565,21 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
     h->self_consistent = false;
   } else if (model == HKBE_MODEL_LATTICE2B) {
     if (no != 1) return fail(h, HKBE_ERR_ARG, "LATTICE2B needs nao = 1");
-    if (!params || nparams < 1) return fail(h, HKBE_ERR_ARG, "LATTICE2B needs params[0] = L");
+    if (!params || nparams < 1 || nparams > 2) return fail(h, HKBE_ERR_ARG, "LATTICE2B needs params [L] or [L, ysymm]");
     const int L = (int)params[0];
-    if (L < 1 || L > 16 || L * L != d.n_inst || (double)L != params[0])
-      return fail(h, HKBE_ERR_ARG, "LATTICE2B needs an integer L in 1..16 with n_inst = L*L");
+    const double ysp = nparams == 2 ? params[1] : 0.0;
+    if (ysp != 0.0 && ysp != 1.0) return fail(h, HKBE_ERR_ARG, "LATTICE2B ysymm must be 0 or 1");
+    const int ys = ysp != 0.0;
+    const int nk = ys ? L * (L / 2 + 1) : L * L;
+    if (L < 1 || L > 16 || (double)L != params[0] || (ys && L % 2) || nk != d.n_inst)
+      return fail(h, HKBE_ERR_ARG, "LATTICE2B needs an integer L in 1..16 with n_inst = L*L (L*(L/2+1), L even, with ysymm)");
     for (int n = 0; n < d.n_inst; ++n)
       if (h->last[n] != d.nt - 1)
         return fail(h, HKBE_ERR_ARG, "LATTICE2B couples its k-points through Sigma: every k needs the same N_t");
-    for (int n = 0; n < d.n_inst; ++n) mp[(size_t)n * hk::MP] = L;
+    for (int n = 0; n < d.n_inst; ++n) {
+      mp[(size_t)n * hk::MP] = L;
+      mp[(size_t)n * hk::MP + 1] = ys;
+    }
     h->self_consistent = true;
   } else if (model == HKBE_MODEL_NAMBU) {
     if (no != 2) return fail(h, HKBE_ERR_ARG, "NAMBU needs nao = 2");

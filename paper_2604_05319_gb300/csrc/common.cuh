@@ -59,6 +59,30 @@ template <typename R> HD cx<R> ldr(const cx<R>* p) { return *p; }
 HD zd wide(const zd& z) { return z; }
 HD zd wide(const zf& z) { return zd((double)z.re, (double)z.im); }
 
+// Accumulator of a long history sum in the bulk arithmetic R.  Complex64
+// form (R = float): compensated (Kahan) summation, the rounding of every
+// addition kept in c and fed back, so the sum keeps FP32 precision relative to
+// its value over any number of terms, on the FP32 pipes (an FP64 add costs a
+// warp about 64 cycles on this chip).  FP64 form: plain FP64 sum.
+template <typename R> struct KAcc;
+template <> struct KAcc<float> {
+  zf s, c;
+  HD KAcc() : s(0.f), c(0.f) {}
+  HD void add(const zf& x) {
+    const zf y = x - c;
+    const zf t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  HD zd get() const { return zd((double)s.re - (double)c.re, (double)s.im - (double)c.im); }
+};
+template <> struct KAcc<double> {
+  zd s;
+  HD KAcc() : s(0.0) {}
+  HD void add(const zd& x) { s += x; }
+  HD zd get() const { return s; }
+};
+
 HD zd cdiv(const zd& a, const zd& b) {
   double d = b.re * b.re + b.im * b.im;
   return zd((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);

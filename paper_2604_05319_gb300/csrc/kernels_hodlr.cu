@@ -70,42 +70,66 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   const int r0 = d.b_r0[b], rl = min(d.b_r1[b], c), c0 = d.b_c0[b], c1 = d.b_c1[b];
   const DevW& W = d.w;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ zd pbuf[8][128];
+  // YB values of y per pass over a factor row (N_o <= 2: all of them), so each
+  // factor row is read once per pair and side.
+  constexpr int YB = NO <= 2 ? NO : 1;
+  __shared__ zd pbuf[8][YB * 128];
   // P1 serves pair p = (x, z) (uses g[z]); P2 serves pair p = (z, x) (uses g[z]);
   // g_l[z][y] = conj(G^R(T,l)[y][z]).  Warps over rows / columns, lanes over rank.
-  for (int job = 0; job < NO2 * NO * 2; ++job) {
-    const int which = job & 1, y = (job >> 1) % NO, p = (job >> 1) / NO;
+  for (int job = 0; job < NO2 * 2 * (NO / YB); ++job) {
+    const int which = job & 1, rest = job >> 1;
+    const int yb = (rest % (NO / YB)) * YB, p = rest / (NO / YB);
     const int z = which == 0 ? p % NO : p / NO;
     const int rk = *Rk<NO>(d, 3, n, b, p);
     const S* F = which == 0 ? Up<NO, S>(d, 3, n, b, p) : Vp<NO, S>(d, 3, n, b, p);
     const int lo = which == 0 ? r0 : c0, hi = which == 0 ? rl : c1;
-    zd part[4] = {zd(), zd(), zd(), zd()};
+    KAcc<R> part[YB][4];   // compensated FP32 sums in the complex64 form
     for (int l0 = lo + warp; l0 < hi; l0 += 8 * FOLD) {
-      cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
+      cx<R> pp[YB][4];
+#pragma unroll
+      for (int yy = 0; yy < YB; ++yy)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pp[yy][u] = cx<R>(0);
 #pragma unroll
       for (int jj = 0; jj < FOLD; ++jj) {
         const int l = l0 + 8 * jj;
         if (l < hi) {
-          const cx<R> g = ldr<R>(el<NO, S>(d.GR, d, n, T, l) + y * NO + z).conj() * rule_wr<R>(W, T, l);
+          const R wl = rule_wr<R>(W, T, l);
+          const S* gp = el<NO, S>(d.GR, d, n, T, l);
+          cx<R> g[YB];
+#pragma unroll
+          for (int yy = 0; yy < YB; ++yy) g[yy] = ldr<R>(gp + (yb + yy) * NO + z).conj() * wl;
           const S* fr = F + (long long)(l - lo) * d.rmax;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int q = lane + 32 * u;
-            if (q < rk) pp[u] = cfma(g, ldr<R>(fr + q), pp[u]);
+            if (q < rk) {
+              const cx<R> f = ldr<R>(fr + q);
+#pragma unroll
+              for (int yy = 0; yy < YB; ++yy) pp[yy][u] = cfma(g[yy], f, pp[yy][u]);
+            }
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
+      for (int yy = 0; yy < YB; ++yy)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) part[yy][u].add(pp[yy][u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+    for (int yy = 0; yy < YB; ++yy)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pbuf[warp][yy * 128 + lane + 32 * u] = part[yy][u].get();
     __syncthreads();
     if (tid < d.rmax) {
-      zd acc = zd();
-      for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][tid];
-      const zd v = tid < rk ? acc * Sp<NO>(d, 3, n, b, p)[tid] : zd();
-      Psrc<NO, R>(d, n, b, p, y, which)[tid] = cx<R>((R)v.re, (R)v.im);
+      const double sv = tid < rk ? Sp<NO>(d, 3, n, b, p)[tid] : 0.0;
+#pragma unroll
+      for (int yy = 0; yy < YB; ++yy) {
+        zd acc = zd();
+        for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][yy * 128 + tid];
+        const zd v = acc * sv;
+        Psrc<NO, R>(d, n, b, p, yb + yy, which)[tid] = cx<R>((R)v.re, (R)v.im);
+      }
     }
     __syncthreads();
   }
@@ -137,6 +161,7 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
   zd acc[NO2];
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  KAcc<R> ka[NO2];   // the history sums: compensated FP32 in the complex64 form
   cx<R> pa[NO2];
   auto zero = [&]() {
 #pragma unroll
@@ -144,7 +169,7 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
   };
   auto fold = [&]() {
 #pragma unroll
-    for (int q = 0; q < NO2; ++q) acc[q] += wide(pa[q]);
+    for (int q = 0; q < NO2; ++q) ka[q].add(pa[q]);
     zero();
   };
   // pa[x][y] += sum_z Sx[x][z] g[z][y], Sx = S or S^dagger
@@ -213,7 +238,7 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
       const S* V = Vp<NO, S>(d, 3, n, b, p) + (long long)(t - c0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
-        acc[x * NO + y] += wide(lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 0), V, rk));
+        ka[x * NO + y].add(lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 0), V, rk));
       }
     }
   }
@@ -228,11 +253,13 @@ __global__ void __launch_bounds__(128) k_src_c(Dev d, int T) {
       const S* U = Up<NO, S>(d, 3, n, b, p) + (long long)(t - r0) * d.rmax;
 #pragma unroll
       for (int y = 0; y < NO; ++y) {
-        acc[x * NO + y] -= wide(lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 1), U, rk));
+        ka[x * NO + y].add(-lr_dot_conj<R, S>(Psrc<NO, R>(d, n, b, p, y, 1), U, rk));
       }
     }
   }
 #pragma unroll
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] += ka[q].get();
   for (int q = 0; q < NO2; ++q) acc[q] = acc[q] * d.h;
   for (int a = 0; a < d.r; ++a) {  // -i sum_a Sigma^tv(t, tau_a) v_a
     const double2* sv = tv<NO>(d.STV, d, n, t, a);
@@ -267,6 +294,7 @@ __global__ void k_src_h(Dev d, int T) {
   zd acc[NO2];
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
+  KAcc<R> ka[NO2];   // the history sums: compensated FP32 in the complex64 form
   const int jt = t / L, A = jt * L, E = min(A + L, d.nt);
   // pa[x][y] += wl sum_z Sx[x][z] conj(G^R(T,l)[y][z]), Sx = S or S^dagger (in R)
   auto sg = [&](cx<R>* pa, const S* sp, bool dagS, const S* gp, R wl) {
@@ -281,7 +309,7 @@ __global__ void k_src_h(Dev d, int T) {
   };
   auto fold = [&](cx<R>* pa) {
 #pragma unroll
-    for (int q = 0; q < NO2; ++q) { acc[q] += wide(pa[q]); pa[q] = cx<R>(0); }
+    for (int q = 0; q < NO2; ++q) { ka[q].add(pa[q]); pa[q] = cx<R>(0); }
   };
   cx<R> pa[NO2];
 #pragma unroll
@@ -308,7 +336,7 @@ __global__ void k_src_h(Dev d, int T) {
         const cx<R>* P = Psrc<NO, R>(d, n, b, p, y, 0);
         cx<R> sb = cx<R>(0);
         for (int q = lane; q < rk; q += 32) sb = cfma(P[q], ldr<R>(V + q).conj(), sb);
-        acc[x * NO + y] += wide(sb);
+        ka[x * NO + y].add(sb);
       }
     }
   }
@@ -340,11 +368,13 @@ __global__ void k_src_h(Dev d, int T) {
           const cx<R>* P = Psrc<NO, R>(d, n, b, p, y, 1);
           cx<R> sb = cx<R>(0);
           for (int q = lane; q < rk; q += 32) sb = cfma(ldr<R>(U + q).conj(), P[q], sb);
-          acc[x * NO + y] -= wide(sb);
+          ka[x * NO + y].add(-sb);
         }
       }
     }
   }
+#pragma unroll
+  for (int q = 0; q < NO2; ++q) acc[q] += ka[q].get();
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = acc[q] * h;
   for (int a = lane; a < d.r; a += 32) {
@@ -746,8 +776,11 @@ __global__ void k_density_at(Dev d, int t, double2* out) {
 
 // ---------------------------------------------------------------------------
 // 2D Hubbard lattice, second Born (Sec. 4.2), N_o = 1, one instance per
-// k = 2 pi (m_x, m_y)/L (instance m_x L + m_y).  One CTA per time t of the
-// current row (and per DLR node for the mixed row); thread q owns k-point q
+// k = 2 pi (m_x, m_y)/L (instance m_x L + m_y), or, with the reflection
+// k_y -> -k_y of a drive along x (Sec. 4.2, the L(L/2+1) k-set), one
+// instance per m_y <= L/2 (instance m_x (L/2+1) + m_y; k-point (m_x, L - m_y)
+// reads instance (m_x, m_y)).  One CTA per time t of the current row (and
+// per DLR node for the mixed row); thread q owns grid point q = m_x L + m_y
 // and real-space point r = (q / L, q % L):
 //   X_r = (1/N_k) sum_k e^{+i k.r} X_k,  Y_{-r} = (1/N_k) sum_k e^{-i k.r} Y_k,
 //   Sigma^>_r = U(T)U(t) G^>_r(T,t)^2 G^<_{-r}(t,T),
@@ -757,6 +790,14 @@ __global__ void k_density_at(Dev d, int t, double2* out) {
 // The 2D transforms are done as two passes of L-point sums (rows, columns).
 // ---------------------------------------------------------------------------
 constexpr int kLatMaxK = 256;
+// instance holding grid point q = m_x L + m_y (ys: reflection-reduced k-set)
+__device__ __forceinline__ int lat_inst(int q, int L, int ys) {
+  if (!ys) return q;
+  const int y = q % L;
+  return (q / L) * (L / 2 + 1) + min(y, L - y);
+}
+// grid point q is the instance's own k-point (not a reflected copy)
+__device__ __forceinline__ bool lat_owner(int q, int L, int ys) { return !ys || q % L <= L / 2; }
 // in-place 2D DFT of a[N] (N = L*L, index m_x L + m_y) with sign sg (+1: e^{+i}),
 // scaled by sc; tw[m] = e^{2 pi i m / L}; every thread of the CTA must call it
 __device__ void lat_dft2(zd* a, zd* tmp, const zd* tw, int L, int sg, double sc) {
@@ -785,7 +826,8 @@ __device__ void lat_dft2(zd* a, zd* tmp, const zd* tw, int L, int sg, double sc)
 template <typename S>
 __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
   __shared__ zd X1[kLatMaxK], X2[kLatMaxK], Y1[kLatMaxK], Y2[kLatMaxK], tmp[kLatMaxK], tw[16];
-  const int L = (int)d.mpar[0], N = L * L, q = threadIdx.x;
+  const int L = (int)d.mpar[0], ys = (int)d.mpar[1], N = L * L, q = threadIdx.x;
+  const int nq = lat_inst(q, L, ys);
   if (q < L) {
     double sn, cs;
     sincospi(2.0 * q / L, &sn, &cs);
@@ -798,8 +840,8 @@ __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
   if (b <= T) {
     const int t = b;
     if (q < N) {
-      const zd gr = ldx<1, S>(d, 0, q, T, t, 0);
-      const zd glc = ldx<1, S>(d, 1, q, T, t, 0);         // G^<(t, T)
+      const zd gr = ldx<1, S>(d, 0, nq, T, t, 0);
+      const zd glc = ldx<1, S>(d, 1, nq, T, t, 0);        // G^<(t, T)
       const zd glr = -glc.conj();                         // G^<(T, t)
       const zd ggr = gr + glr;                            // G^>(T, t)
       X1[q] = ggr; X2[q] = glr; Y1[q] = glc; Y2[q] = -ggr.conj();
@@ -817,16 +859,16 @@ __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
     __syncthreads();
     lat_dft2(X1, tmp, tw, L, -1, 1.0);
     lat_dft2(X2, tmp, tw, L, -1, 1.0);
-    if (q < N) {
-      stx<1, S>(d, 2, q, T, t, 0, X1[q] - X2[q]);
-      stx<1, S>(d, 3, q, T, t, 0, -X2[q].conj());
+    if (q < N && lat_owner(q, L, ys)) {
+      stx<1, S>(d, 2, nq, T, t, 0, X1[q] - X2[q]);
+      stx<1, S>(d, 3, nq, T, t, 0, -X2[q].conj());
     }
   } else {
     const int i = b - (T + 1), r = d.r;
     if (q < N) {
-      X1[q] = ld(tv<1>(d.GTV, d, q, T, i));
+      X1[q] = ld(tv<1>(d.GTV, d, nq, T, i));
       zd gb = zd();                                        // G^tv(T, beta - tau_i)
-      for (int c = 0; c < r; ++c) gb += ld(tv<1>(d.GTV, d, q, T, c)) * d.rev[i * r + c];
+      for (int c = 0; c < r; ++c) gb += ld(tv<1>(d.GTV, d, nq, T, c)) * d.rev[i * r + c];
       Y1[q] = gb.conj() * (-(double)d.xi);                 // G^vt(tau_i, T)
     }
     __syncthreads();
@@ -835,20 +877,22 @@ __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
     if (q < N) X1[q] = X1[q] * X1[q] * Y1[q] * (U[T + 1] * U[0]);
     __syncthreads();
     lat_dft2(X1, tmp, tw, L, -1, 1.0);
-    if (q < N) st(tv<1>(d.STV, d, q, T, i), X1[q]);
+    if (q < N && lat_owner(q, L, ys)) st(tv<1>(d.STV, d, nq, T, i), X1[q]);
   }
 }
 
 // Lattice observables at time t (Sec. 4.2): n = -(i/N) sum_k G^<_k(t,t),
 // E_kin = -(2i/N) sum_k eps_k G^<_k(t,t), eps_k = -2(cos k_x + cos k_y),
-// j = -(2i/N) sum_k 2 sin(k_x - A(t)) G^<_k(t,t); out = (n, E_kin, j).
+// j = -(2i/N) sum_k 2 sin(k_x - A(t)) G^<_k(t,t); out = (n, E_kin, j).  The
+// sums run over the whole L x L grid (a reflected k-point reads its mirror).
 template <typename S>
 __global__ void __launch_bounds__(kLatMaxK) k_lattice_obs(Dev d, int t, double* out) {
   __shared__ double red[3][kLatMaxK];
-  const int L = (int)d.mpar[0], N = L * L, q = threadIdx.x;
+  const int L = (int)d.mpar[0], ys = (int)d.mpar[1], N = L * L, q = threadIdx.x;
   double v[3] = {0, 0, 0};
   if (q < N) {
-    const S* p = (!d.ring || t >= d.cdir) ? el<1, S>(d.GL, d, q, t, t) : Lf<1, S>(d, 1, q, t / d.L, t, t);
+    const int nq = lat_inst(q, L, ys);
+    const S* p = (!d.ring || t >= d.cdir) ? el<1, S>(d.GL, d, nq, t, t) : Lf<1, S>(d, 1, nq, t / d.L, t, t);
     const double mi = (-ld(p) * zd(0, 1)).re;            // Re(-i G^<(t,t))
     const double kx = 2.0 * M_PI * (q / L) / L, ky = 2.0 * M_PI * (q % L) / L;
     const double A = d.drA[t + 1];

@@ -47,10 +47,15 @@ struct Row64<NO, double2> {
   __device__ static Y* get(const Dev&, int, int, int, double2* p) { return p; }
 };
 
-// Inverse of frozen chunk cc of sweep `which`: complex128 in both storage
-// forms (it solves the implicit part of the Volterra equation; a complex64
-// inverse would put a relative error of order 2^-24 times the BDF amplitude
-// a_j / h into every chunk and accumulate along the sweep).
+// Inverse of frozen chunk cc of sweep `which`, (32 N_o)^2 entries.  FP64
+// storage form: complex128.  Complex64 form: the same 16 bytes per entry
+// hold a complex64 pair hi + lo (hi = the inverse rounded to complex64, lo =
+// the rounding of hi), [hi matrix][lo matrix].  The chunk's right-hand side
+// splits into the far field (history sums, lesser source), whose image under
+// the inverse is about h / a_0 times smaller than the row and needs FP32 only,
+// and the BDF terms reaching across the chunk edge (k rows), which carry the
+// implicit recursion and get hi + lo in FP64; a plain complex64 inverse would
+// put 2^-24 times the BDF amplitude a_j / h into every chunk and accumulate.
 template <int NO>
 __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which) {
   const long long nn = (long long)(CK * NO) * (CK * NO);
@@ -99,6 +104,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
   __shared__ zd FB[64][NO];
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
+  __shared__ zd Fb[CK][NO];      // the BDF part of Fs (rows at the chunk edge; zero elsewhere)
   __shared__ double serr;
   extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
                                  // entry (staged != 0) the block projections [maxl][NO2][rmax]
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
           const int m = p / NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
           const S* U = Up<NO, S>(d, 2, n, blk, p);
-          zd part[4] = {zd(), zd(), zd(), zd()};
+          KAcc<R> part[4];
           for (int s0 = r0 + warp; s0 < rl; s0 += 8 * FOLD) {  // warps over rows, lanes over rank
             cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
 #pragma unroll
@@ -182,10 +188,10 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
               }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
+            for (int u = 0; u < 4; ++u) part[u].add(pp[u]);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u].get();
           __syncthreads();
           if (tid < d.rmax) {
             zd acc = zd();
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
         zd acc[NO];
 #pragma unroll
         for (int j = 0; j < NO; ++j) acc[j] = zd();
+        KAcc<R> ka[NO];   // FP32 history sums, compensated (FP64 in the FP64 form)
         const int tp = A + col;
         if (col < L) {
           for (int s0 = c + sl; s0 <= T; s0 += 4 * FOLD) {
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
               }
             }
 #pragma unroll
-            for (int j = 0; j < NO; ++j) acc[j] += wide(pa[j]);
+            for (int j = 0; j < NO; ++j) ka[j].add(pa[j]);
           }
           for (int lv = 0; lv < d.maxl; ++lv) {
             const int blk = d.colblk[jl * d.maxl + lv];
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
                 const double2* P = Pj<NO>(d, n, irow, lv, p);
                 for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(P + q), ldr<R>(V + q).conj(), pb);
               }
-              acc[j] += wide(pb);
+              ka[j].add(pb);
             }
           }
           for (int s2 = E + sl; s2 <= tp + k && s2 < c; s2 += 4) {
@@ -272,6 +279,8 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
             }
           }
         }
+#pragma unroll
+        for (int j = 0; j < NO; ++j) acc[j] += ka[j].get();
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
           acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, 1), __shfl_xor_sync(FULL, acc[j].im, 1));
@@ -290,6 +299,7 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
       zd acc[NO];
 #pragma unroll
       for (int j = 0; j < NO; ++j) acc[j] = zd();
+        KAcc<R> ka[NO];   // FP32 history sums, compensated (FP64 in the FP64 form)
       if (col < cn) {
         const int s_end = comp ? E : T + 1;   // compressed: the rest of the leaf; else every later row
         for (int s0 = b + sl; s0 < s_end; s0 += 8 * FOLD) {
@@ -312,9 +322,11 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
             }
           }
 #pragma unroll
-          for (int j = 0; j < NO; ++j) acc[j] += wide(pa[j]);
+          for (int j = 0; j < NO; ++j) ka[j].add(pa[j]);
         }
       }
+#pragma unroll
+        for (int j = 0; j < NO; ++j) acc[j] += ka[j].get();
 #pragma unroll
       for (int j = 0; j < NO; ++j)
 #pragma unroll
@@ -322,17 +334,24 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
           acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, off), __shfl_xor_sync(FULL, acc[j].im, off));
       if (sl == 0 && col < cn) {
         zd F[NO];
+        zd Fbd[NO];
 #pragma unroll
-        for (int j = 0; j < NO; ++j) F[j] = (acc[j] + (comp ? FB[tp - A][j] : zd())) * h;
+        for (int j = 0; j < NO; ++j) {
+          F[j] = (acc[j] + (comp ? FB[tp - A][j] : zd())) * h;
+          Fbd[j] = zd();
+        }
         for (int jj = 1; jj <= k; ++jj) {  // BDF terms reaching above the chunk
           const int s2 = tp + jj;
           if (s2 < b) continue;
           const zd cf(0, -W.a[jj] / h);
 #pragma unroll
-          for (int m = 0; m < NO; ++m) F[m] += cf * ld(yp(s2) + m);
+          for (int m = 0; m < NO; ++m) Fbd[m] += cf * ld(yp(s2) + m);
         }
 #pragma unroll
-        for (int j = 0; j < NO; ++j) Fs[col][j] = F[j];
+        for (int j = 0; j < NO; ++j) {
+          Fs[col][j] = F[j] + Fbd[j];
+          Fb[col][j] = Fbd[j];
+        }
       }
     }
     __syncthreads();
@@ -344,9 +363,29 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
       for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
         const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, j = o % NO;
         zd sacc = zd();
-        for (int si = sl; si < CK; si += 8)
+        if constexpr (Row64<NO, S>::separate) {
+          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in FP64
+          const float2* Mh = reinterpret_cast<const float2*>(Mi);
+          const float2* Ml = Mh + LD * LD;
+          zf s32 = zf(0);
+          for (int si = sl; si < CK; si += 8)
 #pragma unroll
-          for (int m = 0; m < NO; ++m) sacc = cfma(Fs[si][m], ld(Mi + (long long)(si * NO + m) * LD + ti * NO + j), sacc);
+            for (int m = 0; m < NO; ++m) {
+              const zd ff = Fs[si][m] - Fb[si][m];
+              s32 = cfma(zf((float)ff.re, (float)ff.im), ldr<float>(Mh + (long long)(si * NO + m) * LD + ti * NO + j), s32);
+            }
+          sacc = wide(s32);
+          for (int si = CK - k + sl; si < CK; si += 8)
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              const long long e = (long long)(si * NO + m) * LD + ti * NO + j;
+              sacc = cfma(Fb[si][m], ld(Mh + e) + ld(Ml + e), sacc);
+            }
+        } else {
+          for (int si = sl; si < CK; si += 8)
+#pragma unroll
+            for (int m = 0; m < NO; ++m) sacc = cfma(Fs[si][m], ld(Mi + (long long)(si * NO + m) * LD + ti * NO + j), sacc);
+        }
 #pragma unroll
         for (int off = 1; off < 8; off <<= 1)
           sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
@@ -462,6 +501,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
   __shared__ zd FB[64][NO];
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
+  __shared__ zd Fb[CK][NO];      // the BDF part of Fs (rows at the chunk edge; zero elsewhere)
   __shared__ double serr;
   extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
                                  // entry (staged != 0) the block projections [maxl][NO2][rmax]
@@ -498,7 +538,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
           const int nn = p % NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
           const S* V = Vp<NO, S>(d, 2, n, blk, p);
-          zd part[4] = {zd(), zd(), zd(), zd()};
+          KAcc<R> part[4];
           for (int l0 = c0 + warp; l0 < c1; l0 += 8 * FOLD) {  // warps over columns, lanes over rank
             cx<R> pp[4] = {cx<R>(0), cx<R>(0), cx<R>(0), cx<R>(0)};
 #pragma unroll
@@ -516,10 +556,10 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
               }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) part[u] += wide(pp[u]);
+            for (int u = 0; u < 4; ++u) part[u].add(pp[u]);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u];
+          for (int u = 0; u < 4; ++u) pbuf[warp][lane + 32 * u] = part[u].get();
           __syncthreads();
           if (tid < d.rmax) {
             zd acc = zd();
@@ -550,6 +590,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
         zd acc[NO];
 #pragma unroll
         for (int m = 0; m < NO; ++m) acc[m] = zd();
+        KAcc<R> ka[NO];   // FP32 history sums, compensated (FP64 in the FP64 form)
         if (row < L) {
           for (int lv = 0; lv < d.maxl; ++lv) {
             const int blk = d.rowblk[jl * d.maxl + lv];
@@ -567,7 +608,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
                 const double2* P = Pj<NO>(d, n, jc, lv, p);
                 for (int q = sl; q < rk; q += 4) pb = cfma(ldr<R>(U + q), ldr<R>(P + q), pb);
               }
-              acc[m] += wide(pb);
+              ka[m].add(pb);
             }
           }
           for (int l = max(t - k, 0) + sl; l < A; l += 4) {
@@ -581,6 +622,8 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
             }
           }
         }
+#pragma unroll
+        for (int m = 0; m < NO; ++m) acc[m] += ka[m].get();
 #pragma unroll
         for (int m = 0; m < NO; ++m) {
           acc[m] += zd(__shfl_xor_sync(FULL, acc[m].re, 1), __shfl_xor_sync(FULL, acc[m].im, 1));
@@ -599,17 +642,26 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
       zd acc[NO];
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[m] = zd();
+        KAcc<R> ka[NO];   // FP32 history sums, compensated (FP64 in the FP64 form)
       if (row < cn) {
         if (t <= k) {
-          if (sl == 0) {  // start rows: only l = 0 lies left of chunk 0
+          if (sl == 0) {  // start rows: only l = 0 lies left of chunk 0 (a derivative term: kept in Fb)
+            zd fb[NO];
+#pragma unroll
+            for (int m = 0; m < NO; ++m) fb[m] = zd();
             for (int y = 0; y < NO; ++y) {
               const zd xv = ld(xp(0) + y * NO + jc);
 #pragma unroll
               for (int m = 0; m < NO; ++m) {
                 zd cf = srx_any<NO, S>(d, n, t, 0, m, y) * (-h * W.I0[t][0]);
                 if (m == y) cf += zd(0, W.D[t][0] / h);
-                acc[m] -= cf * xv;
+                fb[m] -= cf * xv;
               }
+            }
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              acc[m] += fb[m];
+              Fb[row][m] = fb[m];
             }
           }
         } else {
@@ -635,18 +687,28 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
               }
             }
 #pragma unroll
-            for (int m = 0; m < NO; ++m) acc[m] += wide(pa[m]);
+            for (int m = 0; m < NO; ++m) ka[m].add(pa[m]);
           }
-          if (sl == 1) {  // BDF terms reaching left of the chunk
+          if (sl == 1) {  // BDF terms reaching left of the chunk, kept apart in Fb
+            zd fb[NO];
+#pragma unroll
+            for (int m = 0; m < NO; ++m) fb[m] = zd();
             for (int jj = 1; jj <= k; ++jj) {
               if (t - jj >= a) continue;
               const zd cf(0, -W.a[jj] / h);
 #pragma unroll
-              for (int m = 0; m < NO; ++m) acc[m] += cf * ld(xp(t - jj) + m * NO + jc);
+              for (int m = 0; m < NO; ++m) fb[m] += cf * ld(xp(t - jj) + m * NO + jc);
+            }
+#pragma unroll
+            for (int m = 0; m < NO; ++m) {
+              acc[m] += fb[m];
+              Fb[row][m] = fb[m];
             }
           }
         }
       }
+#pragma unroll
+        for (int m = 0; m < NO; ++m) acc[m] += ka[m].get();
 #pragma unroll
       for (int m = 0; m < NO; ++m)
 #pragma unroll
@@ -665,10 +727,31 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
       for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
         const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, m = o % NO;
         zd sacc = zd();
-        if (ti < cn)
+        if constexpr (Row64<NO, S>::separate) {
+          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in FP64
+          const float2* Mh = reinterpret_cast<const float2*>(Mi);
+          const float2* Ml = Mh + LD * LD;
+          if (ti < cn) {
+            zf s32 = zf(0);
+            for (int li = sl; li < cn; li += 8)
+#pragma unroll
+              for (int y = 0; y < NO; ++y) {
+                const zd ff = Fs[li][y] - (li < k ? Fb[li][y] : zd());
+                s32 = cfma(ldr<float>(Mh + (long long)(ti * NO + m) * LD + li * NO + y), zf((float)ff.re, (float)ff.im), s32);
+              }
+            sacc = wide(s32);
+            for (int li = sl; li < k && li < cn; li += 8)
+#pragma unroll
+              for (int y = 0; y < NO; ++y) {
+                const long long e = (long long)(ti * NO + m) * LD + li * NO + y;
+                sacc = cfma(ld(Mh + e) + ld(Ml + e), Fb[li][y], sacc);
+              }
+          }
+        } else if (ti < cn) {
           for (int li = sl; li < cn; li += 8)
 #pragma unroll
             for (int y = 0; y < NO; ++y) sacc = cfma(ld(Mi + (long long)(ti * NO + m) * LD + li * NO + y), Fs[li][y], sacc);
+        }
 #pragma unroll
         for (int off = 1; off < 8; off <<= 1)
           sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
@@ -906,7 +989,15 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
   }
   for (int e = tid; e < nn * nn; e += blockDim.x) {
     const int r = e / nn, col = e % nn;
-    st(Bout + (long long)r * LD + col, ld(B + (long long)r * LD + col));
+    const zd v = ld(B + (long long)r * LD + col);
+    if constexpr (sizeof(S) == sizeof(float2)) {   // complex64 form: hi and lo matrices (see Cinv)
+      float2* Oh = reinterpret_cast<float2*>(Bout);
+      const float2 hi = make_float2((float)v.re, (float)v.im);
+      Oh[(long long)r * LD + col] = hi;
+      Oh[(long long)LD * LD + (long long)r * LD + col] = make_float2((float)(v.re - (double)hi.x), (float)(v.im - (double)hi.y));
+    } else {
+      st(Bout + (long long)r * LD + col, v);
+    }
   }
 }
 
@@ -923,10 +1014,15 @@ __global__ void __launch_bounds__(256) k_chunk_inv(Dev d, int which, int cc, dou
     default: return cudaErrorInvalidValue;                                      \
   }
 
-// Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
+// Static plus dynamic shared memory above the 48 KB default needs an opt-in
+// per kernel (the static arrays of the sweeps take 24-31 KB).
 template <typename K>
 static cudaError_t allow_smem(K kern, size_t bytes) {
-  if (bytes + 16 * 1024 <= 48 * 1024) return cudaSuccess;  // with the static arrays, under the default
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  if (a.sharedSizeBytes + bytes <= 48 * 1024) return cudaSuccess;
+  if (a.sharedSizeBytes + bytes > 227 * 1024) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 // Dynamic shared memory of a sweep: the hot-chunk coefficients (N_o <= 2)

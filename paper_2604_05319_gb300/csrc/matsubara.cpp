@@ -183,10 +183,11 @@ extern "C" int hkbe_matsubara_solve(int r, const double* tau, const double* omeg
       model != HKBE_MODEL_LATTICE2B)
     return HKBE_ERR_ARG;
   if (model != HKBE_MODEL_NONE && (!params || nparams < 1)) return HKBE_ERR_ARG;
-  int L = 0;
-  if (model == HKBE_MODEL_LATTICE2B) {
+  int L = 0, ys = 0;
+  if (model == HKBE_MODEL_LATTICE2B) {   // params [L] or [L, ysymm] (reflection-reduced k-set)
     L = (int)params[0];
-    if (L < 1 || L > 16 || L * L != n_inst) return HKBE_ERR_ARG;
+    ys = nparams >= 2 && params[1] != 0.0;
+    if (L < 1 || L > 16 || (ys && L % 2) || (ys ? L * (L / 2 + 1) : L * L) != n_inst) return HKBE_ERR_ARG;
   }
   Solver sv;
   if (!sv.init(r, tau, omega, beta, nao)) return HKBE_ERR_ARG;
@@ -226,9 +227,12 @@ extern "C" int hkbe_matsubara_solve(int r, const double* tau, const double* omeg
         }
       }
     } else if (model == HKBE_MODEL_LATTICE2B) {
-      const int N = n_inst;
-      std::vector<zc> gr((size_t)N * r), gmr((size_t)N * r), sr((size_t)N * r), gmk((size_t)N * r), tmp(r);
-      for (int q = 0; q < N; ++q) {   // G_k(-tau)
+      // grid point q = m_x L + m_y lives in instance kin(q); with ysymm the
+      // point (m_x, L - m_y) is the mirror of (m_x, m_y) and shares its instance
+      const int N = L * L;
+      auto kin = [&](int q) { const int y = q % L; return ys ? (q / L) * (L / 2 + 1) + std::min(y, L - y) : q; };
+      std::vector<zc> gr((size_t)N * r), gmr((size_t)N * r), sr((size_t)N * r), gmk((size_t)n_inst * r), tmp(r);
+      for (int q = 0; q < n_inst; ++q) {   // G_k(-tau)
         sv.reversed(&Gx[(size_t)q * r], tmp.data());
         for (int i = 0; i < r; ++i) gmk[(size_t)q * r + i] = (double)sv.xi * tmp[i];
       }
@@ -236,12 +240,12 @@ extern "C" int hkbe_matsubara_solve(int r, const double* tau, const double* omeg
       for (int rr = 0; rr < N; ++rr) {
         const int rx = rr / L, ry = rr % L;
         for (int q = 0; q < N; ++q) {
-          const int mx = q / L, my = q % L;
+          const int mx = q / L, my = q % L, nq = kin(q);
           const double ph = 2.0 * M_PI * (double)(mx * rx + my * ry) / L;
           const zc e(std::cos(ph), std::sin(ph));
           for (int i = 0; i < r; ++i) {
-            gr[(size_t)rr * r + i] += e * Gx[(size_t)q * r + i] / (double)N;
-            gmr[(size_t)rr * r + i] += std::conj(e) * gmk[(size_t)q * r + i] / (double)N;
+            gr[(size_t)rr * r + i] += e * Gx[(size_t)nq * r + i] / (double)N;
+            gmr[(size_t)rr * r + i] += std::conj(e) * gmk[(size_t)nq * r + i] / (double)N;
           }
         }
         for (int i = 0; i < r; ++i)
@@ -249,11 +253,12 @@ extern "C" int hkbe_matsubara_solve(int r, const double* tau, const double* omeg
       }
       for (int q = 0; q < N; ++q) {    // Sigma_k = sum_r e^{-ikr} Sigma_r
         const int mx = q / L, my = q % L;
+        if (ys && my > L / 2) continue;   // a mirror point: its instance is filled by (m_x, L - m_y)
         for (int rr = 0; rr < N; ++rr) {
           const int rx = rr / L, ry = rr % L;
           const double ph = 2.0 * M_PI * (double)(mx * rx + my * ry) / L;
           const zc e(std::cos(ph), -std::sin(ph));
-          for (int i = 0; i < r; ++i) Sx[(size_t)q * r + i] += e * sr[(size_t)rr * r + i];
+          for (int i = 0; i < r; ++i) Sx[(size_t)kin(q) * r + i] += e * sr[(size_t)rr * r + i];
         }
       }
     }

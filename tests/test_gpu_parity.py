@@ -144,3 +144,37 @@ def test_range_and_order_errors():
     assert e.value.code == -4
     with pytest.raises(pk.HKBEError):
         pk.hkbe_get_ret(st.h, 1, 0, 5, 6)
+
+
+@pytest.mark.parametrize("no,prec", [(3, pk.PREC_FP64), (4, pk.PREC_FP64), (3, pk.PREC_MIXED), (4, pk.PREC_MIXED)])
+def test_bath_three_and_four_orbitals_compressed(no, prec):
+    """N_o = 3 and 4 in the compressed form (leaf 32, four leaves compressed,
+    blocks on two levels), FP64 (eps_SVD 1e-10, bound 1e-9 absolute) and
+    complex64 (eps_SVD 1e-8, bound 1e-6 of max |G| plus 10 eps_SVD), with a
+    driven level matrix eps(t) = eps_d + 0.2 sin(1.3 t) (C5's larger groups)."""
+    nt, h, k = 140, 0.05, 5
+    rng = np.random.default_rng(no)
+    A = rng.normal(size=(no, no)) + 1j * rng.normal(size=(no, no))
+    eps_d = 0.3 * (A + A.conj().T)
+    V = 0.3 * (rng.normal(size=(no, 2)) + 1j * rng.normal(size=(no, 2)))
+    eb = np.array([0.5, -0.6])
+    H = np.block([[eps_d, V], [V.conj().T, np.diag(eb)]])
+    E, U = np.linalg.eigh(H)
+    gm = -np.einsum("xa,ia,ya->ixy", U[:no], wk._lehmann_kernel_unit(TAU / BETA, E * BETA), U[:no].conj())
+    tt = np.concatenate([[0.0], np.arange(nt) * h])
+    eps = eps_d[None] + (0.2 * np.sin(1.3 * tt) * (np.arange(nt + 1) > 0))[:, None, None] * np.eye(no)[None]
+    o = KBEOracle(nt, h, k, BETA, eps, gm, TAU, OM, make_model("bath", {"V": V, "eb": eb}), tol=1e-14)
+    o.run()
+    svd_tol = 1e-10 if prec == pk.PREC_FP64 else 1e-8
+    st = pk.Stepper(nt, h, k, BETA, nao=no, n_inst=1, tol=1e-13 if prec == pk.PREC_FP64 else 1e-7, max_iter=60,
+                    precision=prec, svd_tol=svd_tol, leaf=32, r_max=64)
+    st.set_inputs(TAU, OM, gm[None], eps[None].astype(complex), pk.MODEL_BATH, _bath_params(V, eb)[None])
+    st.run()
+    GR, GL, GTV = st.dense(0)
+    idx = np.tril_indices(nt)
+    ref = max(np.abs(o.GR[idx]).max(), np.abs(o.GLs[idx]).max())
+    err = max(np.abs(GR[idx] - o.GR[idx]).max(), np.abs(GL[idx] - o.GLs[idx]).max(), np.abs(GTV - o.GTV).max())
+    assert pk.hkbe_get_ranks(st.h, 0, 2, len(pk.hkbe_get_blocks(st.h)["r0"]), no)[1] >= 96
+    bound = 1e-9 if prec == pk.PREC_FP64 else 1e-6 * ref + 10 * svd_tol
+    print(f"N_o = {no}, {'FP64' if prec == pk.PREC_FP64 else 'complex64'} compressed: max error {err:.2e}")
+    assert err < bound, err

@@ -70,6 +70,24 @@ def test_lattice_matches_oracle():
     assert np.abs(G - Go).max() < 1e-9
 
 
+def test_lattice_reflection_reduced_set_matches_oracle():
+    """The reflection-reduced k-set (m_y <= L/2, L(L/2+1) instances, Sec. 4.2)
+    gives the oracle's full-grid G^M_k at its k-points: the mirror points
+    enter the lattice sums through their instance."""
+    beta, L = 4.0, 4
+    tau, om = wk.dlr_grid(60.0, 1e-12, beta)
+    mo = MatsubaraOracle(tau, om, beta)
+    m = np.arange(L) * 2 * np.pi / L
+    ek = (-2 * (np.cos(np.repeat(m, L)) + np.cos(np.tile(m, L))))[:, None, None].astype(complex)
+    Go, _, _, _ = mo.solve("lattice2b", ek, {"L": L, "U": 1.5}, tol=1e-13, mix=0.6)
+    red = [x * L + y for x in range(L) for y in range(L // 2 + 1)]
+    G, _, _, _ = pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_LATTICE2B, ek[red], [[L, 1]] * len(red),
+                                         U_eq=1.5, mix=0.6, tol=1e-13)
+    assert np.abs(G - Go[red]).max() < 1e-9
+    with pytest.raises(pk.HKBEError):      # the reduced set has L(L/2+1) points
+        pk.hkbe_matsubara_solve(tau, om, beta, pk.MODEL_LATTICE2B, ek, [[L, 1]] * (L * L))
+
+
 def test_errors(grid5):
     beta, tau, om, _ = grid5
     with pytest.raises(pk.HKBEError):      # Nambu needs two orbitals
