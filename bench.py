@@ -583,6 +583,52 @@ def run_scaling(args, pk, torch):
     print(json.dumps(out))
 
 
+def run_matsubara_study(args, pk, torch):
+    """Equilibrium Dyson solve on the device (hkbe_solve_matsubara) against
+    the library's host solver (hkbe_matsubara_solve) on the initial states of
+    C3 (16 x 16 lattice, U = 2, beta = 10; full and reflection-reduced k-set)
+    and of the C4 batch (128 Nambu instances with the Holstein term, beta =
+    50, DLR Lambda = 200): wall time of each (the device one includes its
+    per-iteration convergence read-back), iterations, max |G_dev - G_host|."""
+    out = {"study": "matsubara", "cases": []}
+
+    def case(name, tau, om, beta, eps0, model, params, U, nao, n_inst):
+        t0 = time.perf_counter()
+        Gh, _, ith, _ = pk.hkbe_matsubara_solve(tau, om, beta, model, eps0, params, U_eq=U, mix=0.5, tol=1e-12,
+                                                max_iter=2000)
+        t_host = time.perf_counter() - t0
+        st = pk.Stepper(16, 0.02, 5, beta, nao=nao, n_inst=n_inst, tol=1e-12, max_iter=80)
+        eps = np.broadcast_to(eps0[:, None], (n_inst, 17, nao, nao)).astype(complex)
+        st.set_inputs(tau, om, None, eps, model, params)
+        pk.hkbe_solve_matsubara(st.h, n_inst, len(tau), nao, U_eq=U, mix=0.5, tol=1e-12, max_iter=2000)  # warm-up
+        torch.cuda.synchronize()
+        st.close()
+        st = pk.Stepper(16, 0.02, 5, beta, nao=nao, n_inst=n_inst, tol=1e-12, max_iter=80)
+        st.set_inputs(tau, om, None, eps, model, params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gd, itd, _ = pk.hkbe_solve_matsubara(st.h, n_inst, len(tau), nao, U_eq=U, mix=0.5, tol=1e-12, max_iter=2000)
+        t_dev = time.perf_counter() - t0
+        st.close()
+        out["cases"].append({"case": name, "n_inst": n_inst, "r": len(tau), "host_s": round(t_host, 4),
+                             "device_s": round(t_dev, 4), "speedup": round(t_host / t_dev, 1),
+                             "iterations_host": ith, "iterations_device": itd,
+                             "max_abs_diff": float(np.abs(Gd - Gh).max())})
+
+    L = 16
+    tau, om = wk.dlr_grid(100.0, 1e-10, 10.0)
+    m = np.arange(L) * 2 * np.pi / L
+    ek = (-2 * (np.cos(np.repeat(m, L)) + np.cos(np.tile(m, L))))[:, None, None].astype(complex)
+    case("C3 16 x 16 lattice, U = 2", tau, om, 10.0, ek, pk.MODEL_LATTICE2B, np.array([[16.0]] * 256), 2.0, 1, 256)
+    red = [x * L + y for x in range(L) for y in range(L // 2 + 1)]
+    case("C3 reduced k-set (144)", tau, om, 10.0, ek[red], pk.MODEL_LATTICE2B, np.array([[16.0, 1.0]] * 144), 2.0,
+         1, 144)
+    tau, om = wk.dlr_grid(200.0, 1e-10, 50.0)
+    case("C4 batch, Nambu + Holstein (g = 0.5, w0 = 0.6), beta = 50", tau, om, 50.0,
+         np.zeros((128, 2, 2), complex), pk.MODEL_NAMBU, np.array([[1.0, 0.5, 0.6]] * 128), 0.0, 2, 128)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,14 +642,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps per process in cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle corrector iterations per step")
-    ap.add_argument("--study", default=None, choices=["scaling"], help="the scaling study instead of the bench line")
+    ap.add_argument("--study", default=None, choices=["scaling", "matsubara"],
+                    help="a study instead of the bench line: rank/time scaling, or the equilibrium solve")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     wname = "C4" if args.workload == "C4-batch" else args.workload
-    if args.study == "scaling":
+    if args.study:
         import torch
         import paper_2604_05319_gb300 as pk
-        return run_scaling(args, pk, torch)
+        return (run_scaling if args.study == "scaling" else run_matsubara_study)(args, pk, torch)
     if wname == "C5":
         import torch
         import paper_2604_05319_gb300 as pk

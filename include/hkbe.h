@@ -137,6 +137,25 @@ int hkbe_matsubara_solve(int r, const double* tau, const double* omega, double b
                          int n_eta, double mix, double tol, int max_iter, double* gm_out, double* eps_out,
                          int32_t* iters, double* err);
 
+/* Equilibrium Dyson equation solved on the device (Eq. KBEM, Sec. 2.5, 3.2):
+ * the iteration of hkbe_matsubara_solve (the same Sigma^M functionals, Dyson
+ * at the same r Matsubara frequencies, the same mixing and stopping rule) run
+ * by kernels on h's stream, for h's model (hkbe_set_model: NONE, BETHE, NAMBU
+ * or LATTICE2B, the reduced k-set included), DLR grid (hkbe_set_dlr) and
+ * equilibrium-branch level eps(0_|) (index 0 of hkbe_set_hamiltonian; NAMBU
+ * adds the Fock term itself).  The converged G^M is installed as by
+ * hkbe_set_matsubara, so it replaces that call.  Must precede hkbe_bootstrap.
+ *   U_eq, eta, n_eta, mix, tol, max_iter: as for hkbe_matsubara_solve;
+ *   gm_out (may be NULL): [n_inst][r][nao][nao] complex, the installed G^M;
+ *   iters, err (may be NULL): iterations taken, last max |G_new - G|.
+ * Allocates and frees its own device buffers (about 3 n_inst r nao^2 complex
+ * values and r^3 doubles).  Errors: HKBE_ERR_ARG (order of calls, argument
+ * ranges, BATH model), HKBE_ERR_NAN (singular Dyson matrix or non-finite
+ * iterate; nothing installed), HKBE_ERR_NOCONV (max_iter reached: the last
+ * iterate is installed), HKBE_ERR_CUDA. */
+int hkbe_solve_matsubara(hkbe_t* h, double U_eq, double eta, int n_eta, double mix, double tol, int max_iter,
+                         double* gm_out, int32_t* iters, double* err);
+
 /* Release every device and host resource of h (NULL is accepted). */
 int hkbe_destroy(hkbe_t* h);
 

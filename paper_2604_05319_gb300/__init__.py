@@ -78,6 +78,8 @@ def load(build_if_missing: bool = True):
         "hkbe_matsubara_solve": ([C.c_int, _D, _D, C.c_double, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int,
                                   C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
                                   _I, _D], C.c_int),
+        "hkbe_solve_matsubara": ([H, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D, _I, _D],
+                                 C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_set_initial_slices": ([H, _D, _D, _D], C.c_int),
         "hkbe_get_observables": ([H, C.c_int, _D, _D, _D], C.c_int),
@@ -296,6 +298,19 @@ def hkbe_matsubara_solve(tau, omega, beta, model, eps, params=None, U_eq=0.0, et
     return gm, eo, int(it[0]), float(er[0])
 
 
+def hkbe_solve_matsubara(h, n_inst, r, nao, U_eq=0.0, eta=0.0, n_eta=0, mix=0.5, tol=1e-12, max_iter=500):
+    """Equilibrium G^M of the handle's model solved on the device and
+    installed (replaces hkbe_set_matsubara).  Returns (G^M [n_inst, r, nao,
+    nao], iterations, final difference); raises HKBEError on failure or
+    non-convergence."""
+    gm = np.zeros((n_inst, r, nao, nao), np.complex128)
+    it = np.zeros(1, np.int32)
+    er = np.zeros(1)
+    _check(load().hkbe_solve_matsubara(h, float(U_eq), float(eta), int(n_eta), float(mix), float(tol), int(max_iter),
+                                       _dp(gm.view(np.float64)), _ip(it), _dp(er)), h)
+    return gm, int(it[0]), float(er[0])
+
+
 def hkbe_get_lattice_observables(h, t):
     """(n, E_kin, j) of a LATTICE2B handle at time t."""
     out = np.zeros(3)
@@ -467,9 +482,11 @@ class Stepper:
             pass
 
     def set_inputs(self, tau, omega, gm, eps, model, model_params):
+        """gm None: no G^M is set (hkbe_solve_matsubara installs one)."""
         self.r = len(tau)
         hkbe_set_dlr(self.h, tau, omega)
-        hkbe_set_matsubara(self.h, gm)
+        if gm is not None:
+            hkbe_set_matsubara(self.h, gm)
         hkbe_set_hamiltonian(self.h, eps)
         hkbe_set_model(self.h, model, model_params)
 

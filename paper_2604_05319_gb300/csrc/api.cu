@@ -11,6 +11,7 @@
 #include "../../include/hkbe.h"
 #include "host_numerics.h"
 #include "state.h"
+#include "matsubara_dev.h"
 
 using hk::Dev;
 using zc = std::complex<double>;
@@ -24,6 +25,7 @@ struct hkbe_s {
   std::vector<int> last;   // last time step of each instance (its N_t - 1)
   bool have_dlr = false, have_gm = false, have_eps = false, have_model = false;
   bool self_consistent = true;
+  int lat_L = 0, lat_ys = 0;   // LATTICE2B grid and reduced-set flag
   std::vector<double> tau, om, gm_host, eps_host;
   hk::DLRMats dm;
   int* any_dev = nullptr;
@@ -59,6 +61,22 @@ struct hkbe_s {
 };
 
 namespace {
+// Device buffers owned by one API call, freed when it returns.
+struct CallBufs {
+  std::vector<void*> p;
+  ~CallBufs() {
+    for (void* x : p) cudaFree(x);
+  }
+  template <typename T>
+  cudaError_t get(T** out, size_t n) {
+    void* x = nullptr;
+    cudaError_t e = cudaMalloc(&x, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) p.push_back(x);
+    *out = (T*)x;
+    return e;
+  }
+};
+
 // Launch one phase: counts its kernels and, when profiling, brackets it with
 // events whose elapsed time is collected at the next drain().
 template <typename F>
@@ -488,6 +506,84 @@ int hkbe_set_matsubara(hkbe_t* h, const double* gm) {
   return HKBE_OK;
 }
 
+int hkbe_solve_matsubara(hkbe_t* h, double U_eq, double eta, int n_eta, double mix, double tol, int max_iter,
+                         double* gm_out, int32_t* iters, double* err_out) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (!h->have_dlr || !h->have_eps || !h->have_model)
+    return fail(h, HKBE_ERR_ARG, "hkbe_set_dlr, hkbe_set_hamiltonian and hkbe_set_model must precede hkbe_solve_matsubara");
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "hkbe_solve_matsubara must precede hkbe_bootstrap");
+  if (!(mix > 0.0 && mix <= 1.0) || max_iter < 1 || n_eta < 0 || !std::isfinite(U_eq) || !std::isfinite(eta) ||
+      !(tol >= 0.0))
+    return fail(h, HKBE_ERR_ARG, "mix in (0, 1], max_iter >= 1, n_eta >= 0, finite U_eq and eta, tol >= 0");
+  Dev& d = h->d;
+  hk::MatsDev m{};
+  switch (d.model) {
+    case HKBE_MODEL_NONE: m.model = hk::kMatsNone; break;
+    case HKBE_MODEL_BETHE: m.model = hk::kMatsBethe; break;
+    case HKBE_MODEL_NAMBU: m.model = hk::kMatsNambu; break;
+    case HKBE_MODEL_LATTICE2B: m.model = hk::kMatsLattice; break;
+    default: return fail(h, HKBE_ERR_ARG, "no equilibrium solve for this model (its G^M has a closed form)");
+  }
+  const int r = d.r, n2 = no2(h), N = d.n_inst;
+  std::vector<zc> F, B;
+  std::vector<double> nu;
+  if (!hk::mats_maps(r, h->tau.data(), h->om.data(), h->p.beta, &F, &B, &nu))
+    return fail(h, HKBE_ERR_ARG, "singular DLR kernel matrix");
+  CallBufs bufs;   // buffers of this call only (an initialisation step, not the per-step path)
+  double2 *dF, *dB, *G, *Gn, *S;
+  double *dnu, *dphi, *derr;
+  const size_t per = (size_t)N * r * n2;
+  HK_CUDA(h, bufs.get(&dF, (size_t)r * r));
+  HK_CUDA(h, bufs.get(&dB, (size_t)r * r));
+  HK_CUDA(h, bufs.get(&dnu, r));
+  HK_CUDA(h, bufs.get(&dphi, (size_t)r * r * r));
+  HK_CUDA(h, bufs.get(&derr, N));
+  HK_CUDA(h, bufs.get(&G, per));
+  HK_CUDA(h, bufs.get(&Gn, per));
+  HK_CUDA(h, bufs.get(&S, per));
+  HK_CUDA(h, cudaMemcpyAsync(dF, F.data(), F.size() * sizeof(double2), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(dB, B.data(), B.size() * sizeof(double2), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(dnu, nu.data(), r * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  HK_CUDA(h, cudaMemcpyAsync(dphi, h->dm.phi.data(), h->dm.phi.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             h->s));
+  HK_CUDA(h, cudaMemsetAsync(S, 0, per * sizeof(double2), h->s));
+  m.r = r; m.no = d.no; m.n_inst = N; m.L = h->lat_L; m.ys = h->lat_ys; m.xi = d.xi; m.n_eta = n_eta;
+  m.beta = h->p.beta; m.U = U_eq; m.eta = eta;
+  m.F = dF; m.B = dB; m.nu = dnu; m.rev = d.rev; m.ebeta = d.ebeta; m.tau = d.tau; m.mpar = d.mpar;
+  m.e0 = d.eps_ext; m.e0_stride = (long long)(d.nt + 1) * n2;
+  m.G = G; m.Gn = Gn; m.S = S; m.err = derr;
+  HK_CUDA(h, hk::launch_mats_dyson(m, 0, G, h->s));   // the non-interacting G^M of eps(0_|)
+  std::vector<double> e_host(N);
+  int it = 0;
+  double err = INFINITY;
+  for (it = 1; it <= max_iter; ++it) {
+    HK_CUDA(h, hk::launch_mats_sigma(m, h->s));
+    HK_CUDA(h, hk::launch_mats_dyson(m, it, Gn, h->s));
+    HK_CUDA(h, cudaMemcpyAsync(e_host.data(), derr, N * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    HK_CUDA(h, cudaStreamSynchronize(h->s));
+    err = 0.0;
+    for (double e : e_host) err = std::isfinite(e) ? std::max(err, e) : NAN;
+    if (!std::isfinite(err)) return fail(h, HKBE_ERR_NAN, "singular Dyson matrix or non-finite iterate");
+    if (err < tol && it > n_eta) {
+      HK_CUDA(h, cudaMemcpyAsync(G, Gn, per * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+      break;
+    }
+    HK_CUDA(h, hk::launch_mats_mix(m, it > 1 ? mix : 1.0, h->s));
+  }
+  // install: G^M, the convolution tensor of the mixed component, the host copy
+  HK_CUDA(h, cudaMemcpyAsync(d.gm, G, per * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+  HK_CUDA(h, hk::launch_mats_wconv(m, dphi, d.wconv, h->s));
+  h->gm_host.assign(per * 2, 0.0);
+  HK_CUDA(h, cudaMemcpyAsync(h->gm_host.data(), G, per * sizeof(double2), cudaMemcpyDeviceToHost, h->s));
+  HK_CUDA(h, cudaStreamSynchronize(h->s));
+  if (gm_out) std::memcpy(gm_out, h->gm_host.data(), per * sizeof(double2));
+  h->have_gm = true;
+  if (iters) *iters = it > max_iter ? max_iter : it;
+  if (err_out) *err_out = err;
+  if (it > max_iter) return fail(h, HKBE_ERR_NOCONV, "equilibrium iteration reached max_iter");
+  return HKBE_OK;
+}
+
 int hkbe_set_hamiltonian(hkbe_t* h, const double* eps) {
   if (!h || !eps) return fail(h, HKBE_ERR_ARG, "null argument");
   Dev& d = h->d;
@@ -580,6 +676,8 @@ int hkbe_set_model(hkbe_t* h, int model, const double* params, int nparams) {
       mp[(size_t)n * hk::MP] = L;
       mp[(size_t)n * hk::MP + 1] = ys;
     }
+    h->lat_L = L;
+    h->lat_ys = ys;
     h->self_consistent = true;
   } else if (model == HKBE_MODEL_NAMBU) {
     if (no != 2) return fail(h, HKBE_ERR_ARG, "NAMBU needs nao = 2");

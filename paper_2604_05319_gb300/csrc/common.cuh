@@ -47,8 +47,9 @@ HD void st(float2* p, const zd& z) { *p = make_float2((float)z.re, (float)z.im);
 // ---- bulk arithmetic of the history sums --------------------------------
 // Bulk<S>::R is the arithmetic type of the long history contractions for
 // storage type S: double for complex128 storage, float for complex64.  Short
-// runs of products are summed in R and folded into FP64 accumulators (fold),
-// so the rounding of a float partial sum covers a few terms only.
+// runs of products (FOLD terms) are summed in R and then added to a
+// compensated accumulator (KAcc below), so a plain float partial sum never
+// runs over more than a few terms.
 template <typename S> struct Bulk;
 template <> struct Bulk<double2> { using R = double; };
 template <> struct Bulk<float2> { using R = float; };

@@ -102,7 +102,7 @@ __device__ __forceinline__ R rule_wr(const DevW& w, int n, int l) {
   }
 }
 
-constexpr int FOLD = 8;  // terms summed in R before folding into an FP64 accumulator
+constexpr int FOLD = 8;  // terms summed in R before they enter the compensated accumulator
 
 __device__ __forceinline__ zd wshfl(zd v, int off) {
   return zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));

@@ -27,4 +27,11 @@ bool dlr_build(int r, const double* tau, const double* om, double beta, int xi, 
 
 void herm_eig(int n, const std::complex<double>* A, double* E, std::complex<double>* U);
 
+// Linear maps of the Matsubara solve as r x r row-major matrices: values on
+// the DLR nodes tau_i -> values at the r chosen fermionic frequencies nu_k
+// (F), and back (B), with the frequencies nu[r] (the same nodes and maps as
+// hkbe_matsubara_solve).  False if a DLR kernel matrix is singular.
+bool mats_maps(int r, const double* tau, const double* om, double beta, std::vector<std::complex<double>>* F,
+               std::vector<std::complex<double>>* B, std::vector<double>* nu);
+
 }  // namespace hk

@@ -21,6 +21,7 @@
 // K = [[S, 0], [P, C]] (C = E Q^dagger), its SVD by one-sided Jacobi, truncation
 // of singular values below the SVD tolerance (Sec. 2.2), and rotation of U, V.
 #include "hodlr_util.cuh"
+#include "lattice.cuh"
 
 namespace hk {
 
@@ -789,50 +790,12 @@ __global__ void k_density_at(Dev d, int t, double2* out) {
 // mixed: Sigma^tv_r = U(T)U(0_|) G^tv_r(T,tau)^2 G^vt_{-r}(tau,T).
 // The 2D transforms are done as two passes of L-point sums (rows, columns).
 // ---------------------------------------------------------------------------
-constexpr int kLatMaxK = 256;
-// instance holding grid point q = m_x L + m_y (ys: reflection-reduced k-set)
-__device__ __forceinline__ int lat_inst(int q, int L, int ys) {
-  if (!ys) return q;
-  const int y = q % L;
-  return (q / L) * (L / 2 + 1) + min(y, L - y);
-}
-// grid point q is the instance's own k-point (not a reflected copy)
-__device__ __forceinline__ bool lat_owner(int q, int L, int ys) { return !ys || q % L <= L / 2; }
-// in-place 2D DFT of a[N] (N = L*L, index m_x L + m_y) with sign sg (+1: e^{+i}),
-// scaled by sc; tw[m] = e^{2 pi i m / L}; every thread of the CTA must call it
-__device__ void lat_dft2(zd* a, zd* tmp, const zd* tw, int L, int sg, double sc) {
-  const int N = L * L, q = threadIdx.x;
-  const int x = q / L, y = q % L;
-  if (q < N) {  // along m_y: tmp[x][y] = sum_m a[x][m] e^{sg i 2pi m y / L}
-    zd s = zd();
-    for (int m = 0; m < L; ++m) {
-      const zd w = tw[(m * y) % L];
-      s += a[x * L + m] * (sg > 0 ? w : w.conj());
-    }
-    tmp[q] = s;
-  }
-  __syncthreads();
-  if (q < N) {  // along m_x
-    zd s = zd();
-    for (int m = 0; m < L; ++m) {
-      const zd w = tw[(m * x) % L];
-      s += tmp[m * L + y] * (sg > 0 ? w : w.conj());
-    }
-    a[q] = s * sc;
-  }
-  __syncthreads();
-}
-
 template <typename S>
 __global__ void __launch_bounds__(kLatMaxK) k_sigma_lattice(Dev d, int T) {
   __shared__ zd X1[kLatMaxK], X2[kLatMaxK], Y1[kLatMaxK], Y2[kLatMaxK], tmp[kLatMaxK], tw[16];
   const int L = (int)d.mpar[0], ys = (int)d.mpar[1], N = L * L, q = threadIdx.x;
   const int nq = lat_inst(q, L, ys);
-  if (q < L) {
-    double sn, cs;
-    sincospi(2.0 * q / L, &sn, &cs);
-    tw[q] = zd(cs, sn);
-  }
+  lat_twiddles(tw, L);
   const double* U = d.drU;   // U(t) of instance 0 (the same for every k)
   const double invN = 1.0 / N;
   const int b = blockIdx.x;

@@ -170,6 +170,32 @@ struct Solver {
 
 }  // namespace
 
+// F = -Kn Kt^{-1} (to_freq) and B = -Kt Kn^{-1} (to_tau), each from one LU
+// solve of the transposed system: Kt^T X = Kn^T gives F = -X^T, and
+// Kn^T Y = Kt^T gives B = -Y^T.
+bool hk::mats_maps(int r, const double* tau, const double* om, double beta, std::vector<zc>* F,
+                   std::vector<zc>* B, std::vector<double>* nu) {
+  Solver sv;
+  if (!sv.init(r, tau, om, beta, 1)) return false;
+  auto tr = [r](const std::vector<zc>& M) {
+    std::vector<zc> T((size_t)r * r);
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) T[(size_t)j * r + i] = M[(size_t)i * r + j];
+    return T;
+  };
+  std::vector<zc> X = tr(sv.Kn), Y = tr(sv.Kt);
+  if (!zsolve(r, tr(sv.Kt), X.data(), r) || !zsolve(r, tr(sv.Kn), Y.data(), r)) return false;
+  F->assign((size_t)r * r, zc(0));
+  B->assign((size_t)r * r, zc(0));
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      (*F)[(size_t)i * r + j] = -X[(size_t)j * r + i];
+      (*B)[(size_t)i * r + j] = -Y[(size_t)j * r + i];
+    }
+  *nu = sv.nu;
+  return true;
+}
+
 extern "C" int hkbe_matsubara_solve(int r, const double* tau, const double* omega, double beta, int model,
                                     int n_inst, int nao, const double* eps, const double* params, int nparams,
                                     double U_eq, double eta, int n_eta, double mix, double tol, int max_iter,
