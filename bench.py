@@ -364,7 +364,9 @@ def roofline_of(pk, st, w, prof, iters, T_s, K, es, dom, n_inst):
             it = int(iters[j, i])
             nbytes += it * phase_bytes(dom, T, wl.k, no, r, wl.leaf, es, blocks, rk, hod)
             nflops += it * phase_flops(dom, T, wl.k, no, wl.leaf, blocks, rk, hod)
-    launches = int(np.sum(iters))  # one launch of the phase per corrector iteration (all instances)
+    # one launch of the phase (over all instances) per corrector iteration of
+    # the step; a step iterates until its slowest instance has converged
+    launches = int(np.sum(np.max(iters, axis=1)))
     t_dom = prof[dom][0] / 1e3
     return nbytes, nflops, t_dom, launches
 
