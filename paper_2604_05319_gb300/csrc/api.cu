@@ -365,7 +365,7 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
     }
     if ((rc = dalloc_el(h, &d.band, N * d.nt * d.k * n2)) ||
         (rc = dalloc(h, &d.proj, N * d.no * d.maxl * n2 * d.rmax + N * d.nblk * n2 * d.no * 2 * d.rmax)) ||
-        (rc = dalloc(h, &d.tsvd_ws, ctas * d.tsvd_ws_per)) || (rc = dalloc(h, &h->status_dev, 2)) ||
+        (rc = dalloc(h, &d.tsvd_ws, ctas * d.tsvd_ws_per)) ||
         (rc = dalloc(h, &h->rowbuf_r, (size_t)d.nt * n2)) || (rc = dalloc(h, &h->rowbuf_l, (size_t)d.nt * n2)) ||
         (rc = upload(h, &d.b_r0, h->g_r0)) || (rc = upload(h, &d.b_r1, h->g_r1)) ||
         (rc = upload(h, &d.b_c0, h->g_c0)) || (rc = upload(h, &d.b_c1, h->g_c1)) ||
@@ -377,7 +377,6 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
       hkbe_destroy(h);
       return rc;
     }
-    d.status = h->status_dev;
     h->scratch.insert(h->scratch.end(), {d.tsvd_ws, h->rowbuf_r, h->rowbuf_l});
   }
   if (d.prec) {
@@ -402,6 +401,14 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
   }
   d.nchunk = (d.nt + 31) / 32;
   d.nfrozR = d.nfrozL = 0;
+  // status words: [0] TSVD ranks capped at r_max, [1] TSVD Jacobi non-convergence,
+  // [2] timed-out waits for a staged chunk inverse (sweeps)
+  if ((rc = dalloc(h, &h->status_dev, 3))) {
+    g_create_error = h->err;
+    hkbe_destroy(h);
+    return rc;
+  }
+  d.status = h->status_dev;
   {
     const size_t ld = 32 * (size_t)d.no;
     if ((rc = dalloc(h, &d.cinv, (size_t)d.n_inst * d.nchunk * 2 * ld * ld)) ||
@@ -1007,15 +1014,17 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
       d.cdir += d.L;
     }
   }
-  if (h->hodlr) {
-    // TSVD status of the compressions of these steps: [0] ranks capped at
-    // r_max, [1] block cores whose Jacobi SVD did not converge in 40 sweeps
-    // (their factors are the last sweep's, still a factorisation of the block).
-    int st[2] = {0, 0};
+  {
+    // status of these steps: [0] ranks capped at r_max, [1] block cores whose
+    // Jacobi SVD did not converge in 40 sweeps (their factors are the last
+    // sweep's, still a factorisation of the block), [2] timed-out waits for a
+    // staged chunk inverse (that chunk was read from global memory instead)
+    int st[3] = {0, 0, 0};
     HK_CUDA(h, cudaMemcpyAsync(st, h->status_dev, sizeof(st), cudaMemcpyDeviceToHost, h->s));
     HK_CUDA(h, cudaMemsetAsync(h->status_dev, 0, sizeof(st), h->s));
     HK_CUDA(h, cudaStreamSynchronize(h->s));
     drain(h);
+    if (st[2] > 0) return fail(h, HKBE_ERR_CUDA, "a bulk copy of a chunk inverse into shared memory timed out");
     if (st[0] > 0) return fail(h, HKBE_ERR_RANK, "a block's epsilon-rank exceeded r_max (truncated to r_max)");
     if (st[1] > 0)
       return fail(h, HKBE_ERR_NOCONV, "the Jacobi SVD of " + std::to_string(st[1]) +
@@ -1300,8 +1309,8 @@ int hkbe_rewind(hkbe_t* h) {
     d.cdir = 0;
     for (int X = 0; X < 4; ++X)
       HK_CUDA(h, cudaMemsetAsync(d.hod[X].rank, 0, (size_t)d.n_inst * d.nblk * n2 * sizeof(int), h->s));
-    HK_CUDA(h, cudaMemsetAsync(h->status_dev, 0, 2 * sizeof(int), h->s));
   }
+  HK_CUDA(h, cudaMemsetAsync(h->status_dev, 0, 3 * sizeof(int), h->s));
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   h->cur = k;
   return HKBE_OK;

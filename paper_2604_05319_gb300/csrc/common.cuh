@@ -60,6 +60,50 @@ template <typename R> HD cx<R> ldr(const cx<R>* p) { return *p; }
 HD zd wide(const zd& z) { return z; }
 HD zd wide(const zf& z) { return zd((double)z.re, (double)z.im); }
 
+// ---- float-float arithmetic ----------------------------------------------
+// A real value held as the unevaluated sum hi + lo of two floats (|lo| at
+// most half an ulp of hi): about 48 significant bits, computed on the FP32
+// pipes with the error-free transformations TwoSum (Knuth) and TwoProduct
+// (Dekker, here with a fused multiply-add).  It replaces FP64 in short,
+// precision-critical sums that many threads evaluate at once (an FP64
+// instruction of a warp costs this chip many times an FP32 one).
+struct ffl {
+  float hi, lo;
+};
+HD ffl ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+HD ffl ff_fast(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+HD ffl ff_add(const ffl& a, const ffl& b) {
+  const ffl s = ff_two_sum(a.hi, b.hi);
+  return ff_fast(s.hi, s.lo + (a.lo + b.lo));
+}
+HD ffl ff_neg(const ffl& a) { return {-a.hi, -a.lo}; }
+HD ffl ff_mul(const ffl& a, const ffl& b) {
+  const float p = a.hi * b.hi;
+  return ff_fast(p, fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+HD ffl ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+HD double ff_val(const ffl& a) { return (double)a.hi + (double)a.lo; }
+
+struct cff {
+  ffl re, im;
+};
+HD cff cff_add(const cff& a, const cff& b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+HD cff cff_mul(const cff& a, const cff& b) {
+  return {ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(a.im, b.im))), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
+}
+HD cff cff_of(const zd& z) { return {ff_of(z.re), ff_of(z.im)}; }
+HD cff cff_of(const zf& z) { return {ffl{z.re, 0.f}, ffl{z.im, 0.f}}; }
+HD zd cff_val(const cff& a) { return zd(ff_val(a.re), ff_val(a.im)); }
+
 // Accumulator of a long history sum in the bulk arithmetic R.  Complex64
 // form (R = float): compensated (Kahan) summation, the rounding of every
 // addition kept in c and fed back, so the sum keeps FP32 precision relative to

@@ -18,6 +18,7 @@
 // A chunk's solve is then F times the inverse (retarded, row vector) or the
 // inverse times F (lesser), where F holds everything outside the chunk (the
 // far field).  Only the chunks near T are solved point by point in one warp.
+#include "bulk_copy.cuh"
 #include "hodlr_util.cuh"
 
 namespace hk {
@@ -28,6 +29,41 @@ constexpr int CK = 32;   // chunk length
 using Y = double2;       // element type of the row / column being solved
 template <int NO> constexpr bool kStage = NO <= 2;   // hot-chunk coefficients staged in shared memory
 template <int NO> constexpr size_t kStageBytes = kStage<NO> ? sizeof(zd) * CK * CK * NO * NO : 0;
+// Bytes of a frozen chunk inverse that are staged in shared memory (the
+// dynamic buffer of the hot-chunk coefficients, free while a frozen chunk is
+// solved) by a bulk copy issued before the chunk's far field, so the copy
+// overlaps that phase: the whole inverse (FP64, or the hi and lo matrices of
+// the complex64 form, 16 bytes per entry either way); 0 (read from global
+// memory) for N_o > 2.
+template <int NO, typename S>
+constexpr uint32_t kInvStage = kStage<NO> ? (uint32_t)(CK * NO * CK * NO * sizeof(double2)) : 0u;
+static_assert(kInvStage<2, double2> <= kStageBytes<2> && kInvStage<1, double2> <= kStageBytes<1>,
+              "a staged inverse must fit the hot-chunk buffer");
+constexpr int kCopyWaitPolls = 1 << 20;   // bound of the wait for a staged inverse
+
+// Sum over the 8 lanes of an aligned lane group of their history
+// accumulators (every lane receives it).  Complex64 form: the compensated
+// FP32 sums are combined in float-float, so the reduction runs on the FP32
+// pipes; FP64 form: plain FP64.  val_of converts to FP64 (once, by the lane
+// that uses the sum).
+__device__ __forceinline__ cff cff_shfl_xor(const cff& a, int off) {
+  return {{__shfl_xor_sync(FULL, a.re.hi, off), __shfl_xor_sync(FULL, a.re.lo, off)},
+          {__shfl_xor_sync(FULL, a.im.hi, off), __shfl_xor_sync(FULL, a.im.lo, off)}};
+}
+__device__ __forceinline__ cff reduce8(const KAcc<float>& k) {
+  cff r = {ff_two_sum(k.s.re, -k.c.re), ff_two_sum(k.s.im, -k.c.im)};
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) r = cff_add(r, cff_shfl_xor(r, off));
+  return r;
+}
+__device__ __forceinline__ zd reduce8(const KAcc<double>& k) {
+  zd v = k.get();
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) v += zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));
+  return v;
+}
+__device__ __forceinline__ zd val_of(const cff& a) { return cff_val(a); }
+__device__ __forceinline__ zd val_of(const zd& a) { return a; }
 
 // Where a sweep keeps the row it solves: in place (FP64 storage), or in FP64
 // next to the complex64 storage: the row's slot of the FP64 ring copies of the
@@ -62,6 +98,79 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
   return d.cinv + (((long long)n * d.nchunk + cc) * 2 + which) * nn;
 }
 
+// Projections of one block of Sigma^R for all N_o^2 orbital pairs in one pass
+// (N_o <= 2, rank <= 64): out_p[q] = S_p[q] sum_{l in [l0, l1)} v_p(l) F_p(l, q)
+// for q < rank_p, with F = U (ROWS: the retarded sweep, v_p = y_m, m = p / N_o)
+// or F = conj(V) (the lesser sweep, v_p = w_l x_nn, nn = p % N_o); vf(l, i)
+// returns the vector's component i at l.  Warps split the rows of the block,
+// lanes the rank; the N_o^2 pairs share the vector loads and one cross-warp
+// reduction in red ([8][N_o^2][64], shared memory).  Every thread calls it.
+template <int NO, typename S, bool ROWS, typename VF>
+__device__ __forceinline__ void proj_block(const Dev& d, int n, int blk, int lv, int slot, int l0, int l1, VF vf,
+                                           zd* red) {
+  constexpr int NO2 = NO * NO;
+  using R = typename Bulk<S>::R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int rk[NO2];
+  const S* F[NO2];
+#pragma unroll
+  for (int p = 0; p < NO2; ++p) {
+    rk[p] = *Rk<NO>(d, 2, n, blk, p);
+    F[p] = ROWS ? Up<NO, S>(d, 2, n, blk, p) : Vp<NO, S>(d, 2, n, blk, p);
+  }
+  const int base = ROWS ? d.b_r0[blk] : d.b_c0[blk];
+  KAcc<R> part[NO2][2];
+  for (int s0 = l0 + warp; s0 < l1; s0 += 8 * FOLD) {
+    cx<R> pp[NO2][2];
+#pragma unroll
+    for (int p = 0; p < NO2; ++p) pp[p][0] = pp[p][1] = cx<R>(0);
+#pragma unroll
+    for (int jj = 0; jj < FOLD; ++jj) {
+      const int l = s0 + 8 * jj;
+      if (l < l1) {
+        cx<R> v[NO];
+#pragma unroll
+        for (int i = 0; i < NO; ++i) v[i] = vf(l, i);
+#pragma unroll
+        for (int p = 0; p < NO2; ++p) {
+          const S* fr = F[p] + (long long)(l - base) * d.rmax;
+          const cx<R> vp = v[ROWS ? p / NO : p % NO];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = lane + 32 * u;
+            if (q < rk[p]) {
+              const cx<R> f = ROWS ? ldr<R>(fr + q) : ldr<R>(fr + q).conj();
+              pp[p][u] = cfma(vp, f, pp[p][u]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NO2; ++p) {
+      part[p][0].add(pp[p][0]);
+      part[p][1].add(pp[p][1]);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NO2; ++p) {
+    red[(warp * NO2 + p) * 64 + lane] = part[p][0].get();
+    red[(warp * NO2 + p) * 64 + lane + 32] = part[p][1].get();
+  }
+  __syncthreads();
+  for (int e = tid; e < NO2 * d.rmax; e += blockDim.x) {
+    const int p = e / d.rmax, q = e % d.rmax;
+    zd acc = zd();
+    for (int w2 = 0; w2 < 8; ++w2) acc += red[(w2 * NO2 + p) * 64 + q];
+    int rkp = 0;
+#pragma unroll
+    for (int pp2 = 0; pp2 < NO2; ++pp2)
+      if (pp2 == p) rkp = rk[pp2];
+    st(Pj<NO>(d, n, slot, lv, p) + q, q < rkp ? acc * Sp<NO>(d, 2, n, blk, p)[q] : zd());
+  }
+  __syncthreads();
+}
+
 // Sum over q < rk of P[q] * F[q] (or P[q] * conj(F[q])): the far field of one
 // compressed block at one row or column, P its projection vector staged in
 // shared memory, F the block's factor row in global memory.  Four threads
@@ -90,7 +199,7 @@ __device__ __forceinline__ cx<R> lr_dot4(const cx<R>* P, const S* F, int rk, int
 // t' = T-1 .. 0; the start block t' >= T-k is solved together.
 // ---------------------------------------------------------------------------
 template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
+__global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_ret2(Dev d, int T, int staged) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
   const int n = blockIdx.y, irow = blockIdx.x;
@@ -105,10 +214,21 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ zd Fb[CK][NO];      // the BDF part of Fs (rows at the chunk edge; zero elsewhere)
+  __shared__ zd Old[CK][NO];     // the chunk's previous iterate (convergence measure)
+  __shared__ zf Ff[CK][NO];      // complex64 form: the far field (Fs - Fb) rounded to complex64
+  __shared__ cff FbF[CK][NO];    // complex64 form: Fb in float-float
   __shared__ double serr;
-  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
-                                 // entry (staged != 0) the block projections [maxl][NO2][rmax]
-  if (tid == 0) serr = 0.0;
+  extern __shared__ __align__(16) zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2);
+                                 // at leaf entry (staged != 0) the block projections
+                                 // [maxl][NO2][rmax]; for a frozen chunk its staged inverse
+  __shared__ __align__(8) uint64_t cbar;   // completion of the inverse's bulk copy
+  __shared__ int s_stage;                  // 0 once a wait for a copy has timed out
+  uint32_t cphase = 0;
+  if (tid == 0) {
+    serr = 0.0;
+    s_stage = 1;
+    if (kInvStage<NO, S>) mbar_init(&cbar);
+  }
   // The row being solved lives in FP64 during the sweep (in the complex64
   // storage form a separate buffer), so the point-to-point recursion of the
   // sweep (BDF terms, point solves) does not accumulate storage rounding.
@@ -167,6 +287,12 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
         const int blk = d.colblk[jl * d.maxl + lv];
         if (blk < 0 || d.b_c1[blk] != E) continue;
         const int r0 = d.b_r0[blk], rl = min(d.b_r1[blk], c);
+        if (kStage<NO> && Row64<NO, S>::separate && d.rmax <= 64) {   // complex64 form: all pairs
+                                                                       // in one pass (ctile is free here)
+          proj_block<NO, S, true>(d, n, blk, lv, irow, r0, rl,
+                                  [&](int s2, int m) { return ldr<R>(sp(s2) + m); }, ctile);
+          continue;
+        }
         for (int p = 0; p < NO2; ++p) {
           const int m = p / NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
@@ -292,6 +418,9 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
       }
       __syncthreads();
     }
+    // the frozen inverse of this chunk into shared memory, overlapping the far field
+    const bool stage_now = kInvStage<NO, S> && cc < d.nfrozR && s_stage;
+    if (stage_now && tid == 0) bulk_g2s(ctile, Cinv<NO>(d, n, cc, 0), kInvStage<NO, S>, &cbar);
     // ---- far field of the chunk: rows s >= b not covered above; 8 threads per column ----
     {
       const int col = tid >> 3, sl = tid & 7;
@@ -326,12 +455,10 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
         }
       }
 #pragma unroll
-        for (int j = 0; j < NO; ++j) acc[j] += ka[j].get();
-#pragma unroll
-      for (int j = 0; j < NO; ++j)
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1)
-          acc[j] += zd(__shfl_xor_sync(FULL, acc[j].re, off), __shfl_xor_sync(FULL, acc[j].im, off));
+      for (int j = 0; j < NO; ++j) {
+        const auto r = reduce8(ka[j]);
+        if (sl == 0) acc[j] = val_of(r);
+      }
       if (sl == 0 && col < cn) {
         zd F[NO];
         zd Fbd[NO];
@@ -351,46 +478,64 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
         for (int j = 0; j < NO; ++j) {
           Fs[col][j] = F[j] + Fbd[j];
           Fb[col][j] = Fbd[j];
+          Ff[col][j] = zf((float)F[j].re, (float)F[j].im);
+          FbF[col][j] = cff_of(Fbd[j]);
         }
       }
+      if (sl == 1 && col < cn)
+#pragma unroll
+        for (int j = 0; j < NO; ++j) Old[col][j] = ld(sp(tp) + j);
     }
     __syncthreads();
     if (cc < d.nfrozR) {
       // frozen chunk: y = F C^-1 (row vector times the precomputed inverse),
       // 8 threads per output element
       const double2* Mi = Cinv<NO>(d, n, cc, 0);
+      bool smem_inv = false;
+      if (stage_now) {
+        smem_inv = mbar_wait(&cbar, cphase, kCopyWaitPolls);
+        cphase ^= 1u;
+        if (!smem_inv) {
+          s_stage = 0;
+          atomicAdd(d.status + 2, 1);
+        }
+      }
+      const double2* Mg = smem_inv ? reinterpret_cast<const double2*>(ctile) : Mi;
       constexpr int LD = CK * NO;
       for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
         const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, j = o % NO;
         zd sacc = zd();
         if constexpr (Row64<NO, S>::separate) {
-          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in FP64
-          const float2* Mh = reinterpret_cast<const float2*>(Mi);
+          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo)
+          // in float-float, reduced over the 8 lanes in float-float
+          const float2* Mh = reinterpret_cast<const float2*>(Mg);
           const float2* Ml = Mh + LD * LD;
           zf s32 = zf(0);
           for (int si = sl; si < CK; si += 8)
 #pragma unroll
-            for (int m = 0; m < NO; ++m) {
-              const zd ff = Fs[si][m] - Fb[si][m];
-              s32 = cfma(zf((float)ff.re, (float)ff.im), ldr<float>(Mh + (long long)(si * NO + m) * LD + ti * NO + j), s32);
-            }
-          sacc = wide(s32);
+            for (int m = 0; m < NO; ++m)
+              s32 = cfma(Ff[si][m], ldr<float>(Mh + (long long)(si * NO + m) * LD + ti * NO + j), s32);
+          cff sf = cff_of(s32);
           for (int si = CK - k + sl; si < CK; si += 8)
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               const long long e = (long long)(si * NO + m) * LD + ti * NO + j;
-              sacc = cfma(Fb[si][m], ld(Mh + e) + ld(Ml + e), sacc);
+              const float2 hv = Mh[e], lv = Ml[e];
+              sf = cff_add(sf, cff_mul(FbF[si][m], cff{{hv.x, lv.x}, {hv.y, lv.y}}));
             }
+#pragma unroll
+          for (int off = 1; off < 8; off <<= 1) sf = cff_add(sf, cff_shfl_xor(sf, off));
+          if (sl == 0) sacc = cff_val(sf);
         } else {
           for (int si = sl; si < CK; si += 8)
 #pragma unroll
-            for (int m = 0; m < NO; ++m) sacc = cfma(Fs[si][m], ld(Mi + (long long)(si * NO + m) * LD + ti * NO + j), sacc);
-        }
+            for (int m = 0; m < NO; ++m) sacc = cfma(Fs[si][m], ld(Mg + (long long)(si * NO + m) * LD + ti * NO + j), sacc);
 #pragma unroll
-        for (int off = 1; off < 8; off <<= 1)
-          sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
+          for (int off = 1; off < 8; off <<= 1)
+            sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
+        }
         if (sl == 0) {
-          myerr = fmax(myerr, (sacc - ld(sp(a + ti) + j)).abs2());
+          myerr = fmax(myerr, (sacc - Old[ti][j]).abs2());
           st(yp(a + ti) + j, sacc);
           if constexpr (Row64<NO, S>::separate) st(sp(a + ti) + j, sacc);
         }
@@ -481,13 +626,16 @@ __global__ void __launch_bounds__(256) k_ret2(Dev d, int T, int staged) {
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
   if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+  // after a timed-out wait, a copy may still be in flight into this CTA's
+  // shared memory: wait for it (bounded) before the CTA exits
+  if (kInvStage<NO, S> && tid == 0 && !s_stage) mbar_wait(&cbar, cphase ^ 1u, kCopyWaitPolls);
 }
 
 // ---------------------------------------------------------------------------
 // Lesser column, Eq. KBEL: unknown x(t) = G^<(t, T) (column jc), t = 0..T.
 // ---------------------------------------------------------------------------
 template <int NO, typename S>
-__global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
+__global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_les2(Dev d, int T, int staged) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
   const int n = blockIdx.y, jc = blockIdx.x;
@@ -502,10 +650,21 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
   __shared__ zd pbuf[8][128];
   __shared__ zd Fs[CK][NO];
   __shared__ zd Fb[CK][NO];      // the BDF part of Fs (rows at the chunk edge; zero elsewhere)
+  __shared__ zd Old[CK][NO];     // the chunk's previous iterate (convergence measure)
+  __shared__ zf Ff[CK][NO];      // complex64 form: the far field (Fs - Fb) rounded to complex64
+  __shared__ cff FbF[CK][NO];    // complex64 form: Fb in float-float
   __shared__ double serr;
-  extern __shared__ zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2); at leaf
-                                 // entry (staged != 0) the block projections [maxl][NO2][rmax]
-  if (tid == 0) serr = 0.0;
+  extern __shared__ __align__(16) zd ctile[];  // [CK][CK][NO2] hot-chunk coefficients (N_o <= 2);
+                                 // at leaf entry (staged != 0) the block projections
+                                 // [maxl][NO2][rmax]; for a frozen chunk its staged inverse
+  __shared__ __align__(8) uint64_t cbar;   // completion of the inverse's bulk copy
+  __shared__ int s_stage;                  // 0 once a wait for a copy has timed out
+  uint32_t cphase = 0;
+  if (tid == 0) {
+    serr = 0.0;
+    s_stage = 1;
+    if (kInvStage<NO, S>) mbar_init(&cbar);
+  }
   // FP64 column during the sweep (see k_ret2); xp: as solved, sp: storage
   S* colp = el<NO, S>(d.GL, d, n, T, 0);
   Y* coly = Row64<NO, S>::get(d, n, 1, T, colp);
@@ -534,6 +693,14 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
         const int blk = d.rowblk[jl * d.maxl + lv];
         if (blk < 0 || d.b_r0[blk] != A) continue;
         const int c0 = d.b_c0[blk], c1 = d.b_c1[blk];
+        if (kStage<NO> && Row64<NO, S>::separate && d.rmax <= 64) {   // complex64 form: all pairs
+                                                                       // in one pass (ctile is free here)
+          proj_block<NO, S, false>(d, n, blk, lv, jc, c0, c1, [&](int l, int nn) {
+            const R wl = (l <= k) ? (R)W.omega[l] : (R)1;
+            return ldr<R>(sp(l) + nn * NO + jc) * wl;
+          }, ctile);
+          continue;
+        }
         for (int p = 0; p < NO2; ++p) {
           const int nn = p % NO;
           const int rk = *Rk<NO>(d, 2, n, blk, p);
@@ -635,13 +802,17 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
       }
       __syncthreads();
     }
+    const bool frozen = (cc < d.nfrozL) && (b - a == ((cc == 0) ? CK - 1 : CK));
+    // the frozen inverse of this chunk into shared memory, overlapping the far field
+    const bool stage_now = kInvStage<NO, S> && frozen && s_stage;
+    if (stage_now && tid == 0) bulk_g2s(ctile, Cinv<NO>(d, n, cc, 1), kInvStage<NO, S>, &cbar);
     // ---- far field F(t) = q(t) - sum_{l < a} C(t,l) x(l); 8 threads per row ----
     {
       const int row = tid >> 3, sl = tid & 7;
       const int t = a + row;
-      zd acc[NO];
+      zd acc[NO], fbo[NO];   // fbo: this lane's BDF part (only the owner lane's is nonzero)
 #pragma unroll
-      for (int m = 0; m < NO; ++m) acc[m] = zd();
+      for (int m = 0; m < NO; ++m) acc[m] = fbo[m] = zd();
         KAcc<R> ka[NO];   // FP32 history sums, compensated (FP64 in the FP64 form)
       if (row < cn) {
         if (t <= k) {
@@ -660,7 +831,7 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
             }
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
-              acc[m] += fb[m];
+              fbo[m] = fb[m];
               Fb[row][m] = fb[m];
             }
           }
@@ -701,62 +872,83 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
             }
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
-              acc[m] += fb[m];
+              fbo[m] = fb[m];
               Fb[row][m] = fb[m];
             }
           }
         }
       }
+      // the BDF part from its owner lane (sl 0 for the start rows, else sl 1)
+      const int owner = (lane & ~7) | (t <= k ? 0 : 1);
 #pragma unroll
-        for (int m = 0; m < NO; ++m) acc[m] += ka[m].get();
+      for (int m = 0; m < NO; ++m) {
+        const auto r = reduce8(ka[m]);
+        const zd fbm(__shfl_sync(FULL, fbo[m].re, owner), __shfl_sync(FULL, fbo[m].im, owner));
+        if (sl == 0 && row < cn) {
+          const zd far = val_of(r) + (comp && t > k ? FB[t - A][m] * h : zd()) +
+                         ld(qs + (long long)t * NO2 + m * NO + jc);
+          Fs[row][m] = far + fbm;
+          Ff[row][m] = zf((float)far.re, (float)far.im);
+          FbF[row][m] = cff_of(fbm);
+        }
+      }
+      (void)acc;
+      if (sl == 1 && row < cn)
 #pragma unroll
-      for (int m = 0; m < NO; ++m)
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1)
-          acc[m] += zd(__shfl_xor_sync(FULL, acc[m].re, off), __shfl_xor_sync(FULL, acc[m].im, off));
-      if (sl == 0 && row < cn)
-#pragma unroll
-        for (int m = 0; m < NO; ++m)
-          Fs[row][m] = acc[m] + (comp && t > k ? FB[t - A][m] * h : zd()) + ld(qs + (long long)t * NO2 + m * NO + jc);
+        for (int m = 0; m < NO; ++m) Old[row][m] = ld(sp(t) + m * NO + jc);
     }
     __syncthreads();
-    const bool frozen = (cc < d.nfrozL) && (b - a == ((cc == 0) ? CK - 1 : CK));
     if (frozen) {
       const double2* Mi = Cinv<NO>(d, n, cc, 1);
+      bool smem_inv = false;
+      if (stage_now) {
+        smem_inv = mbar_wait(&cbar, cphase, kCopyWaitPolls);
+        cphase ^= 1u;
+        if (!smem_inv) {
+          s_stage = 0;
+          atomicAdd(d.status + 2, 1);
+        }
+      }
+      const double2* Mg = smem_inv ? reinterpret_cast<const double2*>(ctile) : Mi;
       constexpr int LD = CK * NO;
       for (int o8 = tid; o8 < CK * NO * 8; o8 += blockDim.x) {
         const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, m = o % NO;
         zd sacc = zd();
         if constexpr (Row64<NO, S>::separate) {
           // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in FP64
-          const float2* Mh = reinterpret_cast<const float2*>(Mi);
+          const float2* Mh = reinterpret_cast<const float2*>(Mg);
           const float2* Ml = Mh + LD * LD;
+          cff sf = cff_of(zf(0));
           if (ti < cn) {
             zf s32 = zf(0);
             for (int li = sl; li < cn; li += 8)
 #pragma unroll
-              for (int y = 0; y < NO; ++y) {
-                const zd ff = Fs[li][y] - (li < k ? Fb[li][y] : zd());
-                s32 = cfma(ldr<float>(Mh + (long long)(ti * NO + m) * LD + li * NO + y), zf((float)ff.re, (float)ff.im), s32);
-              }
-            sacc = wide(s32);
+              for (int y = 0; y < NO; ++y)
+                s32 = cfma(ldr<float>(Mh + (long long)(ti * NO + m) * LD + li * NO + y), Ff[li][y], s32);
+            sf = cff_of(s32);
             for (int li = sl; li < k && li < cn; li += 8)
 #pragma unroll
               for (int y = 0; y < NO; ++y) {
                 const long long e = (long long)(ti * NO + m) * LD + li * NO + y;
-                sacc = cfma(ld(Mh + e) + ld(Ml + e), Fb[li][y], sacc);
+                const float2 hv = Mh[e], lv = Ml[e];
+                sf = cff_add(sf, cff_mul(cff{{hv.x, lv.x}, {hv.y, lv.y}}, FbF[li][y]));
               }
           }
-        } else if (ti < cn) {
-          for (int li = sl; li < cn; li += 8)
 #pragma unroll
-            for (int y = 0; y < NO; ++y) sacc = cfma(ld(Mi + (long long)(ti * NO + m) * LD + li * NO + y), Fs[li][y], sacc);
+          for (int off = 1; off < 8; off <<= 1) sf = cff_add(sf, cff_shfl_xor(sf, off));
+          if (sl == 0) sacc = cff_val(sf);
+        } else {
+          if (ti < cn)
+            for (int li = sl; li < cn; li += 8)
+#pragma unroll
+              for (int y = 0; y < NO; ++y)
+                sacc = cfma(ld(Mg + (long long)(ti * NO + m) * LD + li * NO + y), Fs[li][y], sacc);
+#pragma unroll
+          for (int off = 1; off < 8; off <<= 1)
+            sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
         }
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1)
-          sacc += zd(__shfl_xor_sync(FULL, sacc.re, off), __shfl_xor_sync(FULL, sacc.im, off));
         if (sl == 0 && ti < cn) {
-          myerr = fmax(myerr, (sacc - ld(sp(a + ti) + m * NO + jc)).abs2());
+          myerr = fmax(myerr, (sacc - Old[ti][m]).abs2());
           st(xp(a + ti) + m * NO + jc, sacc);
           if constexpr (Row64<NO, S>::separate) st(sp(a + ti) + m * NO + jc, sacc);
         }
@@ -886,6 +1078,9 @@ __global__ void __launch_bounds__(256) k_les2(Dev d, int T, int staged) {
   if (lane == 0 && myerr > 0) atomic_max_nonneg(&serr, myerr);
   __syncthreads();
   if (tid == 0) atomic_max_nonneg(d.err + n, serr);
+  // after a timed-out wait, a copy may still be in flight into this CTA's
+  // shared memory: wait for it (bounded) before the CTA exits
+  if (kInvStage<NO, S> && tid == 0 && !s_stage) mbar_wait(&cbar, cphase ^ 1u, kCopyWaitPolls);
 }
 
 // ---------------------------------------------------------------------------
