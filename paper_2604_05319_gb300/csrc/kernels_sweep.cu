@@ -99,34 +99,43 @@ __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which)
 }
 
 // Projections of one block of Sigma^R for all N_o^2 orbital pairs in one pass
-// (N_o <= 2, rank <= 64): out_p[q] = S_p[q] sum_{l in [l0, l1)} v_p(l) F_p(l, q)
-// for q < rank_p, with F = U (ROWS: the retarded sweep, v_p = y_m, m = p / N_o)
-// or F = conj(V) (the lesser sweep, v_p = w_l x_nn, nn = p % N_o); vf(l, i)
-// returns the vector's component i at l.  Warps split the rows of the block,
-// lanes the rank; the N_o^2 pairs share the vector loads and one cross-warp
-// reduction in red ([8][N_o^2][64], shared memory).  Every thread calls it.
+// (complex64 form, N_o <= 2, rank <= 64): out_p[q] = S_p[q] sum_{l in [l0, l1)}
+// v_p(l) F_p(l, q) for q < rank_p, with F = U (ROWS: the retarded sweep, v_p =
+// y_m, m = p / N_o) or F = conj(V) (the lesser sweep, v_p = w_l x_nn, nn =
+// p % N_o); vf(l, i) returns the vector's component i at l.  A warp covers
+// 32 / lpr rows per step, lpr = 8, 16 or 32 lanes per row (the smallest that
+// holds the largest rank), so small ranks keep every lane loading; warps split
+// the rows, and the pairs share the vector loads.  Partial sums (compensated
+// FP32) are combined across a warp's rows in float-float and across warps in
+// red ([8][N_o^2][64], shared memory).  Every thread calls it.
 template <int NO, typename S, bool ROWS, typename VF>
 __device__ __forceinline__ void proj_block(const Dev& d, int n, int blk, int lv, int slot, int l0, int l1, VF vf,
                                            zd* red) {
   constexpr int NO2 = NO * NO;
   using R = typename Bulk<S>::R;
+  static_assert(sizeof(R) == sizeof(float), "the one-pass projections serve the complex64 form");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int rk[NO2];
   const S* F[NO2];
+  int rkmax = 0;
 #pragma unroll
   for (int p = 0; p < NO2; ++p) {
     rk[p] = *Rk<NO>(d, 2, n, blk, p);
     F[p] = ROWS ? Up<NO, S>(d, 2, n, blk, p) : Vp<NO, S>(d, 2, n, blk, p);
+    rkmax = max(rkmax, rk[p]);
   }
   const int base = ROWS ? d.b_r0[blk] : d.b_c0[blk];
+  const int lpr = rkmax <= 8 ? 8 : rkmax <= 16 ? 16 : 32;   // lanes per row
+  const int rps = 32 / lpr, sub = lane / lpr, q0 = lane % lpr;
+  const int stride = 8 * rps;                               // rows per CTA step
   KAcc<R> part[NO2][2];
-  for (int s0 = l0 + warp; s0 < l1; s0 += 8 * FOLD) {
+  for (int sb = l0 + warp * rps + sub; sb < l1; sb += stride * FOLD) {
     cx<R> pp[NO2][2];
 #pragma unroll
     for (int p = 0; p < NO2; ++p) pp[p][0] = pp[p][1] = cx<R>(0);
 #pragma unroll
     for (int jj = 0; jj < FOLD; ++jj) {
-      const int l = s0 + 8 * jj;
+      const int l = sb + stride * jj;
       if (l < l1) {
         cx<R> v[NO];
 #pragma unroll
@@ -137,7 +146,7 @@ __device__ __forceinline__ void proj_block(const Dev& d, int n, int blk, int lv,
           const cx<R> vp = v[ROWS ? p / NO : p % NO];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const int q = lane + 32 * u;
+            const int q = q0 + lpr * u;
             if (q < rk[p]) {
               const cx<R> f = ROWS ? ldr<R>(fr + q) : ldr<R>(fr + q).conj();
               pp[p][u] = cfma(vp, f, pp[p][u]);
@@ -153,19 +162,24 @@ __device__ __forceinline__ void proj_block(const Dev& d, int n, int blk, int lv,
     }
   }
 #pragma unroll
-  for (int p = 0; p < NO2; ++p) {
-    red[(warp * NO2 + p) * 64 + lane] = part[p][0].get();
-    red[(warp * NO2 + p) * 64 + lane + 32] = part[p][1].get();
-  }
+  for (int p = 0; p < NO2; ++p)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      cff r = {ff_two_sum(part[p][u].s.re, -part[p][u].c.re), ff_two_sum(part[p][u].s.im, -part[p][u].c.im)};
+      for (int off = lpr; off < 32; off <<= 1) r = cff_add(r, cff_shfl_xor(r, off));
+      const int q = q0 + lpr * u;
+      if (sub == 0 && q < 64) red[(warp * NO2 + p) * 64 + q] = cff_val(r);
+    }
   __syncthreads();
   for (int e = tid; e < NO2 * d.rmax; e += blockDim.x) {
     const int p = e / d.rmax, q = e % d.rmax;
-    zd acc = zd();
-    for (int w2 = 0; w2 < 8; ++w2) acc += red[(w2 * NO2 + p) * 64 + q];
     int rkp = 0;
 #pragma unroll
     for (int pp2 = 0; pp2 < NO2; ++pp2)
       if (pp2 == p) rkp = rk[pp2];
+    zd acc = zd();
+    if (q < rkp)   // entries q >= the pair's rank are not written by every warp
+      for (int w2 = 0; w2 < 8; ++w2) acc += red[(w2 * NO2 + p) * 64 + q];
     st(Pj<NO>(d, n, slot, lv, p) + q, q < rkp ? acc * Sp<NO>(d, 2, n, blk, p)[q] : zd());
   }
   __syncthreads();
@@ -287,11 +301,12 @@ __global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_ret2(Dev d, int T, i
         const int blk = d.colblk[jl * d.maxl + lv];
         if (blk < 0 || d.b_c1[blk] != E) continue;
         const int r0 = d.b_r0[blk], rl = min(d.b_r1[blk], c);
-        if (kStage<NO> && Row64<NO, S>::separate && d.rmax <= 64) {   // complex64 form: all pairs
-                                                                       // in one pass (ctile is free here)
-          proj_block<NO, S, true>(d, n, blk, lv, irow, r0, rl,
-                                  [&](int s2, int m) { return ldr<R>(sp(s2) + m); }, ctile);
-          continue;
+        if constexpr (kStage<NO> && Row64<NO, S>::separate) {   // complex64 form: all pairs in one
+          if (d.rmax <= 64) {                                     // pass (ctile is free here)
+            proj_block<NO, S, true>(d, n, blk, lv, irow, r0, rl,
+                                    [&](int s2, int m) { return ldr<R>(sp(s2) + m); }, ctile);
+            continue;
+          }
         }
         for (int p = 0; p < NO2; ++p) {
           const int m = p / NO;
@@ -693,13 +708,14 @@ __global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_les2(Dev d, int T, i
         const int blk = d.rowblk[jl * d.maxl + lv];
         if (blk < 0 || d.b_r0[blk] != A) continue;
         const int c0 = d.b_c0[blk], c1 = d.b_c1[blk];
-        if (kStage<NO> && Row64<NO, S>::separate && d.rmax <= 64) {   // complex64 form: all pairs
-                                                                       // in one pass (ctile is free here)
-          proj_block<NO, S, false>(d, n, blk, lv, jc, c0, c1, [&](int l, int nn) {
-            const R wl = (l <= k) ? (R)W.omega[l] : (R)1;
-            return ldr<R>(sp(l) + nn * NO + jc) * wl;
-          }, ctile);
-          continue;
+        if constexpr (kStage<NO> && Row64<NO, S>::separate) {   // complex64 form: all pairs in one
+          if (d.rmax <= 64) {                                     // pass (ctile is free here)
+            proj_block<NO, S, false>(d, n, blk, lv, jc, c0, c1, [&](int l, int nn) {
+              const R wl = (l <= k) ? (R)W.omega[l] : (R)1;
+              return ldr<R>(sp(l) + nn * NO + jc) * wl;
+            }, ctile);
+            continue;
+          }
         }
         for (int p = 0; p < NO2; ++p) {
           const int nn = p % NO;
