@@ -104,6 +104,14 @@ HD cff cff_of(const zd& z) { return {ff_of(z.re), ff_of(z.im)}; }
 HD cff cff_of(const zf& z) { return {ffl{z.re, 0.f}, ffl{z.im, 0.f}}; }
 HD zd cff_val(const cff& a) { return zd(ff_val(a.re), ff_val(a.im)); }
 
+#ifdef __CUDACC__
+// a float-float complex from lane (this lane ^ off) of the warp (all lanes call it)
+__device__ __forceinline__ cff cff_shfl_xor(const cff& a, int off) {
+  return {{__shfl_xor_sync(0xffffffffu, a.re.hi, off), __shfl_xor_sync(0xffffffffu, a.re.lo, off)},
+          {__shfl_xor_sync(0xffffffffu, a.im.hi, off), __shfl_xor_sync(0xffffffffu, a.im.lo, off)}};
+}
+#endif
+
 // Accumulator of a long history sum in the bulk arithmetic R.  Complex64
 // form (R = float): compensated (Kahan) summation, the rounding of every
 // addition kept in c and fed back, so the sum keeps FP32 precision relative to
@@ -127,6 +135,26 @@ template <> struct KAcc<double> {
   HD void add(const zd& x) { s += x; }
   HD zd get() const { return s; }
 };
+
+#ifdef __CUDACC__
+// Sum of a history accumulator over the lanes reached by xor offsets from,
+// 2 from, ... below to (an aligned lane group); every lane of the group
+// receives it.  Compensated FP32: combined in float-float (FP32 pipes);
+// FP64: plain.  val_of gives the FP64 value (taken by the lane that uses it).
+__device__ __forceinline__ cff kacc_lanes(const KAcc<float>& k, int from, int to) {
+  cff r = {ff_two_sum(k.s.re, -k.c.re), ff_two_sum(k.s.im, -k.c.im)};
+  for (int off = from; off < to; off <<= 1) r = cff_add(r, cff_shfl_xor(r, off));
+  return r;
+}
+__device__ __forceinline__ zd kacc_lanes(const KAcc<double>& k, int from, int to) {
+  zd v = k.get();
+  for (int off = from; off < to; off <<= 1)
+    v += zd(__shfl_xor_sync(0xffffffffu, v.re, off), __shfl_xor_sync(0xffffffffu, v.im, off));
+  return v;
+}
+__device__ __forceinline__ zd val_of(const cff& a) { return cff_val(a); }
+__device__ __forceinline__ zd val_of(const zd& a) { return a; }
+#endif
 
 HD zd cdiv(const zd& a, const zd& b) {
   double d = b.re * b.re + b.im * b.im;

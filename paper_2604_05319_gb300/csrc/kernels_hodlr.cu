@@ -74,18 +74,31 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
   // YB values of y per pass over a factor row (N_o <= 2: all of them), so each
   // factor row is read once per pair and side.
   constexpr int YB = NO <= 2 ? NO : 1;
-  __shared__ zd pbuf[8][YB * 128];
-  // P1 serves pair p = (x, z) (uses g[z]); P2 serves pair p = (z, x) (uses g[z]);
-  // g_l[z][y] = conj(G^R(T,l)[y][z]).  Warps over rows / columns, lanes over rank.
-  for (int job = 0; job < NO2 * 2 * (NO / YB); ++job) {
+  // A job is one (side, pair, y-block); it runs on a group of wpj warps (one
+  // warp per job when there are at least 8 jobs), the group splitting the
+  // job's rows.  Within a warp, lpr = 8, 16 or 32 lanes cover the rank of a
+  // factor row (with up to 4 entries per lane: ranks up to 128), so a small
+  // rank keeps every lane loading (32 / lpr rows per step).  P1 serves pair p = (x, z) (uses g[z]); P2 serves pair p = (z, x)
+  // (uses g[z]); g_l[z][y] = conj(G^R(T,l)[y][z]).
+  constexpr int NJOB = NO2 * 2 * (NO / YB);
+  constexpr int WPJ = NJOB >= 8 ? 1 : 8 / NJOB;
+  constexpr int NGRP = 8 / WPJ;
+  __shared__ zd pbuf[WPJ > 1 ? 8 : 1][YB * 128];  // a group's per-warp partial sums
+  const int grp = warp / WPJ, wig = warp % WPJ;
+  for (int job0 = 0; job0 < NJOB; job0 += NGRP) {
+    const int job = job0 + grp;
+    const bool act = job < NJOB;
     const int which = job & 1, rest = job >> 1;
-    const int yb = (rest % (NO / YB)) * YB, p = rest / (NO / YB);
+    const int yb = (rest % (NO / YB)) * YB, p = act ? rest / (NO / YB) : 0;
     const int z = which == 0 ? p % NO : p / NO;
-    const int rk = *Rk<NO>(d, 3, n, b, p);
+    const int rk = act ? *Rk<NO>(d, 3, n, b, p) : 0;
     const S* F = which == 0 ? Up<NO, S>(d, 3, n, b, p) : Vp<NO, S>(d, 3, n, b, p);
-    const int lo = which == 0 ? r0 : c0, hi = which == 0 ? rl : c1;
+    const int lo = which == 0 ? r0 : c0, hi = act ? (which == 0 ? rl : c1) : lo;
+    const int lpr = rk <= 8 ? 8 : rk <= 16 ? 16 : 32;
+    const int rps = 32 / lpr, sub = lane / lpr, q0 = lane % lpr;
+    const int stride = WPJ * rps;
     KAcc<R> part[YB][4];   // compensated FP32 sums in the complex64 form
-    for (int l0 = lo + warp; l0 < hi; l0 += 8 * FOLD) {
+    for (int l0 = lo + wig * rps + sub; l0 < hi; l0 += stride * FOLD) {
       cx<R> pp[YB][4];
 #pragma unroll
       for (int yy = 0; yy < YB; ++yy)
@@ -93,7 +106,7 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
         for (int u = 0; u < 4; ++u) pp[yy][u] = cx<R>(0);
 #pragma unroll
       for (int jj = 0; jj < FOLD; ++jj) {
-        const int l = l0 + 8 * jj;
+        const int l = l0 + stride * jj;
         if (l < hi) {
           const R wl = rule_wr<R>(W, T, l);
           const S* gp = el<NO, S>(d.GR, d, n, T, l);
@@ -103,7 +116,7 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
           const S* fr = F + (long long)(l - lo) * d.rmax;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int q = lane + 32 * u;
+            const int q = q0 + lpr * u;
             if (q < rk) {
               const cx<R> f = ldr<R>(fr + q);
 #pragma unroll
@@ -117,22 +130,34 @@ __global__ void __launch_bounds__(256) k_src_proj(Dev d, int T) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) part[yy][u].add(pp[yy][u]);
     }
+    // the warp's rows combined (every lane calls the shuffles)
 #pragma unroll
     for (int yy = 0; yy < YB; ++yy)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pbuf[warp][yy * 128 + lane + 32 * u] = part[yy][u].get();
-    __syncthreads();
-    if (tid < d.rmax) {
-      const double sv = tid < rk ? Sp<NO>(d, 3, n, b, p)[tid] : 0.0;
-#pragma unroll
-      for (int yy = 0; yy < YB; ++yy) {
-        zd acc = zd();
-        for (int w2 = 0; w2 < 8; ++w2) acc += pbuf[w2][yy * 128 + tid];
-        const zd v = acc * sv;
-        Psrc<NO, R>(d, n, b, p, yb + yy, which)[tid] = cx<R>((R)v.re, (R)v.im);
+      for (int u = 0; u < 4; ++u) {
+        const auto r = kacc_lanes(part[yy][u], lpr, 32);
+        const int q = q0 + lpr * u;   // < 128
+        if (sub == 0 && q < rk) {
+          if (WPJ == 1) {
+            const zd v = val_of(r) * Sp<NO>(d, 3, n, b, p)[q];
+            Psrc<NO, R>(d, n, b, p, yb + yy, which)[q] = cx<R>((R)v.re, (R)v.im);
+          } else {
+            pbuf[warp][yy * 128 + q] = val_of(r);
+          }
+        }
       }
+    if (WPJ > 1) {   // the group's warps combined: at most one job per group here (NJOB <= 8)
+      __syncthreads();
+      if (act && wig == 0)
+        for (int e = lane; e < YB * rk; e += 32) {
+          const int yy = e / rk, q = e % rk;
+          zd acc = zd();
+          for (int w2 = 0; w2 < WPJ; ++w2) acc += pbuf[grp * WPJ + w2][yy * 128 + q];
+          const zd v = acc * Sp<NO>(d, 3, n, b, p)[q];
+          Psrc<NO, R>(d, n, b, p, yb + yy, which)[q] = cx<R>((R)v.re, (R)v.im);
+        }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

@@ -46,24 +46,8 @@ constexpr int kCopyWaitPolls = 1 << 20;   // bound of the wait for a staged inve
 // FP32 sums are combined in float-float, so the reduction runs on the FP32
 // pipes; FP64 form: plain FP64.  val_of converts to FP64 (once, by the lane
 // that uses the sum).
-__device__ __forceinline__ cff cff_shfl_xor(const cff& a, int off) {
-  return {{__shfl_xor_sync(FULL, a.re.hi, off), __shfl_xor_sync(FULL, a.re.lo, off)},
-          {__shfl_xor_sync(FULL, a.im.hi, off), __shfl_xor_sync(FULL, a.im.lo, off)}};
-}
-__device__ __forceinline__ cff reduce8(const KAcc<float>& k) {
-  cff r = {ff_two_sum(k.s.re, -k.c.re), ff_two_sum(k.s.im, -k.c.im)};
-#pragma unroll
-  for (int off = 1; off < 8; off <<= 1) r = cff_add(r, cff_shfl_xor(r, off));
-  return r;
-}
-__device__ __forceinline__ zd reduce8(const KAcc<double>& k) {
-  zd v = k.get();
-#pragma unroll
-  for (int off = 1; off < 8; off <<= 1) v += zd(__shfl_xor_sync(FULL, v.re, off), __shfl_xor_sync(FULL, v.im, off));
-  return v;
-}
-__device__ __forceinline__ zd val_of(const cff& a) { return cff_val(a); }
-__device__ __forceinline__ zd val_of(const zd& a) { return a; }
+template <typename R>
+__device__ __forceinline__ auto reduce8(const KAcc<R>& k) { return kacc_lanes(k, 1, 8); }
 
 // Where a sweep keeps the row it solves: in place (FP64 storage), or in FP64
 // next to the complex64 storage: the row's slot of the FP64 ring copies of the
@@ -165,8 +149,7 @@ __device__ __forceinline__ void proj_block(const Dev& d, int n, int blk, int lv,
   for (int p = 0; p < NO2; ++p)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      cff r = {ff_two_sum(part[p][u].s.re, -part[p][u].c.re), ff_two_sum(part[p][u].s.im, -part[p][u].c.im)};
-      for (int off = lpr; off < 32; off <<= 1) r = cff_add(r, cff_shfl_xor(r, off));
+      const cff r = kacc_lanes(part[p][u], lpr, 32);
       const int q = q0 + lpr * u;
       if (sub == 0 && q < 64) red[(warp * NO2 + p) * 64 + q] = cff_val(r);
     }
