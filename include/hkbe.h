@@ -365,6 +365,14 @@ int hkbe_snapshot_free(hkbe_t* h);
  * counterpart.  Errors: HKBE_ERR_ARG (null), HKBE_ERR_NOMEM, HKBE_ERR_CUDA. */
 int hkbe_fma_peaks(double* fp64_tflops, double* fp32_tflops);
 
+/* The device's FP64 -> FP32 conversion of the complex64 form's mixed-component
+ * history sums (integer-pipe rounding from the IEEE 754 fields, to nearest
+ * with ties away from zero; magnitudes below the normal FP32 range become
+ * zero), applied to x[n] (host) into y[n] (host), for checking it against a
+ * reference rounding.  No handle.  Errors: HKBE_ERR_ARG, HKBE_ERR_NOMEM,
+ * HKBE_ERR_CUDA. */
+int hkbe_f32_of(int n, const double* x, float* y);
+
 /* Checkpoint (Sec. 3.6, checkpoint files: the full simulation state, restart
  * through a constructor).  hkbe_save writes to `path` the parameters, the
  * host-side set-up (DLR grid, G^M, eps, model, step counter, compression

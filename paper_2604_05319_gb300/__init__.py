@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "hkbe_snapshot_restore": ([H], C.c_int),
         "hkbe_snapshot_free": ([H], C.c_int),
         "hkbe_fma_peaks": ([_D, _D], C.c_int),
+        "hkbe_f32_of": ([C.c_int, _D, C.c_void_p], C.c_int),
         "hkbe_get_blocks": ([H, _I, _I, _I, _I, _I, _I], C.c_int),
         "hkbe_get_ranks": ([H, C.c_int, C.c_int, _I, _I], C.c_int),
         "hkbe_set_profiling": ([H, C.c_int], C.c_int),
@@ -309,6 +310,14 @@ def hkbe_solve_matsubara(h, n_inst, r, nao, U_eq=0.0, eta=0.0, n_eta=0, mix=0.5,
     _check(load().hkbe_solve_matsubara(h, float(U_eq), float(eta), int(n_eta), float(mix), float(tol), int(max_iter),
                                        _dp(gm.view(np.float64)), _ip(it), _dp(er)), h)
     return gm, int(it[0]), float(er[0])
+
+
+def hkbe_f32_of(x):
+    """The device's integer-pipe FP64 -> FP32 rounding applied to x (float64 array)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.zeros(x.size, np.float32)
+    _check(load().hkbe_f32_of(int(x.size), _dp(x), y.ctypes.data))
+    return y
 
 
 def hkbe_get_lattice_observables(h, t):

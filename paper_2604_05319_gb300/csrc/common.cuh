@@ -105,6 +105,26 @@ HD cff cff_of(const zf& z) { return {ffl{z.re, 0.f}, ffl{z.im, 0.f}}; }
 HD zd cff_val(const cff& a) { return zd(ff_val(a.re), ff_val(a.im)); }
 
 #ifdef __CUDACC__
+// FP64 -> FP32 on the integer pipes from the IEEE 754 fields: sign, exponent
+// rebiased 1023 -> 127, the top 23 mantissa bits, plus the next bit (round
+// to nearest, ties away from zero; a mantissa carry moves into the exponent):
+// relative error at most 2^-24; magnitudes below the normal FP32 range become
+// zero.  Used where complex128 data feed FP32 products and an FP64 conversion
+// instruction per element would cost more than the products.
+__device__ __forceinline__ float f32_of(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned sign = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned mag = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(sign | (mag + ((lo >> 28) & 1u)));
+}
+__device__ __forceinline__ zf ld_f32(const double2* p) {
+  const double2 v = *p;
+  return zf(f32_of(v.x), f32_of(v.y));
+}
+
 // a float-float complex from lane (this lane ^ off) of the warp (all lanes call it)
 __device__ __forceinline__ cff cff_shfl_xor(const cff& a, int off) {
   return {{__shfl_xor_sync(0xffffffffu, a.re.hi, off), __shfl_xor_sync(0xffffffffu, a.re.lo, off)},

@@ -284,18 +284,54 @@ __global__ void k_mixed(Dev d, int T) {
   zd acc[NO2];
 #pragma unroll
   for (int q = 0; q < NO2; ++q) acc[q] = zd();
-  for (int l = lane; l < T; l += 32) {  // h sum_l w_l Sigma^R(T,l) G^tv(l, tau_i)
-    const double wl = h * rule_w(W, T, l);
-    M<NO> Sm = load<NO>(el<NO, S>(d.SR, d, n, T, l));
-    M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, l, i));
+  if constexpr (sizeof(S) == sizeof(float2)) {
+    // complex64 form: h sum_l w_l Sigma^R(T,l) G^tv(l, tau_i) with FP32 products
+    // (G^tv truncated to FP32 on the integer pipes) in compensated FP32 sums
+    KAcc<float> ka[NO2];
+    const float hf = (float)h;
+    for (int l0 = lane; l0 < T; l0 += 32 * 4) {
+      zf pa[NO2];
 #pragma unroll
-    for (int x = 0; x < NO; ++x)
+      for (int q = 0; q < NO2; ++q) pa[q] = zf(0.f);
 #pragma unroll
-      for (int z = 0; z < NO; ++z) {
-        zd sx = Sm.a[x][z] * wl;
+      for (int jj = 0; jj < 4; ++jj) {
+        const int l = l0 + 32 * jj;
+        if (l < T) {
+          const float wl = hf * rule_wr<float>(W, T, l);
+          const S* sp = el<NO, S>(d.SR, d, n, T, l);
+          const double2* gp = tv<NO>(d.GTV, d, n, l, i);
+          zf g[NO2];
 #pragma unroll
-        for (int y = 0; y < NO; ++y) acc[x * NO + y] = cfma(sx, G.a[z][y], acc[x * NO + y]);
+          for (int q = 0; q < NO2; ++q) g[q] = ld_f32(gp + q);
+#pragma unroll
+          for (int x = 0; x < NO; ++x)
+#pragma unroll
+            for (int z = 0; z < NO; ++z) {
+              const zf sx = ldr<float>(sp + x * NO + z) * wl;
+#pragma unroll
+              for (int y = 0; y < NO; ++y) pa[x * NO + y] = cfma(sx, g[z * NO + y], pa[x * NO + y]);
+            }
+        }
       }
+#pragma unroll
+      for (int q = 0; q < NO2; ++q) ka[q].add(pa[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NO2; ++q) acc[q] = ka[q].get();
+  } else {
+    for (int l = lane; l < T; l += 32) {  // h sum_l w_l Sigma^R(T,l) G^tv(l, tau_i)
+      const double wl = h * rule_w(W, T, l);
+      M<NO> Sm = load<NO>(el<NO, S>(d.SR, d, n, T, l));
+      M<NO> G = load<NO>(tv<NO>(d.GTV, d, n, l, i));
+#pragma unroll
+      for (int x = 0; x < NO; ++x)
+#pragma unroll
+        for (int z = 0; z < NO; ++z) {
+          zd sx = Sm.a[x][z] * wl;
+#pragma unroll
+          for (int y = 0; y < NO; ++y) acc[x * NO + y] = cfma(sx, G.a[z][y], acc[x * NO + y]);
+        }
+    }
   }
   for (int a = lane; a < d.r; a += 32) {  // sum_a Sigma^tv(T, tau_a) W[a][i]
     M<NO> Sm = load<NO>(tv<NO>(d.STV, d, n, T, a));

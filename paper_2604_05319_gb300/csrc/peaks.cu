@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/hkbe.h"
+#include "common.cuh"
 
 namespace {
 
@@ -52,5 +53,33 @@ extern "C" int hkbe_fma_peaks(double* fp64_tflops, double* fp32_tflops) {
     return HKBE_ERR_CUDA;
   int rc = time_fma<double>(sms * 8, 1 << 12, fp64_tflops);
   if (rc == HKBE_OK) rc = time_fma<float>(sms * 8, 1 << 14, fp32_tflops);
+  return rc;
+}
+
+namespace {
+__global__ void k_f32_of(int n, const double* x, float* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = hk::f32_of(x[i]);
+}
+}  // namespace
+
+extern "C" int hkbe_f32_of(int n, const double* x, float* y) {
+  if (n < 0 || (n > 0 && (!x || !y))) return HKBE_ERR_ARG;
+  if (n == 0) return HKBE_OK;
+  double* dx = nullptr;
+  float* dy = nullptr;
+  int rc = HKBE_OK;
+  if (cudaMalloc(&dx, (size_t)n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dy, (size_t)n * sizeof(float)) != cudaSuccess) {
+    rc = HKBE_ERR_NOMEM;
+  } else if (cudaMemcpy(dx, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = HKBE_ERR_CUDA;
+  } else {
+    k_f32_of<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256>>>(n, dx, dy);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(y, dy, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = HKBE_ERR_CUDA;
+  }
+  cudaFree(dx);
+  cudaFree(dy);
   return rc;
 }

@@ -109,3 +109,22 @@ def test_mixed_batch_of_instances_matches_single():
         o.run()
         err = _rel_err(st, o, i)
         assert err < REL, (i, err)
+
+
+def test_integer_fp64_to_fp32_rounding():
+    """The complex64 form's FP64 -> FP32 conversion of G^tv (integer pipes,
+    IEEE 754 fields): equal to round-to-nearest FP32 away from ties, ties away
+    from zero, relative error at most 2^-24, sub-normal-range magnitudes to
+    zero, sign kept."""
+    rng = np.random.default_rng(5)
+    x = rng.choice([-1.0, 1.0], 200000) * 10.0 ** rng.uniform(-37, 30, 200000)   # normal FP32 range
+    y = pk.hkbe_f32_of(x)
+    ref = x.astype(np.float32)
+    assert np.array_equal(y, ref), np.flatnonzero(y != ref)[:5]
+    assert (np.abs(y.astype(np.float64) - x) <= 2.0 ** -24 * np.abs(x)).all()
+    one_tie = 1.0 + 2.0 ** -24          # halfway between 1 and 1 + 2^-23
+    special = np.array([0.0, -0.0, 1.0, -2.5, one_tie, -one_tie, 1e-39, -1e-300, 3.0e38])
+    ys = pk.hkbe_f32_of(special)
+    assert ys[0] == 0 and np.signbit(ys[1]) and ys[2] == 1.0 and ys[3] == -2.5
+    assert ys[4] == np.float32(1.0 + 2.0 ** -23) and ys[5] == -np.float32(1.0 + 2.0 ** -23)
+    assert ys[6] == 0 and ys[7] == 0 and np.signbit(ys[7]) and ys[8] == np.float32(3.0e38)
