@@ -318,6 +318,7 @@ int hkbe_create(const hkbe_params* p, const int32_t* nt_per_inst, void* stream, 
   std::memcpy(d.w.D, w.D, sizeof(w.D));
   std::memcpy(d.w.I0, w.I0, sizeof(w.I0));
   for (int i = 0; i < 6; ++i) {
+    d.w.ah[i] = w.a[i] / p->h;
     d.w.omegaf[i] = (float)w.omega[i];
     for (int j = 0; j < 6; ++j) d.w.I0f[i][j] = (float)w.I0[i][j];
   }

@@ -465,12 +465,15 @@ __global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_ret2(Dev d, int T, i
           F[j] = (acc[j] + (comp ? FB[tp - A][j] : zd())) * h;
           Fbd[j] = zd();
         }
-        for (int jj = 1; jj <= k; ++jj) {  // BDF terms reaching above the chunk
+        for (int jj = 1; jj <= k; ++jj) {  // BDF terms reaching above the chunk: (-i a_j / h) y(s2)
           const int s2 = tp + jj;
           if (s2 < b) continue;
-          const zd cf(0, -W.a[jj] / h);
+          const double cj = W.ah[jj];
 #pragma unroll
-          for (int m = 0; m < NO; ++m) Fbd[m] += cf * ld(yp(s2) + m);
+          for (int m = 0; m < NO; ++m) {
+            const zd y = ld(yp(s2) + m);
+            Fbd[m] = zd(fma(cj, y.im, Fbd[m].re), fma(-cj, y.re, Fbd[m].im));
+          }
         }
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
@@ -863,11 +866,14 @@ __global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_les2(Dev d, int T, i
             zd fb[NO];
 #pragma unroll
             for (int m = 0; m < NO; ++m) fb[m] = zd();
-            for (int jj = 1; jj <= k; ++jj) {
+            for (int jj = 1; jj <= k; ++jj) {   // (-i a_j / h) x(t - j)
               if (t - jj >= a) continue;
-              const zd cf(0, -W.a[jj] / h);
+              const double cj = W.ah[jj];
 #pragma unroll
-              for (int m = 0; m < NO; ++m) fb[m] += cf * ld(xp(t - jj) + m * NO + jc);
+              for (int m = 0; m < NO; ++m) {
+                const zd x = ld(xp(t - jj) + m * NO + jc);
+                fb[m] = zd(fma(cj, x.im, fb[m].re), fma(-cj, x.re, fb[m].im));
+              }
             }
 #pragma unroll
             for (int m = 0; m < NO; ++m) {

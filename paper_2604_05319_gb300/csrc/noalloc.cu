@@ -89,6 +89,7 @@ extern "C" int hkbe_lesser_column_noalloc(int nt, int k, int nao, int r, double 
   std::memcpy(d.w.omega, w.omega, sizeof(w.omega));
   std::memcpy(d.w.D, w.D, sizeof(w.D));
   std::memcpy(d.w.I0, w.I0, sizeof(w.I0));
+  for (int i = 0; i < 6; ++i) d.w.ah[i] = w.a[i] / h;
   d.GR = (double2*)d_gr; d.SR = (double2*)d_sr; d.SL = (double2*)d_sl; d.GL = (double2*)d_gl;
   d.GTV = (double2*)d_gtv; d.STV = (double2*)d_stv; d.eps = (double2*)d_eps;
   d.e0 = (double*)d_e0; d.rev = (double*)d_rev; d.q = (double*)d_q;

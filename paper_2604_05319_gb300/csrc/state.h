@@ -11,6 +11,7 @@ struct DevW {
   int k;
   double a[6], omega[6], D[6][6], I0[6][6];
   float omegaf[6], I0f[6][6];   // float copies for the bulk sums of the complex64 form
+  double ah[6];                  // a_j / h (the BDF coefficients of the time derivative)
 };
 
 constexpr int MP = 64;  // doubles of model parameters per instance
