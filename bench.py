@@ -43,6 +43,7 @@ import argparse
 import hashlib
 import json
 import multiprocessing as mp
+import re
 import statistics
 import subprocess
 import sys
@@ -171,23 +172,38 @@ def phase_flops(phase, T, k, no, L, blocks, ranks, hodlr):
 
 
 KERNEL_OF = {"ret": "k_ret2", "les": "k_les2", "src": "k_src_c"}
-SOURCE_OF = {"ret": "kernels_sweep.cu", "les": "kernels_sweep.cu", "src": "kernels_hodlr.cu"}
+_SWEEP_SRC = ["kernels_sweep.cu", "bulk_copy.cuh", "hodlr_util.cuh", "dev_util.cuh", "common.cuh", "state.h"]
+_SRC_SRC = ["kernels_hodlr.cu", "lattice.cuh", "hodlr_util.cuh", "dev_util.cuh", "common.cuh", "state.h"]
+SOURCE_OF = {"ret": _SWEEP_SRC, "les": _SWEEP_SRC, "src": _SRC_SRC}
+
+
+def code_digest(names):
+    """sha256 of the kernel's translation unit (its .cu and local headers) with
+    comments and white space removed: a change of code, not of comments,
+    invalidates a traffic record taken on the old code."""
+    h = hashlib.sha256()
+    for nm in names:
+        text = open(os.path.join(ROOT, "paper_2604_05319_gb300", "csrc", nm)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [" ".join(line.split()) for line in text.splitlines()]
+        h.update(("\n".join(line for line in lines if line) + "\n").encode())
+    return h.hexdigest()
 
 
 def traffic_record(phase, n_inst, T):
     """DRAM bytes per launch of the phase's main kernel from a committed ncu
     summary (profiles/traffic_<kernel>.json: dram__bytes_read.sum +
-    dram__bytes_write.sum of one capture, per instance, with the sha256 of
-    the kernel source it was taken on), scaled to n_inst instances and to
-    step T in proportion to T.  None when there is no capture or the source
-    has changed since."""
+    dram__bytes_write.sum of one capture, per instance, with the code digest
+    of the kernel's sources it was taken on), scaled to n_inst instances and to
+    step T in proportion to T.  None when there is no capture or the code has
+    changed since."""
     kern = KERNEL_OF.get(phase)
     p = os.path.join(ROOT, "profiles", f"traffic_{kern}.json")
     if kern is None or not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    src = os.path.join(ROOT, "paper_2604_05319_gb300", "csrc", SOURCE_OF[phase])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec.get("source_sha256"):
+    if code_digest(SOURCE_OF[phase]) != rec.get("code_sha256"):
         return None
     return float(rec["dram_bytes_per_instance"]) * n_inst * (T / float(rec["T"]))
 

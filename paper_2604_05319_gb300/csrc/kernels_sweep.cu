@@ -74,8 +74,9 @@ struct Row64<NO, double2> {
 // splits into the far field (history sums, lesser source), whose image under
 // the inverse is about h / a_0 times smaller than the row and needs FP32 only,
 // and the BDF terms reaching across the chunk edge (k rows), which carry the
-// implicit recursion and get hi + lo in FP64; a plain complex64 inverse would
-// put 2^-24 times the BDF amplitude a_j / h into every chunk and accumulate.
+// implicit recursion and get hi + lo in float-float (about 48 bits); a plain
+// complex64 inverse would put 2^-24 times the BDF amplitude a_j / h into
+// every chunk and accumulate.
 template <int NO>
 __device__ __forceinline__ double2* Cinv(const Dev& d, int n, int cc, int which) {
   const long long nn = (long long)(CK * NO) * (CK * NO);
@@ -920,7 +921,8 @@ __global__ void __launch_bounds__(256, (NO <= 2) ? 2 : 1) k_les2(Dev d, int T, i
         const int o = o8 >> 3, sl = o8 & 7, ti = o / NO, m = o % NO;
         zd sacc = zd();
         if constexpr (Row64<NO, S>::separate) {
-          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in FP64
+          // complex64 form: far field x hi in FP32, the k edge rows x (hi + lo) in
+          // float-float, reduced over the 8 lanes in float-float
           const float2* Mh = reinterpret_cast<const float2*>(Mg);
           const float2* Ml = Mh + LD * LD;
           cff sf = cff_of(zf(0));

@@ -101,3 +101,17 @@ def test_library_partition_matches_the_definition():
         assert (lib["level"] >= 0).all() and (np.diff(np.sort(np.unique(lib["level"]))) == 1).all()
     with pytest.raises(pk.HKBEError):
         pk.hkbe_hodlr_partition(0, 64)
+
+
+def test_code_digest_ignores_comments_only(tmp_path, monkeypatch):
+    """A traffic record stays valid across comment edits of the kernel's
+    sources and is invalidated by a code edit."""
+    csrc = tmp_path / "paper_2604_05319_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("// header\nint f(int x) {  /* block\n comment */ return x + 1; }\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.code_digest(["k.cu"])
+    (csrc / "k.cu").write_text("// another header\n\nint f(int x) { return   x + 1; }  // note\n")
+    assert bench.code_digest(["k.cu"]) == d0
+    (csrc / "k.cu").write_text("int f(int x) { return x + 2; }\n")
+    assert bench.code_digest(["k.cu"]) != d0
