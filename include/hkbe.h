@@ -263,8 +263,11 @@ int hkbe_set_initial_slices(hkbe_t* h, const double* gr, const double* gl, const
  * nt-1), HKBE_ERR_NOCONV (state kept; the step counter still advances: the
  * self-consistency loop reached max_iter, or, HODLR form, the Jacobi SVD of a
  * TSVD block core did not converge in 40 sweeps), HKBE_ERR_RANK (a block's
- * epsilon-rank was capped at r_max).  The TSVD conditions are counted over
- * the n_steps of this call and reset afterwards. */
+ * epsilon-rank was capped at r_max), HKBE_ERR_CUDA (a CUDA error, or a
+ * sweep's bounded wait for the shared-memory copy of a frozen chunk inverse
+ * timed out; that chunk was then read from global memory).  The TSVD and
+ * copy conditions are counted over the n_steps of this call and reset
+ * afterwards. */
 int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err);
 
 /* Current time step T (the last completed step), -1 before the bootstrap. */
