@@ -291,6 +291,22 @@ class KBEOracle:
         """Row G^R(T, .) from Eq. KBER in the second argument: start block
         s = 1..k, then BDF + Gregory (Appendix A) point solves for s > k."""
         k, h, No, W = self.k, self.h, self.no, self.W
+        y = self._ret_start_block(T)
+        a = W.a
+        for s in range(k + 1, T + 1):
+            w = W.rule(s)
+            Ks = self.SR[T - np.arange(s + 1), T - s]          # SR(T-l, T-s), l=0..s
+            rhs = -(1j / h) * np.einsum("j,jxy->xy", a[1:], y[s - 1:s - k - 1:-1] if s - k - 1 >= 0 else y[s - 1::-1][:k])
+            rhs = rhs + h * np.einsum("l,lxy,lyz->xz", w[:s], y[:s], Ks[:s])
+            M = (1j * a[0] / h) * self.I1 - self.ep(T - s) - h * w[s] * Ks[s]
+            y[s] = np.linalg.solve(M.T, rhs.T).T
+        for s in range(T + 1):
+            self.GR[T, T - s] = y[s]
+
+    def _ret_start_block(self, T):
+        """y_s = G^R(T, T-s) for s = 0..k (y_0 = -i, the start block of
+        Eq. KBER solved together); entries s > k left zero."""
+        k, h, No, W = self.k, self.h, self.no, self.W
         y = np.zeros((T + 1, No, No), complex)
         y[0] = -1j * self.I1
 
@@ -311,16 +327,7 @@ class KBEOracle:
         Ys = np.linalg.solve(C.T, Bm.T).T
         for s in range(1, k + 1):
             y[s] = Ys[:, (s - 1) * No:s * No]
-        a = W.a
-        for s in range(k + 1, T + 1):
-            w = W.rule(s)
-            Ks = self.SR[T - np.arange(s + 1), T - s]          # SR(T-l, T-s), l=0..s
-            rhs = -(1j / h) * np.einsum("j,jxy->xy", a[1:], y[s - 1:s - k - 1:-1] if s - k - 1 >= 0 else y[s - 1::-1][:k])
-            rhs = rhs + h * np.einsum("l,lxy,lyz->xz", w[:s], y[:s], Ks[:s])
-            M = (1j * a[0] / h) * self.I1 - self.ep(T - s) - h * w[s] * Ks[s]
-            y[s] = np.linalg.solve(M.T, rhs.T).T
-        for s in range(T + 1):
-            self.GR[T, T - s] = y[s]
+        return y
 
     def solve_mixed(self, T):
         """G^tv(T, tau_i) from Eq. KBET: BDF + Gregory point solve with the DLR
