@@ -156,6 +156,22 @@ int hkbe_matsubara_solve(int r, const double* tau, const double* omega, double b
 int hkbe_solve_matsubara(hkbe_t* h, double U_eq, double eta, int n_eta, double mix, double tol, int max_iter,
                          double* gm_out, int32_t* iters, double* err);
 
+/* Time-step scheme of the retarded row and the lesser column (default:
+ * HKBE_SCHEME_PAPER, the sweeps of Eqs. KBER and KBEL).
+ * HKBE_SCHEME_SWEEP_FREE is a variant that is not in the paper (it differs
+ * from the paper's discretisation at O(h^k)):
+ *   - retarded row: the k points next to the diagonal are the start block of
+ *     Eq. KBER; every t' further away comes from the retarded Dyson equation
+ *     in its first time argument (BDF over the rows T - j, the Gregory rule
+ *     of Appendix A over [t', T]), one N_o x N_o solve per t';
+ *   - lesser column: the resolvent form of Eq. KBEL's equation in its first
+ *     argument, G^<(t,T) = i G^R(t,0) G^<(0,T) + h sum_l w^(t)_l G^R(t,l) q_l;
+ *   - so no point of either waits for its neighbour.
+ * Dense FP64 storage only (compressed or complex64 handles: HKBE_ERR_ARG).
+ * Must precede hkbe_bootstrap; hkbe_save refuses a handle of this scheme. */
+enum { HKBE_SCHEME_PAPER = 0, HKBE_SCHEME_SWEEP_FREE = 1 };
+int hkbe_set_scheme(hkbe_t* h, int scheme);
+
 /* Release every device and host resource of h (NULL is accepted). */
 int hkbe_destroy(hkbe_t* h);
 

@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
                                   _I, _D], C.c_int),
         "hkbe_solve_matsubara": ([H, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D, _I, _D],
                                  C.c_int),
+        "hkbe_set_scheme": ([H, C.c_int], C.c_int),
         "hkbe_bootstrap": ([H, C.c_int, C.c_double, _I, _D], C.c_int),
         "hkbe_set_initial_slices": ([H, _D, _D, _D], C.c_int),
         "hkbe_get_observables": ([H, C.c_int, _D, _D, _D], C.c_int),
@@ -318,6 +319,13 @@ def hkbe_f32_of(x):
     y = np.zeros(x.size, np.float32)
     _check(load().hkbe_f32_of(int(x.size), _dp(x), y.ctypes.data))
     return y
+
+
+SCHEME_PAPER, SCHEME_SWEEP_FREE = 0, 1
+
+
+def hkbe_set_scheme(h, scheme):
+    _check(load().hkbe_set_scheme(h, int(scheme)), h)
 
 
 def hkbe_get_lattice_observables(h, t):

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhkbe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "kernels_dense.cu", "kernels_hodlr.cu", "kernels_sweep.cu", "host_numerics.cpp", "noalloc.cu", "matsubara.cpp", "matsubara_dev.cu", "peaks.cu"]
+SOURCES = ["api.cu", "kernels_dense.cu", "kernels_hodlr.cu", "kernels_sweep.cu", "kernels_sweepfree.cu", "host_numerics.cpp", "noalloc.cu", "matsubara.cpp", "matsubara_dev.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 

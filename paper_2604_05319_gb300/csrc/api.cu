@@ -12,6 +12,7 @@
 #include "host_numerics.h"
 #include "state.h"
 #include "matsubara_dev.h"
+#include "sweepfree.h"
 
 using hk::Dev;
 using zc = std::complex<double>;
@@ -26,6 +27,7 @@ struct hkbe_s {
   bool have_dlr = false, have_gm = false, have_eps = false, have_model = false;
   bool self_consistent = true;
   int lat_L = 0, lat_ys = 0;   // LATTICE2B grid and reduced-set flag
+  int scheme = 0;              // HKBE_SCHEME_PAPER or HKBE_SCHEME_SWEEP_FREE
   std::vector<double> tau, om, gm_host, eps_host;
   hk::DLRMats dm;
   int* any_dev = nullptr;
@@ -592,6 +594,17 @@ int hkbe_solve_matsubara(hkbe_t* h, double U_eq, double eta, int n_eta, double m
   return HKBE_OK;
 }
 
+int hkbe_set_scheme(hkbe_t* h, int scheme) {
+  if (!h) return fail(h, HKBE_ERR_ARG, "null handle");
+  if (scheme != HKBE_SCHEME_PAPER && scheme != HKBE_SCHEME_SWEEP_FREE)
+    return fail(h, HKBE_ERR_ARG, "unknown scheme");
+  if (h->cur >= 0) return fail(h, HKBE_ERR_ARG, "hkbe_set_scheme must precede hkbe_bootstrap");
+  if (scheme == HKBE_SCHEME_SWEEP_FREE && (h->hodlr || h->d.prec != 0 || h->d.k * h->d.no > 20))
+    return fail(h, HKBE_ERR_ARG, "the sweep-free scheme runs in the dense FP64 storage form (k N_o <= 20)");
+  h->scheme = scheme;
+  return HKBE_OK;
+}
+
 int hkbe_set_hamiltonian(hkbe_t* h, const double* eps) {
   if (!h || !eps) return fail(h, HKBE_ERR_ARG, "null argument");
   Dev& d = h->d;
@@ -962,7 +975,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
   for (int st = 0; st < n_steps; ++st) {
     const int T = h->cur + 1;
     // inverses of the chunks that became frozen (their rows are final and far enough from T)
-    {
+    if (h->scheme == HKBE_SCHEME_PAPER) {
       const int tR = std::max(0, (T - 2 * d.k) / 32), tL = std::max(0, T / 32);
       if (tR > d.nfrozR) {
         HK_CUDA(h, run_phase(h, HKBE_PHASE_CHUNKINV, tR - d.nfrozR,
@@ -985,7 +998,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                    if ((e = run_phase(h, HKBE_PHASE_SIGMA, 1, [&]() { return hk::launch_sigma(d, T, h->s); })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_RET, 1, [&]() {
-                          return hk::launch_ret_h(d, T, h->s);
+                          return h->scheme ? hk::launch_ret_sf(d, T, h->s) : hk::launch_ret_h(d, T, h->s);
                         })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_MIXED, 1, [&]() { return hk::launch_mixed(d, T, h->s); })))
@@ -996,7 +1009,7 @@ int hkbe_step(hkbe_t* h, int n_steps, int32_t* iters, double* err) {
                         })))
                      return e;
                    if ((e = run_phase(h, HKBE_PHASE_LES, 1, [&]() {
-                          return hk::launch_les_h(d, T, h->s);
+                          return h->scheme ? hk::launch_les_sf(d, T, h->s) : hk::launch_les_h(d, T, h->s);
                         })))
                      return e;
                    if (d.rho_mode == 1 &&
@@ -1387,6 +1400,7 @@ extern "C" {
 
 int hkbe_save(hkbe_t* h, const char* path) {
   if (!h || !path) return fail(h, HKBE_ERR_ARG, "null argument");
+  if (h->scheme != HKBE_SCHEME_PAPER) return fail(h, HKBE_ERR_ARG, "checkpoints hold runs of the paper's scheme only");
   HK_CUDA(h, cudaStreamSynchronize(h->s));
   drain(h);
   FILE* f = std::fopen(path, "w+b");   // read back for the checksum trailer
