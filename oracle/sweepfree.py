@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-This is not the paper's discretisation but a variant of it (the survey's
-NEXT-2): every point of the new retarded row and of the new lesser column is
+This is not the paper's discretisation but a variant of it: every point of
+the new retarded row and of the new lesser column is
 an independent small solve or a quadrature over stored history, so nothing is
 solved point after point along the row.  It shares the bootstrap (the k + 1
 start steps), the mixed component (Eq. KBET), the lesser source q (Eq. KBEL,
